@@ -1,0 +1,178 @@
+"""O3: analytic potentials and energies used to pin the oracle.  TEST INFRASTRUCTURE ONLY.
+
+Sources:
+  * 3D Coulomb of a Gaussian: u = Q erf(r/s) / (4 pi r) for rho = exp(-r^2/s^2), Q = pi^{3/2} s^3
+    (Gauss's law); pair energies of Gaussian clouds Q_i Q_j erf(d / sqrt(s_i^2+s_j^2))/(4 pi d).
+  * 2.5D Coulomb of a Gaussian, eq. (4.2) (Example 1).
+  * Example 4 (eqs. 4.10-4.11): rho = [-2 beta + 4 sum x_i^2/a_i^2] e^{-g}  ->  u = -e^{-g}.
+  * Example 5: 3D dipole, u = -rho + 6 [2 g_n^2 - sum n_i^2/a_i] e^{-g}.
+  * Example 7: dipole energy of a cylindrical Gaussian, closed form in kappa = sqrt(gz/gx).
+  * The 1D t-integral for anisotropic Gaussians, from 1/|x| = (2/sqrt(pi)) int_0^inf
+    e^{-|x|^2 t^2} dt: for rho = prod_i exp(-x_i^2/a_i),
+        u(x) = C_d (2/sqrt(pi)) int_0^inf prod_i sqrt(pi a_i/(1+a_i t^2))
+                                       exp(-x_i^2 t^2/(1+a_i t^2)) dt,
+    C_3 = 1/(4 pi) (3D Coulomb), C_2 = 1/(2 pi) (2.5D Coulomb).
+Coordinates: functions take the coordinate arrays in (x, y[, z]) order.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from scipy import special
+
+
+# ----------------------------------------------------------------- 3D Coulomb, Gaussians
+def coulomb3d_gauss(r: np.ndarray, s: float = 1.0, w: float = 1.0) -> np.ndarray:
+    """Potential of w exp(-r^2/s^2): w pi^{3/2} s^3 erf(r/s) / (4 pi r), finite at r = 0."""
+    r = np.asarray(r, dtype=np.float64)
+    Q = w * math.pi ** 1.5 * s ** 3
+    out = np.empty_like(r)
+    small = r < 1e-8 * s
+    rr = r[~small]
+    out[~small] = Q * special.erf(rr / s) / (4.0 * math.pi * rr)
+    out[small] = Q * (2.0 / (math.sqrt(math.pi) * s)) / (4.0 * math.pi)
+    return out
+
+
+def coulomb3d_mixture(x, y, z, centres, widths, weights) -> np.ndarray:
+    u = 0.0
+    for c, s, w in zip(centres, widths, weights):
+        r = np.sqrt((x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2)
+        u = u + coulomb3d_gauss(r, s, w)
+    return u
+
+
+def coulomb3d_mixture_energy(centres, widths, weights, lam: float = 1.0) -> float:
+    """(lambda/2) sum_ij Q_i Q_j erf(d_ij/S_ij)/(4 pi d_ij), S_ij = sqrt(s_i^2 + s_j^2)."""
+    Q = [w * math.pi ** 1.5 * s ** 3 for s, w in zip(widths, weights)]
+    tot = 0.0
+    for i in range(len(Q)):
+        for j in range(len(Q)):
+            S = math.sqrt(widths[i] ** 2 + widths[j] ** 2)
+            dd = float(np.linalg.norm(np.asarray(centres[i]) - np.asarray(centres[j])))
+            if dd < 1e-12:
+                g = 2.0 / (math.sqrt(math.pi) * S)
+            else:
+                g = math.erf(dd / S) / dd
+            tot += Q[i] * Q[j] * g / (4.0 * math.pi)
+    return 0.5 * lam * tot
+
+
+def coulomb3d_gauss_energy(s: float = 1.0, lam: float = 1.0) -> float:
+    """Energy of exp(-r^2/s^2): lambda pi^{3/2} s^5 / (4 sqrt 2)."""
+    return lam * math.pi ** 1.5 * s ** 5 / (4.0 * math.sqrt(2.0))
+
+
+# ----------------------------------------------------------------- 2.5D Coulomb (eq. 4.2)
+def coulomb2d_gauss(r: np.ndarray, a: float) -> np.ndarray:
+    """Eq. (4.2): rho = exp(-r^2/a) -> u = (sqrt(pi a)/2) e^{-r^2/2a} I_0(r^2/2a)."""
+    z = np.asarray(r, dtype=np.float64) ** 2 / (2.0 * a)
+    return 0.5 * math.sqrt(math.pi * a) * special.i0e(z)
+
+
+# ----------------------------------------------------------------- 1D t-integral forms
+def _t_rule(n_panels: int = 96, order: int = 24):
+    """Composite Gauss-Legendre rule for int_0^inf f(t) dt via t = s/(1-s), s in [0,1),
+    with panels graded towards s = 0 (the integrand varies on the scale t ~ 1/|x|)."""
+    edges = np.concatenate([[0.0], np.geomspace(1e-6, 1.0, n_panels)])
+    xi, om = np.polynomial.legendre.leggauss(order)
+    s_all, w_all = [], []
+    for a, b in zip(edges[:-1], edges[1:]):
+        s = a + (b - a) * (1 + xi) / 2
+        w = (b - a) * om / 2
+        s_all.append(s)
+        w_all.append(w)
+    s = np.concatenate(s_all)
+    w = np.concatenate(w_all)
+    t = s / (1.0 - s)
+    return t, w / (1.0 - s) ** 2
+
+
+def aniso_gauss_potential(coords, a, centre=None, kind: str = "coulomb3d", axis=None,
+                          chunk: int = 65536) -> np.ndarray:
+    """Potential of prod_i exp(-(x_i - c_i)^2 / a_i) by the t-integral.
+
+    kind: "coulomb3d" (1/(4 pi |x|)), "coulomb2d" (1/(2 pi |x|)), or "dipole_nn3d", which
+    returns -3 d_nn u_Coulomb (the dipole potential without its -rho term), differentiating
+    the Gaussian factor under the integral: d_nn G = [4 (sum b_i n_i x_i)^2 - 2 sum b_i n_i^2] G,
+    b_i = t^2/(1 + a_i t^2).
+    """
+    d = len(coords)
+    shape = np.broadcast(*coords).shape
+    X = [np.broadcast_to(c, shape).ravel() - (0.0 if centre is None else centre[i])
+         for i, c in enumerate(coords)]
+    a = np.asarray(a, dtype=np.float64)
+    t, wt = _t_rule()
+    pref = (1.0 / (4.0 * math.pi) if kind != "coulomb2d" else 1.0 / (2.0 * math.pi)) * 2.0 / math.sqrt(math.pi)
+    out = np.empty(X[0].size)
+    for s0 in range(0, X[0].size, chunk):
+        xs = [xx[s0:s0 + chunk, None] for xx in X]
+        t2 = t[None, :] ** 2
+        amp = np.ones((1, t.size))
+        expo = np.zeros((xs[0].shape[0], t.size))
+        b = []
+        for i in range(d):
+            bi = t2 / (1.0 + a[i] * t2)
+            b.append(bi)
+            amp = amp * np.sqrt(math.pi * a[i] / (1.0 + a[i] * t2))
+            expo = expo - xs[i] ** 2 * bi
+        G = amp * np.exp(expo)
+        if kind == "dipole_nn3d":
+            n = np.asarray(axis, dtype=np.float64)
+            n = n / np.linalg.norm(n)
+            s1 = sum(b[i] * n[i] * xs[i] for i in range(d))
+            s2 = sum(b[i] * n[i] ** 2 for i in range(d))
+            G = -3.0 * (4.0 * s1 ** 2 - 2.0 * s2) * G
+        out[s0:s0 + chunk] = pref * (G @ wt)
+    return out.reshape(shape)
+
+
+# ----------------------------------------------------------------- Examples 4 and 5
+def ex4_rho(x, y, z, a=(1.0, 1.3, 1.5)):
+    g = x * x / a[0] + y * y / a[1] + z * z / a[2]
+    beta = 1 / a[0] + 1 / a[1] + 1 / a[2]
+    return (-2.0 * beta + 4.0 * (x * x / a[0] ** 2 + y * y / a[1] ** 2 + z * z / a[2] ** 2)) * np.exp(-g)
+
+
+def ex4_u(x, y, z, a=(1.0, 1.3, 1.5)):
+    return -np.exp(-(x * x / a[0] + y * y / a[1] + z * z / a[2]))
+
+
+def ex5_u(x, y, z, n, a=(1.3, 1.5, 1.8)):
+    n = np.asarray(n, dtype=np.float64)
+    n = n / np.linalg.norm(n)
+    g = x * x / a[0] + y * y / a[1] + z * z / a[2]
+    gn = x * n[0] / a[0] + y * n[1] / a[1] + z * n[2] / a[2]
+    s = n[0] ** 2 / a[0] + n[1] ** 2 / a[1] + n[2] ** 2 / a[2]
+    return -ex4_rho(x, y, z, a) + 6.0 * (2.0 * gn * gn - s) * np.exp(-g)
+
+
+# ----------------------------------------------------------------- Example 7
+def ex7_rho(x, y, z, gx: float, gz: float):
+    return math.pi ** -1.5 * gx * math.sqrt(gz) * np.exp(-(gx * (x * x + y * y) + gz * z * z))
+
+
+def ex7_energy(gx: float, gz: float, lam: float) -> float:
+    """Dipole energy (axis z) of pi^{-3/2} gx sqrt(gz) exp(-(gx (x^2+y^2) + gz z^2))."""
+    kap2 = gz / gx
+    pre = -lam * gx * math.sqrt(gz) / (4.0 * math.pi * math.sqrt(2.0 * math.pi))
+    if abs(kap2 - 1.0) < 1e-15:
+        return 0.0
+    base = (1.0 + 2.0 * kap2) / (1.0 - kap2)
+    if kap2 > 1.0:
+        q = math.sqrt(kap2 - 1.0)
+        return pre * (base - 3.0 * kap2 * math.atan(q) / ((1.0 - kap2) * q))
+    q = math.sqrt(1.0 - kap2)
+    return pre * (base - 3.0 * kap2 / (2.0 * (1.0 - kap2) * q) * math.log((1.0 + q) / (1.0 - q)))
+
+
+def dipole_energy_cylindrical(n, gx: float, gz: float, lam: float, scale: float = 1.0) -> float:
+    """Energy of scale * ex7_rho for a dipole axis n: E(z-axis) * P2(n_z).
+
+    For a density symmetric about the z axis, int |rho_hat|^2 (n.k)^2/|k|^2 dk is A n_z^2 +
+    B (1 - n_z^2) with A + 2B the total, so the dipole energy is proportional to 3 n_z^2 - 1.
+    """
+    n = np.asarray(n, dtype=np.float64)
+    nz = n[2] / np.linalg.norm(n)
+    return scale ** 2 * ex7_energy(gx, gz, lam) * 0.5 * (3.0 * nz * nz - 1.0)

@@ -1,0 +1,105 @@
+"""Plant plausible mistakes in the oracle (CPU only) and check that a pin catches each one.
+
+Each mutation patches one oracle function for the duration of a test; the pin it should trip
+is re-run and must fail.  This shows the pins are sharp enough to see a dropped term, a wrong
+sign, a transposed operand or a wrong index.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import closed_forms as cf
+from oracle import direct, pipeline, quadrature
+
+ORIG_NW = quadrature.nodes_weights
+ORIG_UHAT = quadrature.u_hat
+ORIG_T2 = pipeline.type2
+
+
+def _interior_err(kernel, axis, rho_fn, u_fn, method="nufft", n=20):
+    L = 10.0
+    z, y, x = synth.grid_coords(3, n, L)
+    o = pipeline.oracle_eval(rho_fn(x, y, z), L, (n, n, 2 * n), kernel, axis=axis,
+                             method=method)
+    ref = u_fn(x, y, z)
+    m = np.sqrt(x * x + y * y + z * z) < 3
+    return np.max(np.abs(o["u"][m] - ref[m])) / np.max(np.abs(ref[m]))
+
+
+AX = np.array([-0.36589, -0.69481, 0.61916])
+MIX_C = np.array([[1.5, -0.5, 0.3], [-1.0, 1.0, -0.8]])
+MIX_S = np.array([1.0, 1.2])
+MIX_W = np.array([1.0, 0.6])
+
+
+def ex4_err():
+    return _interior_err("coulomb", None, cf.ex4_rho, cf.ex4_u)
+
+
+def ex5_err():
+    a = (1.3, 1.5, 1.8)
+    return _interior_err("dipole", AX, lambda x, y, z: cf.ex4_rho(x, y, z, a),
+                         lambda x, y, z: cf.ex5_u(x, y, z, AX, a))
+
+
+def mix_err(method="nufft", n=20):
+    # an off-centre mixture: not even under x -> -x, so a conjugated transform shows
+    return _interior_err(
+        "coulomb", None,
+        lambda x, y, z: sum(w * np.exp(-((x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2) / s ** 2)
+                            for c, s, w in zip(MIX_C, MIX_S, MIX_W)),
+        lambda x, y, z: cf.coulomb3d_mixture(x, y, z, MIX_C, MIX_S, MIX_W), method, n)
+
+
+def test_unmutated_baseline_passes():
+    assert ex4_err() < 1e-4 and ex5_err() < 1e-4 and mix_err() < 1e-4
+
+
+def _drop_sin(d, n, L, nodes, kernel="coulomb", axis=None, axis2=None, alpha=0.0, P=None):
+    k, W = ORIG_NW(d, n, L, nodes, kernel, axis, axis2, alpha, P)
+    if d == 3:
+        st = np.sqrt(k[:, 0] ** 2 + k[:, 1] ** 2) / np.linalg.norm(k, axis=1)
+        W = W / st
+    return k, W
+
+
+def _flip_dipole(k, d, kernel, axis=None, axis2=None, alpha=0.0):
+    v = ORIG_UHAT(k, d, kernel, axis, axis2, alpha)
+    return -v if kernel == "dipole" else v
+
+
+def _transpose_nodes(d, n, L, nodes, kernel="coulomb", axis=None, axis2=None, alpha=0.0, P=None):
+    k, W = ORIG_NW(d, n, L, nodes, kernel, axis, axis2, alpha, P)
+    return k[:, ::-1].copy(), W
+
+
+def _conj_type2(rho, L, k, method="nufft", setting="parity"):
+    return np.conj(ORIG_T2(rho, L, k, method, setting))
+
+
+@pytest.mark.parametrize("mutation", ["drop_sin", "flip_dipole", "transpose", "conj_type2",
+                                      "grid_offset"])
+def test_pins_catch_mutation(monkeypatch, mutation):
+    if mutation == "drop_sin":
+        monkeypatch.setattr(quadrature, "nodes_weights", _drop_sin)
+        err = ex4_err()
+    elif mutation == "flip_dipole":
+        monkeypatch.setattr(quadrature, "u_hat", _flip_dipole)
+        err = ex5_err()
+    elif mutation == "transpose":
+        monkeypatch.setattr(quadrature, "nodes_weights", _transpose_nodes)
+        err = max(ex4_err(), ex5_err())
+    elif mutation == "conj_type2":
+        monkeypatch.setattr(pipeline, "type2", _conj_type2)
+        err = mix_err()
+    else:
+        # type-2 sampled on a grid offset by one cell (x_i = -L/2 + (i+1) h) while type-1
+        # uses the right one
+        def offset_type2(rho, L, k, method="nufft", setting="parity"):
+            h = L / rho.shape[0]
+            return ORIG_T2(rho, L, k, method, setting) * np.exp(-1j * (k @ np.full(k.shape[1], h)))
+        monkeypatch.setattr(pipeline, "type2", offset_type2)
+        err = mix_err()
+    assert err > 5e-2, f"{mutation} not detected (err={err:.2e})"
