@@ -1,0 +1,141 @@
+/*
+ * nlint — free-space Coulomb / dipole-dipole convolution on a uniform grid by the
+ * phase-space quadrature + NUFFT method of Jiang, Greengard & Bao (arXiv 1311.4120,
+ * Algorithm 1, Section 3.2), on one NVIDIA GB300 (sm_103a).
+ *
+ * What the library computes (eq. gpe, eq. gpe2, eq. 3.2, eq. 3.7, Remark 3.3):
+ *   grid      x_i = -L/2 + i h, h = L/n, i = 0..n-1 on every axis (d = 2 or 3),
+ *             arrays in C order, last index fastest: (i_z, i_y, i_x) or (i_y, i_x);
+ *   nodes     k_j = r (sin t cos p, sin t sin p, cos t) in 3D, r (cos p, sin p) in 2D, with
+ *             r Gauss-Legendre on [0, P], t Gauss-Legendre on [0, pi], p = 2 pi l / N_phi;
+ *   weights   W_j = (2 pi)^{-d} w_r w_t sin(t) w_p |k_j|^{d-1} U_hat(k_j)     (eq. 3.7)
+ *             U_hat = 1/|k|^2 (3D Coulomb), -1 + 3 (n.k)^2/|k|^2 (3D dipole),
+ *             1/|k| (2.5D Coulomb)                                        (eq. int3dd)
+ *   type 2    rho_hat_j = h^d sum_i rho_i exp(-i k_j . x_i)                  (eq. 3.2)
+ *   type 1    u_i = Re sum_j W_j rho_hat_j exp(+i k_j . x_i)                 (eq. 3.7)
+ *   energy    E = (lambda / 2) h^d sum_i u_i rho_i                    (Remark 3.3)
+ * Both sums are evaluated by NUFFTs (Section 2) to the plan's tolerance.
+ *
+ * Canonical node order (used by nlint_type2 / nlint_type1): j = (a N_theta + b) N_phi + c
+ * in 3D and j = a N_phi + c in 2D (a radial, b polar, c azimuthal index).
+ *
+ * Conventions for every entry point:
+ *   - Device pointers are CUDA device (or managed) addresses on the plan's device, owned by
+ *     the caller, in the plan's precision (float or double; complex values interleaved).
+ *     They must stay valid until the work queued on `stream` has finished.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Work
+ *     is queued on it; nothing synchronises the host unless a host output is requested.
+ *   - Return value: NLINT_OK or a negative status; nlint_last_error() then returns a
+ *     message for the calling thread.  No C++ exception crosses this interface.
+ *   - A plan is not re-entrant: one evaluation at a time per plan (its workspaces are
+ *     reused).  Different plans may run concurrently on different streams.
+ */
+#ifndef NLINT_H
+#define NLINT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct nlint_plan_s *nlint_plan;
+typedef struct nlint_batch_s *nlint_batch;
+
+enum { NLINT_COULOMB = 0, NLINT_DIPOLE = 1 };
+enum { NLINT_FP32 = 0, NLINT_FP64 = 1 };
+enum {
+    NLINT_OK = 0,
+    NLINT_EINVAL = -1,       /* bad argument (message says which)                  */
+    NLINT_ENOMEM = -2,       /* device or host allocation failed                    */
+    NLINT_ECUDA = -3,        /* a CUDA call failed (message carries CUDA's string)  */
+    NLINT_ETIMEOUT = -4,     /* a bounded device-side wait gave up                  */
+    NLINT_EUNSUPPORTED = -5  /* valid request outside what this build implements    */
+};
+
+/* Full set of plan parameters.  nlint_params_default() fills every field; zero in an
+ * optional field means "choose from the other fields". */
+typedef struct nlint_params {
+    int d;               /* 2 or 3                                                      */
+    int64_t n;           /* grid points per axis, even, >= 8                            */
+    double L;            /* box side; the box is [-L/2, L/2)^d                          */
+    int kernel;          /* NLINT_COULOMB or NLINT_DIPOLE (3D only)                     */
+    double axis[3];      /* dipole axis n (normalised internally); ignored for Coulomb  */
+    int64_t n_r, n_theta, n_phi; /* node counts; 0 = default for n (n_theta ignored in 2D) */
+    double P;            /* radial cutoff; 0 = pi / h (the Nyquist radius of the grid)   */
+    double eps;          /* NUFFT tolerance; picks the precision and spreading width     */
+    int precision;       /* -1 = from eps (eps >= 1e-7 -> FP32), else NLINT_FP32/FP64     */
+    int w;               /* spreading width in fine cells; 0 = from eps                  */
+    double sigma;        /* oversampling factor of the fine grid; 0 = 2                  */
+    int device;          /* CUDA device ordinal; -1 = current device                     */
+} nlint_params;
+
+/* Read-only description of a plan. */
+typedef struct nlint_info {
+    int d, precision, w, kernel;
+    int64_t n, n_fine, n_nodes, n_half_nodes;
+    int64_t n_r, n_theta, n_phi;
+    double L, h, P, sigma, beta;
+    size_t workspace_bytes; /* device bytes owned by the plan */
+} nlint_info;
+
+/* Fill *p with defaults (d = 3, Coulomb, eps = 1e-6, everything else automatic). */
+void nlint_params_default(nlint_params *p);
+
+/* Build a plan: nodes and weights in FP64 on the host, sorted into fine-grid tiles, uploaded
+ * once; device workspaces allocated.  Algorithm 1 steps 1-3 (Section 3.2).
+ * dipole_axis: 3 doubles for NLINT_DIPOLE (must be non-zero), NULL for Coulomb.
+ * Errors: NLINT_EINVAL (d not 2/3, n odd or < 8, L <= 0, bad axis, 2D dipole),
+ *         NLINT_ENOMEM, NLINT_ECUDA. */
+int nlint_plan_create(int d, int64_t n, double L, int kernel, const double *dipole_axis,
+                      double eps, nlint_plan *out);
+int nlint_plan_create_ex(const nlint_params *p, nlint_plan *out);
+int nlint_plan_info(nlint_plan plan, nlint_info *info);
+void nlint_plan_destroy(nlint_plan plan); /* NULL is a no-op; waits for the plan's work */
+
+/* u = U * rho on the grid (Algorithm 1 steps 4-5: type-2 NUFFT, multiply by W_j, type-1
+ * NUFFT).  rho_dev, u_dev: n^d reals in the plan precision; they may not alias. */
+int nlint_eval(nlint_plan plan, const void *rho_dev, void *u_dev, void *stream);
+
+/* nlint_eval followed by the energy (lambda/2) h^d sum u rho, written as one double to
+ * E_dev (device).  The sum is taken in FP64 with compensated (Neumaier) partial sums in a
+ * fixed order, so repeated calls give identical results. */
+int nlint_eval_energy(nlint_plan plan, const void *rho_dev, void *u_dev, double lambda,
+                      double *E_dev, void *stream);
+
+/* E = (lambda/2) h^d sum u rho for caller-supplied rho and u (Remark 3.3).  E_dev (device
+ * double) and/or E_host may be NULL; a non-NULL E_host synchronises `stream`. */
+int nlint_energy(nlint_plan plan, const void *rho_dev, const void *u_dev, double lambda,
+                 double *E_dev, double *E_host, void *stream);
+
+/* End-to-end form with HOST buffers: copies rho_host to the device, evaluates u and E,
+ * copies u back to u_host and E to *E_host (E_host may be NULL), and synchronises
+ * `stream`.  Pinned host memory gives the fastest copies. */
+int nlint_eval_host(nlint_plan plan, const void *rho_host, void *u_host, double lambda,
+                    double *E_host, void *stream);
+
+/* Stage entry points.  nlint_type2: rho (n^d reals) -> rho_hat_dev (n_nodes complex, the
+ * canonical node order, eq. 3.2).  nlint_type1: c_dev (n_nodes complex, canonical order)
+ * -> u_dev = Re sum_j c_j exp(+i k_j . x) (eq. 3.7 with c_j in place of W_j rho_hat_j). */
+int nlint_type2(nlint_plan plan, const void *rho_dev, void *rho_hat_dev, void *stream);
+int nlint_type1(nlint_plan plan, const void *c_dev, void *u_dev, void *stream);
+
+/* Node data in canonical order, FP64, for inspection: k_host (n_nodes x d, (k_x,k_y[,k_z]))
+ * and W_host (n_nodes); either may be NULL. */
+int nlint_plan_nodes(nlint_plan plan, double *k_host, double *W_host);
+
+/* Per-stage timing: when enabled, each evaluation records CUDA events between its stages
+ * on the evaluation stream; nlint_stage_times returns the milliseconds of the last
+ * evaluation (synchronising on its final event) and the stage names. */
+int nlint_set_stage_timing(nlint_plan plan, int enable);
+int nlint_stage_times(nlint_plan plan, float *ms, const char **names, int max_stages,
+                      int *n_stages);
+
+/* Thread-local message for the last failed call on this thread ("" if none). */
+const char *nlint_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NLINT_H */

@@ -8,6 +8,8 @@ TEST INFRASTRUCTURE ONLY.  Parameter settings:
   * "fine"    sigma = 2, w = 24, tau = (w pi / sigma) / (2 N^2 sqrt(sigma (sigma - 1))), which
                 balances aliasing against truncation (about 1e-11 in 3D, limited by rounding
                 amplified by exp(3 N^2 tau / 4) at the corner modes);
+  * "fp32ref" sigma = 2, w = 16, tau balanced as for "fine" (about 2e-8): a reference for
+                FP32 results at a third of the cost of "fine";
   * "paper12" the paper's 12-digit setting: Mr = 2N, tau = 12 / N^2, 24 points;
   * "paper6"  the paper's 6-digit setting:  Mr = 2N, tau = 6 / N^2, 12 points.
 The balanced tau is this project's reading (the paper states only the two settings above);
@@ -63,8 +65,8 @@ def params(N: int, setting: str = "parity"):
     """(Mr, w, tau) for a grid of N modes per axis."""
     if setting == "parity":
         return 3 * N, 28, 5.5 / N ** 2
-    if setting == "fine":
-        sigma, w = 2, 24
+    if setting in ("fine", "fp32ref"):
+        sigma, w = 2, (24 if setting == "fine" else 16)
         tau = (w * np.pi / sigma) / (2.0 * N ** 2 * np.sqrt(sigma * (sigma - 1.0)))
         return sigma * N, w, tau
     if setting == "paper12":

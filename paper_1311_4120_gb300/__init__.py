@@ -1,0 +1,264 @@
+"""GB300-native free-space Coulomb / dipole convolution (Jiang, Greengard & Bao, Algorithm 1).
+
+Thin Python binding over the C-ABI in ``include/nlint.h`` (``libnlint.so``).  The binding only
+marshals arguments: every step of the computation runs in the library's CUDA kernels.  PyTorch
+is used for device memory and streams.  There is no CPU fallback: if the library is missing or
+fails to load, importing the binding raises.
+
+    plan = Plan(d=3, n=256, L=32.0, kernel="coulomb", eps=1e-6)   # FP32 path
+    u, E = plan.eval_energy(rho, lam=1.0)                           # rho: CUDA tensor (n,n,n)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libnlint.so")
+
+NLINT_COULOMB, NLINT_DIPOLE = 0, 1
+NLINT_FP32, NLINT_FP64 = 0, 1
+STATUS = {0: "NLINT_OK", -1: "NLINT_EINVAL", -2: "NLINT_ENOMEM", -3: "NLINT_ECUDA",
+          -4: "NLINT_ETIMEOUT", -5: "NLINT_EUNSUPPORTED"}
+
+EXPORTED = [
+    "nlint_params_default", "nlint_plan_create", "nlint_plan_create_ex", "nlint_plan_info",
+    "nlint_plan_destroy", "nlint_eval", "nlint_eval_energy", "nlint_energy", "nlint_eval_host",
+    "nlint_type2", "nlint_type1", "nlint_plan_nodes", "nlint_set_stage_timing",
+    "nlint_stage_times", "nlint_last_error",
+]
+
+
+class NlintError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class nlint_params(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("n", ctypes.c_int64), ("L", ctypes.c_double),
+                ("kernel", ctypes.c_int), ("axis", ctypes.c_double * 3),
+                ("n_r", ctypes.c_int64), ("n_theta", ctypes.c_int64), ("n_phi", ctypes.c_int64),
+                ("P", ctypes.c_double), ("eps", ctypes.c_double), ("precision", ctypes.c_int),
+                ("w", ctypes.c_int), ("sigma", ctypes.c_double), ("device", ctypes.c_int)]
+
+
+class nlint_info(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("precision", ctypes.c_int), ("w", ctypes.c_int),
+                ("kernel", ctypes.c_int), ("n", ctypes.c_int64), ("n_fine", ctypes.c_int64),
+                ("n_nodes", ctypes.c_int64), ("n_half_nodes", ctypes.c_int64),
+                ("n_r", ctypes.c_int64), ("n_theta", ctypes.c_int64), ("n_phi", ctypes.c_int64),
+                ("L", ctypes.c_double), ("h", ctypes.c_double), ("P", ctypes.c_double),
+                ("sigma", ctypes.c_double), ("beta", ctypes.c_double),
+                ("workspace_bytes", ctypes.c_size_t)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libnlint.so (raises if it is missing: there is no fallback path)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libnlint.so not found at {path}; run __graft_entry__.build() "
+                          "or python paper_1311_4120_gb300/build.py")
+    lib = ctypes.CDLL(path)
+    vp, i64, dbl, ci = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+    pplan = ctypes.POINTER(vp)
+    lib.nlint_params_default.argtypes = [ctypes.POINTER(nlint_params)]
+    lib.nlint_params_default.restype = None
+    lib.nlint_plan_create.argtypes = [ci, i64, dbl, ci, ctypes.POINTER(dbl), dbl, pplan]
+    lib.nlint_plan_create_ex.argtypes = [ctypes.POINTER(nlint_params), pplan]
+    lib.nlint_plan_info.argtypes = [vp, ctypes.POINTER(nlint_info)]
+    lib.nlint_plan_destroy.argtypes = [vp]
+    lib.nlint_plan_destroy.restype = None
+    lib.nlint_eval.argtypes = [vp, vp, vp, vp]
+    lib.nlint_eval_energy.argtypes = [vp, vp, vp, dbl, vp, vp]
+    lib.nlint_energy.argtypes = [vp, vp, vp, dbl, vp, ctypes.POINTER(dbl), vp]
+    lib.nlint_eval_host.argtypes = [vp, vp, vp, dbl, ctypes.POINTER(dbl), vp]
+    lib.nlint_type2.argtypes = [vp, vp, vp, vp]
+    lib.nlint_type1.argtypes = [vp, vp, vp, vp]
+    lib.nlint_plan_nodes.argtypes = [vp, vp, vp]
+    lib.nlint_set_stage_timing.argtypes = [vp, ci]
+    lib.nlint_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float),
+                                      ctypes.POINTER(ctypes.c_char_p), ci, ctypes.POINTER(ci)]
+    lib.nlint_last_error.argtypes = []
+    lib.nlint_last_error.restype = ctypes.c_char_p
+    for name in EXPORTED:
+        if name not in ("nlint_params_default", "nlint_plan_destroy", "nlint_last_error"):
+            getattr(lib, name).restype = ci
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        msg = load_library().nlint_last_error().decode(errors="replace")
+        raise NlintError(rc, msg)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream) -> int:
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+class Plan:
+    """A plan for u = U * rho and E = (lambda/2) <u, rho> on an n^d grid over [-L/2, L/2)^d.
+
+    kernel: "coulomb" (3D: 1/(4 pi |x|); 2D: 1/(2 pi |x|)) or "dipole" (3D, needs ``axis``).
+    eps picks the precision (>= 1e-7: FP32, else FP64) and the spreading width unless given.
+    nodes: (n_r, n_theta, n_phi) in 3D or (n_r, n_phi) in 2D; default from n.
+    """
+
+    def __init__(self, d: int, n: int, L: float, kernel: str = "coulomb",
+                 axis: Optional[Sequence[float]] = None, eps: float = 1e-6,
+                 precision: Optional[str] = None, nodes: Optional[Sequence[int]] = None,
+                 w: int = 0, sigma: float = 0.0, P: float = 0.0, device: Optional[int] = None):
+        lib = load_library()
+        prm = nlint_params()
+        lib.nlint_params_default(ctypes.byref(prm))
+        prm.d, prm.n, prm.L = int(d), int(n), float(L)
+        prm.kernel = {"coulomb": NLINT_COULOMB, "dipole": NLINT_DIPOLE}[kernel]
+        if axis is not None:
+            for a in range(3):
+                prm.axis[a] = float(axis[a])
+        if nodes is not None:
+            if d == 3:
+                prm.n_r, prm.n_theta, prm.n_phi = (int(v) for v in nodes)
+            else:
+                prm.n_r, prm.n_phi = (int(v) for v in nodes)
+        prm.eps = float(eps)
+        prm.precision = {None: -1, "fp32": NLINT_FP32, "fp64": NLINT_FP64}[precision]
+        prm.w, prm.sigma, prm.P = int(w), float(sigma), float(P)
+        if device is None:
+            torch = _torch()
+            device = torch.cuda.current_device() if torch.cuda.is_available() else -1
+        prm.device = int(device)
+        h = ctypes.c_void_p()
+        _check(lib.nlint_plan_create_ex(ctypes.byref(prm), ctypes.byref(h)))
+        self._h = h
+        self._lib = lib
+        info = nlint_info()
+        _check(lib.nlint_plan_info(h, ctypes.byref(info)))
+        self.info = {f: getattr(info, f) for f, _ in nlint_info._fields_}
+        self.d, self.n, self.L = d, n, L
+        self.device = int(device)
+        self.precision = "fp32" if info.precision == NLINT_FP32 else "fp64"
+
+    # ------------------------------------------------------------------ helpers
+    @property
+    def dtype(self):
+        torch = _torch()
+        return torch.float32 if self.precision == "fp32" else torch.float64
+
+    @property
+    def cdtype(self):
+        torch = _torch()
+        return torch.complex64 if self.precision == "fp32" else torch.complex128
+
+    def _dev(self, t, shape, dtype, name):
+        torch = _torch()
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError(f"{name} must be a CUDA tensor")
+        if t.dtype != dtype or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous {dtype} tensor of shape {tuple(shape)}")
+        if t.device.index != self.device:
+            raise ValueError(f"{name} is on cuda:{t.device.index}, the plan on cuda:{self.device}")
+        return t.data_ptr()
+
+    @property
+    def grid_shape(self):
+        return (self.n,) * self.d
+
+    # ------------------------------------------------------------------ entry points
+    def eval(self, rho, out=None, stream=None):
+        torch = _torch()
+        u = out if out is not None else torch.empty(self.grid_shape, dtype=self.dtype, device=rho.device)
+        _check(self._lib.nlint_eval(self._h, self._dev(rho, self.grid_shape, self.dtype, "rho"),
+                                    self._dev(u, self.grid_shape, self.dtype, "u"), _stream_ptr(stream)))
+        return u
+
+    def eval_energy(self, rho, lam: float = 1.0, out=None, E_out=None, stream=None):
+        torch = _torch()
+        u = out if out is not None else torch.empty(self.grid_shape, dtype=self.dtype, device=rho.device)
+        E = E_out if E_out is not None else torch.empty((), dtype=torch.float64, device=rho.device)
+        _check(self._lib.nlint_eval_energy(self._h, self._dev(rho, self.grid_shape, self.dtype, "rho"),
+                                           self._dev(u, self.grid_shape, self.dtype, "u"), float(lam),
+                                           E.data_ptr(), _stream_ptr(stream)))
+        return u, E
+
+    def energy(self, rho, u, lam: float = 1.0, stream=None) -> float:
+        Eh = ctypes.c_double()
+        _check(self._lib.nlint_energy(self._h, self._dev(rho, self.grid_shape, self.dtype, "rho"),
+                                      self._dev(u, self.grid_shape, self.dtype, "u"), float(lam),
+                                      None, ctypes.byref(Eh), _stream_ptr(stream)))
+        return Eh.value
+
+    def eval_host(self, rho_host, lam: float = 1.0, u_host=None, stream=None):
+        """End-to-end call with host buffers (numpy arrays or CPU tensors, pinned is best)."""
+        torch = _torch()
+        if isinstance(rho_host, np.ndarray):
+            rho_host = torch.from_numpy(np.ascontiguousarray(rho_host))
+        if rho_host.is_cuda or rho_host.dtype != self.dtype or tuple(rho_host.shape) != self.grid_shape:
+            raise ValueError("rho_host must be a CPU array of the plan's dtype and grid shape")
+        u = u_host if u_host is not None else torch.empty(self.grid_shape, dtype=self.dtype)
+        Eh = ctypes.c_double()
+        _check(self._lib.nlint_eval_host(self._h, rho_host.data_ptr(), u.data_ptr(), float(lam),
+                                         ctypes.byref(Eh), _stream_ptr(stream)))
+        return u, Eh.value
+
+    def type2(self, rho, out=None, stream=None):
+        torch = _torch()
+        M = self.info["n_nodes"]
+        r = out if out is not None else torch.empty((M,), dtype=self.cdtype, device=rho.device)
+        _check(self._lib.nlint_type2(self._h, self._dev(rho, self.grid_shape, self.dtype, "rho"),
+                                     self._dev(r, (M,), self.cdtype, "rho_hat"), _stream_ptr(stream)))
+        return r
+
+    def type1(self, c, out=None, stream=None):
+        torch = _torch()
+        M = self.info["n_nodes"]
+        u = out if out is not None else torch.empty(self.grid_shape, dtype=self.dtype, device=c.device)
+        _check(self._lib.nlint_type1(self._h, self._dev(c, (M,), self.cdtype, "c"),
+                                     self._dev(u, self.grid_shape, self.dtype, "u"), _stream_ptr(stream)))
+        return u
+
+    def nodes(self):
+        M = self.info["n_nodes"]
+        k = np.empty((M, self.d), dtype=np.float64)
+        W = np.empty(M, dtype=np.float64)
+        _check(self._lib.nlint_plan_nodes(self._h, k.ctypes.data, W.ctypes.data))
+        return k, W
+
+    def set_stage_timing(self, enable: bool = True):
+        _check(self._lib.nlint_set_stage_timing(self._h, 1 if enable else 0))
+
+    def stage_times(self):
+        ms = (ctypes.c_float * 32)()
+        names = (ctypes.c_char_p * 32)()
+        k = ctypes.c_int()
+        _check(self._lib.nlint_stage_times(self._h, ms, names, 32, ctypes.byref(k)))
+        return [(names[i].decode(), ms[i]) for i in range(k.value)]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.nlint_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

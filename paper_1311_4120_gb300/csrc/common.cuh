@@ -1,0 +1,48 @@
+// Shared device helpers: complex arithmetic on float2/double2 and precision traits.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace nlint {
+
+template <typename T> struct Cx;
+template <> struct Cx<float> { using T2 = float2; };
+template <> struct Cx<double> { using T2 = double2; };
+template <typename T> using cx_t = typename Cx<T>::T2;
+
+template <typename T2> __device__ __forceinline__ T2 cmake(decltype(T2{}.x) a, decltype(T2{}.x) b) {
+    T2 r; r.x = a; r.y = b; return r;
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+// multiply by sign*i: (x + iy) * (s i) = -s y + i s x
+__device__ __forceinline__ float2 cmuli(float2 a, int s) { return make_float2(-s * a.y, s * a.x); }
+__device__ __forceinline__ double2 cmuli(double2 a, int s) { return make_double2(-s * a.y, s * a.x); }
+template <typename T2> __device__ __forceinline__ T2 czero() { T2 r; r.x = 0; r.y = 0; return r; }
+
+// Neumaier-compensated FP64 accumulator: s + c carries the sum.
+struct KSum {
+    double s, c;
+    __device__ __forceinline__ void init() { s = 0.0; c = 0.0; }
+    __device__ __forceinline__ void add(double x) {
+        double t = s + x;
+        if (fabs(s) >= fabs(x)) c += (s - t) + x;
+        else c += (x - t) + s;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return s + c; }
+};
+
+}  // namespace nlint

@@ -1,0 +1,97 @@
+// Internal declarations shared by the host plan code and the kernel launchers.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "nlint.h"
+
+namespace nlint {
+
+// ---------------------------------------------------------------------------- FFT passes
+// One pass transforms every line along one axis of a 2D/3D array.  A "column" pass works
+// on an axis that is not contiguous (the batch index is contiguous); a "row" pass works on
+// the contiguous axis.
+enum InKind {
+    IN_REAL_MODES = 0,   // N reals at centred mode positions, times the deconvolution product
+    IN_CPLX_MODES = 1,   // N complex at centred mode positions
+    IN_CPLX_FULL = 2,    // n complex
+    IN_CPLX_HERM = 3,    // n/2+1 complex of a Hermitian line (rest by conjugate symmetry)
+    IN_CPLX_FOLD = 4     // row pass only: n complex plus the conjugated mirror row (fold)
+};
+enum OutKind {
+    OUT_CPLX_FULL = 0,   // n complex
+    OUT_CPLX_HALF = 1,   // first n/2+1 complex
+    OUT_CPLX_MODES = 2,  // N complex at centred mode positions
+    OUT_REAL_MODES = 3   // N reals (real part) times the deconvolution product, + energy
+};
+
+struct PassDesc {
+    int n;               // FFT length
+    int nrad;
+    int rad[12];         // radix sequence (8, 4, 2, 3)
+    int sign;            // -1 forward, +1 backward
+    int N;               // number of modes per axis
+    int in_kind, out_kind;
+    int dim;             // d, for the deconvolution product over the batch index
+    int64_t I;           // batch length along the contiguous index (column pass) / rows (row pass)
+    int64_t n_outer;     // outer count (column pass)
+    int64_t in_so, in_sa;    // element strides: outer, axis (column pass); row stride (row pass)
+    int64_t out_so, out_sa;
+    int B, TPC, LD;      // columns (or rows) per CTA, threads per column, smem leading dim
+    // fold (row pass over the extended spread grid): see the row-pass kernel
+    int fold_pad;        // pad planes below/above the stored half of the slowest axis
+    int64_t fold_plane;  // elements per plane of the slowest axis (rows per plane * n)
+    int64_t fold_rows_per_plane;
+    const void *fac;     // deconvolution factors, length N (plan precision)
+    const void *rho;     // energy: density (OUT_REAL_MODES)
+    double2 *partials;   // energy: one compensated partial per CTA (OUT_REAL_MODES)
+};
+
+void make_radix(int n, PassDesc &p);
+int64_t pass_blocks(const PassDesc &p, bool row);
+size_t pass_smem(const PassDesc &p, int prec);
+void config_pass(PassDesc &p, int prec, bool row);
+bool pass_fits(const PassDesc &p);
+
+template <typename T>
+cudaError_t launch_colpass(const PassDesc &p, const void *in, void *out, const void *tw,
+                           cudaStream_t s);
+template <typename T>
+cudaError_t launch_rowpass(const PassDesc &p, const void *in, void *out, const void *tw,
+                           cudaStream_t s);
+
+// ---------------------------------------------------------------------------- NUFFT kernels
+struct NodeDesc {
+    int d;
+    int64_t M;           // number of nodes (half set)
+    int n;               // fine grid size per axis
+    int w;               // stencil width
+    int pad;             // extended planes below/above the half grid (slowest axis)
+    double beta;         // ES kernel shape parameter
+    const int32_t *l0;   // d x M, first stencil cell per axis (array-axis order)
+    const void *frac;    // d x M, g - l0 per axis (plan precision)
+    const void *W;       // M, h^d W_j (plan precision), may be NULL (type-2 only)
+};
+
+template <typename T>
+cudaError_t launch_interp(const NodeDesc &nd, const void *G, void *c_out, int apply_W,
+                          cudaStream_t s);
+template <typename T>
+cudaError_t launch_spread(const NodeDesc &nd, const void *c_in, void *Hext, cudaStream_t s);
+template <typename T>
+cudaError_t launch_scatter_canonical(int64_t M, const void *vals, const int32_t *perm,
+                                     const int32_t *mirror, double scale, void *out,
+                                     cudaStream_t s);
+template <typename T>
+cudaError_t launch_gather_canonical(int64_t M, const void *c_canon, const int32_t *perm,
+                                    const int32_t *mirror, void *c_half, cudaStream_t s);
+template <typename T>
+cudaError_t launch_energy_partials(int64_t count, const void *u, const void *rho,
+                                   double2 *partials, int nblocks, cudaStream_t s);
+cudaError_t launch_energy_final(const double2 *partials, int nparts, double scale, double *E,
+                                cudaStream_t s);
+
+}  // namespace nlint

@@ -1,0 +1,751 @@
+// Plan builder and C-ABI entry points.
+//
+// The plan follows Algorithm 1 (Section 3.2): steps 1-3 (grid, nodes and weights of
+// eq. 3.7) run once on the host in FP64; steps 4-5 (type-2 NUFFT, multiply, type-1 NUFFT)
+// and the energy of Remark 3.3 run on the device for every evaluation.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace nlint {
+
+static thread_local std::string g_err;
+
+static int fail(int code, const std::string &msg) {
+    g_err = msg;
+    return code;
+}
+static int cuda_fail(cudaError_t e, const char *where) {
+    g_err = std::string(where) + ": " + cudaGetErrorString(e);
+    return NLINT_ECUDA;
+}
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
+    } while (0)
+
+// ------------------------------------------------------------------ Gauss-Legendre (FP64)
+// m-point rule on [-1, 1]: Newton's method on P_m, with P_m and P_m' from the three-term
+// recurrence (j+1) P_{j+1} = (2j+1) x P_j - j P_{j-1}.
+static void gauss_legendre(int m, std::vector<double> &x, std::vector<double> &w) {
+    x.assign(m, 0.0);
+    w.assign(m, 0.0);
+    for (int i = 0; i < (m + 1) / 2; i++) {
+        double z = std::cos(M_PI * (i + 0.75) / (m + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; it++) {
+            double p0 = 1.0, p1 = z;
+            for (int j = 1; j < m; j++) {
+                double p2 = ((2.0 * j + 1.0) * z * p1 - j * p0) / (j + 1.0);
+                p0 = p1;
+                p1 = p2;
+            }
+            if (m == 1) { p1 = z; p0 = 1.0; }
+            dp = m * (z * p1 - p0) / (z * z - 1.0);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        double p0 = 1.0, p1 = z;
+        for (int j = 1; j < m; j++) {
+            double p2 = ((2.0 * j + 1.0) * z * p1 - j * p0) / (j + 1.0);
+            p0 = p1;
+            p1 = p2;
+        }
+        dp = m * (z * p1 - p0) / (z * z - 1.0);
+        x[i] = -z;
+        x[m - 1 - i] = z;
+        w[i] = w[m - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+static bool smooth_size(int64_t n) {
+    if (n <= 0) return false;
+    while (n % 2 == 0) n /= 2;
+    while (n % 3 == 0) n /= 3;
+    return n == 1;
+}
+
+}  // namespace nlint
+
+// ---------------------------------------------------------------------------------- plan
+struct nlint_plan_s {
+    nlint_params prm;
+    int d, prec, w, pad, n_fine;
+    int64_t N, nr, nt, nphi, Nf, Mh;
+    double L, h, P, sigma, beta;
+    double axis[3];
+    int device;
+    // device memory
+    int32_t *d_l0 = nullptr;
+    void *d_frac = nullptr, *d_W = nullptr, *d_fac = nullptr, *d_tw = nullptr;
+    int32_t *d_perm = nullptr, *d_mirror = nullptr;
+    void *d_bufA = nullptr, *d_bufB = nullptr, *d_bufG = nullptr, *d_c = nullptr;
+    double2 *d_partials = nullptr;
+    double *d_E = nullptr;
+    void *d_rho_io = nullptr, *d_u_io = nullptr;  // nlint_eval_host staging
+    int n_partials = 0;
+    size_t bytes_A = 0, bytes_B = 0, bytes_G = 0, bytes_Hext = 0, bytes_c = 0;
+    size_t ws_bytes = 0;
+    nlint::PassDesc P1, P2, P3, Q1, Q2, Q3;
+    // host copies for inspection (canonical order)
+    std::vector<double> k_canon, W_canon;
+    // stage timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;
+    std::vector<const char *> ev_names;
+    int ev_used = 0;
+};
+
+namespace nlint {
+
+static int64_t default_nr(int d, int64_t n) {
+    if (d == 2) return std::max<int64_t>(8, n / 4);
+    double v;
+    if (n <= 32) v = (double)n;
+    else if (n <= 128) v = 32.0 + (n - 32) * (64.0 / 96.0);
+    else if (n <= 256) v = 96.0 + (n - 128) * (64.0 / 128.0);
+    else v = 160.0 + (n - 256) * 0.5;
+    int64_t r = (int64_t)std::llround(v / 8.0) * 8;
+    return std::max<int64_t>(8, r);
+}
+
+static double u_hat(const nlint_plan_s *p, const double k[3]) {
+    const double k2 = k[0] * k[0] + k[1] * k[1] + (p->d == 3 ? k[2] * k[2] : 0.0);
+    if (p->prm.kernel == NLINT_COULOMB) return p->d == 3 ? 1.0 / k2 : 1.0 / std::sqrt(k2);
+    const double kn = k[0] * p->axis[0] + k[1] * p->axis[1] + k[2] * p->axis[2];
+    return -1.0 + 3.0 * kn * kn / k2;
+}
+
+// Fourier transform of the ES kernel, Phi(xi) = int_{-1}^{1} phi(z) cos(xi z) dz, by a
+// 256-point Gauss-Legendre rule in FP64.
+static double es_ft(double xi, double beta, const std::vector<double> &qx,
+                    const std::vector<double> &qw) {
+    double s = 0.0;
+    for (size_t i = 0; i < qx.size(); i++) {
+        const double z = qx[i];
+        const double ph = std::exp(beta * (std::sqrt(std::max(0.0, 1.0 - z * z)) - 1.0));
+        s += qw[i] * ph * std::cos(xi * z);
+    }
+    return s;
+}
+
+template <typename T>
+static std::vector<T> cast_vec(const std::vector<double> &v) {
+    std::vector<T> o(v.size());
+    for (size_t i = 0; i < v.size(); i++) o[i] = (T)v[i];
+    return o;
+}
+
+template <typename T>
+static int upload(void **dst, const std::vector<double> &v, size_t &acc) {
+    std::vector<T> h = cast_vec<T>(v);
+    size_t b = h.size() * sizeof(T);
+    if (b == 0) b = sizeof(T);
+    CK(cudaMalloc(dst, b));
+    acc += b;
+    if (!h.empty()) CK(cudaMemcpy(*dst, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return NLINT_OK;
+}
+
+static void plan_free(nlint_plan_s *p) {
+    void *ptrs[] = {p->d_l0, p->d_frac, p->d_W, p->d_fac, p->d_tw, p->d_perm, p->d_mirror,
+                    p->d_bufA, p->d_bufB, p->d_bufG, p->d_c, p->d_partials, p->d_E,
+                    p->d_rho_io, p->d_u_io};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
+}
+
+static int build_plan(const nlint_params *in, nlint_plan_s *p) {
+    p->prm = *in;
+    const nlint_params &q = *in;
+    if (q.d != 2 && q.d != 3) return fail(NLINT_EINVAL, "d must be 2 or 3");
+    if (q.n < 8 || q.n % 2) return fail(NLINT_EINVAL, "n must be even and >= 8");
+    if (!(q.L > 0.0) || !std::isfinite(q.L)) return fail(NLINT_EINVAL, "L must be positive");
+    if (q.kernel != NLINT_COULOMB && q.kernel != NLINT_DIPOLE)
+        return fail(NLINT_EINVAL, "kernel must be NLINT_COULOMB or NLINT_DIPOLE");
+    if (q.kernel == NLINT_DIPOLE && q.d == 2)
+        return fail(NLINT_EUNSUPPORTED, "the 2.5D dipole kernel is not implemented");
+    p->d = q.d;
+    p->N = q.n;
+    p->L = q.L;
+    p->h = q.L / (double)q.n;
+    if (q.kernel == NLINT_DIPOLE) {
+        const double nn = std::sqrt(q.axis[0] * q.axis[0] + q.axis[1] * q.axis[1] + q.axis[2] * q.axis[2]);
+        if (!(nn > 0.0) || !std::isfinite(nn)) return fail(NLINT_EINVAL, "dipole axis must be non-zero");
+        for (int a = 0; a < 3; a++) p->axis[a] = q.axis[a] / nn;
+    } else {
+        p->axis[0] = p->axis[1] = p->axis[2] = 0.0;
+    }
+    const double pmax = M_PI / p->h;
+    p->P = (q.P > 0.0) ? q.P : pmax;
+    if (p->P > pmax * (1.0 + 1e-12))
+        return fail(NLINT_EINVAL, "P must not exceed pi/h (nodes beyond the grid's Nyquist radius)");
+    double eps = q.eps > 0.0 ? q.eps : 1e-6;
+    if (eps < 1e-15) eps = 1e-15;
+    p->prec = (q.precision == NLINT_FP32 || q.precision == NLINT_FP64) ? q.precision
+                                                                       : (eps >= 1e-7 ? NLINT_FP32 : NLINT_FP64);
+    int w = q.w > 0 ? q.w : (int)std::ceil(-std::log10(eps)) + 1;
+    if (w < 2) w = 2;
+    if (w > 16) return fail(NLINT_EINVAL, "spreading width must be <= 16");
+    p->w = w;
+    p->sigma = q.sigma > 0.0 ? q.sigma : 2.0;
+    if (p->sigma < 1.25) return fail(NLINT_EINVAL, "sigma must be >= 1.25");
+    int64_t nf = (int64_t)std::ceil(p->sigma * (double)p->N);
+    if (nf % 2) nf++;
+    while (!smooth_size(nf)) nf += 2;
+    if (nf > 4096) return fail(NLINT_EUNSUPPORTED, "fine grid larger than 4096 per axis");
+    p->n_fine = (int)nf;
+    p->pad = w / 2 + 1;
+    if (p->n_fine < 4 * p->pad + 2)
+        return fail(NLINT_EUNSUPPORTED, "grid too small for this spreading width (n_fine < 4*(w/2+1)+2)");
+    const double sig_eff = (double)p->n_fine / (double)p->N;
+    p->beta = 0.97 * M_PI * (1.0 - 1.0 / (2.0 * sig_eff)) * w;  // ES shape parameter
+
+    p->nr = q.n_r > 0 ? q.n_r : default_nr(p->d, p->N);
+    if (p->d == 3) {
+        p->nt = q.n_theta > 0 ? q.n_theta : p->nr;
+        p->nphi = q.n_phi > 0 ? q.n_phi : 2 * p->nr;
+    } else {
+        p->nt = 1;
+        p->nphi = q.n_phi > 0 ? q.n_phi : 2 * p->nr;
+    }
+    if (p->nphi % 2) return fail(NLINT_EINVAL, "n_phi must be even (the node set must be symmetric)");
+    if (p->d == 3 && p->nt % 2) return fail(NLINT_EINVAL, "n_theta must be even");
+    p->Nf = p->nr * p->nt * p->nphi;
+    p->Mh = p->Nf / 2;
+    if (p->Nf > (int64_t)2000000000) return fail(NLINT_EUNSUPPORTED, "too many nodes");
+
+    int dev = q.device;
+    if (dev < 0) CK(cudaGetDevice(&dev));
+    CK(cudaSetDevice(dev));
+    p->device = dev;
+
+    // ---------------- nodes and weights (eq. 3.7), FP64, canonical order
+    std::vector<double> xr, wr, xt, wt;
+    gauss_legendre((int)p->nr, xr, wr);
+    for (auto &v : xr) v = p->P * (1.0 + v) / 2.0;
+    for (auto &v : wr) v = p->P * v / 2.0;
+    if (p->d == 3) {
+        gauss_legendre((int)p->nt, xt, wt);
+        for (auto &v : xt) v = M_PI * (1.0 + v) / 2.0;
+        for (auto &v : wt) v = M_PI * v / 2.0;
+    }
+    const double wphi = 2.0 * M_PI / (double)p->nphi;
+    const double twopi_d = std::pow(2.0 * M_PI, p->d);
+    p->k_canon.assign((size_t)p->Nf * p->d, 0.0);
+    p->W_canon.assign((size_t)p->Nf, 0.0);
+    for (int64_t a = 0; a < p->nr; a++)
+        for (int64_t b = 0; b < p->nt; b++)
+            for (int64_t c = 0; c < p->nphi; c++) {
+                const int64_t j = (a * p->nt + b) * p->nphi + c;
+                const double r = xr[a], ph = wphi * (double)c;
+                double k[3] = {0, 0, 0}, wj;
+                if (p->d == 3) {
+                    const double st = std::sin(xt[b]), ct = std::cos(xt[b]);
+                    k[0] = r * st * std::cos(ph);
+                    k[1] = r * st * std::sin(ph);
+                    k[2] = r * ct;
+                    wj = wr[a] * wt[b] * st * wphi * r * r;
+                } else {
+                    k[0] = r * std::cos(ph);
+                    k[1] = r * std::sin(ph);
+                    wj = wr[a] * wphi * r;
+                }
+                for (int e = 0; e < p->d; e++) p->k_canon[(size_t)j * p->d + e] = k[e];
+                p->W_canon[j] = wj * u_hat(p, k) / twopi_d;
+            }
+
+    // ---------------- half node set, stencil origins, tile sort
+    const int64_t Mh = p->Mh;
+    std::vector<int64_t> half(Mh), mir(Mh);
+    {
+        int64_t o = 0;
+        for (int64_t a = 0; a < p->nr; a++)
+            for (int64_t b = 0; b < p->nt; b++)
+                for (int64_t c = 0; c < p->nphi; c++) {
+                    const bool keep = (p->d == 3) ? (b < p->nt / 2) : (c < p->nphi / 2);
+                    if (!keep) continue;
+                    const int64_t j = (a * p->nt + b) * p->nphi + c;
+                    const int64_t bm = (p->d == 3) ? (p->nt - 1 - b) : 0;
+                    const int64_t cm = (c + p->nphi / 2) % p->nphi;
+                    half[o] = j;
+                    mir[o] = (a * p->nt + bm) * p->nphi + cm;
+                    o++;
+                }
+    }
+    const int d = p->d, n = p->n_fine;
+    const double gscale = p->h * (double)n / (2.0 * M_PI);
+    std::vector<int32_t> l0((size_t)d * Mh);
+    std::vector<double> fr((size_t)d * Mh);
+    std::vector<int64_t> tile(Mh);
+    const int TS = 8;
+    const int64_t ntile = (n + TS - 1) / TS + 2;
+    for (int64_t o = 0; o < Mh; o++) {
+        const int64_t j = half[o];
+        int64_t tkey = 0;
+        for (int ax = 0; ax < d; ax++) {
+            // array axis ax pairs with node component d-1-ax (axis 0 is k_z in 3D, k_y in 2D)
+            const double g = p->k_canon[(size_t)j * d + (d - 1 - ax)] * gscale;
+            const int32_t l = (int32_t)std::ceil(g - 0.5 * w);
+            l0[(size_t)ax * Mh + o] = l;
+            fr[(size_t)ax * Mh + o] = g - (double)l;
+            if (ax == 0 && (l < -p->pad || l + w - 1 > n / 2 + p->pad))
+                return fail(NLINT_EINVAL, "internal: node stencil outside the stored half grid");
+            tkey = tkey * ntile + ((int64_t)l + n + TS) / TS;
+        }
+        tile[o] = tkey;
+    }
+    std::vector<int64_t> ord(Mh);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) { return tile[a] < tile[b]; });
+    std::vector<int32_t> l0s((size_t)d * Mh), perm(Mh), mirror(Mh);
+    std::vector<double> frs((size_t)d * Mh), Ws(Mh);
+    const double hd = std::pow(p->h, d);
+    for (int64_t o = 0; o < Mh; o++) {
+        const int64_t s = ord[o];
+        for (int ax = 0; ax < d; ax++) {
+            l0s[(size_t)ax * Mh + o] = l0[(size_t)ax * Mh + s];
+            frs[(size_t)ax * Mh + o] = fr[(size_t)ax * Mh + s];
+        }
+        perm[o] = (int32_t)half[s];
+        mirror[o] = (int32_t)mir[s];
+        Ws[o] = hd * p->W_canon[half[s]];
+    }
+
+    // ---------------- deconvolution factors f[m'] = (2 pi / n) / psi_hat(m), m = m' - N/2
+    std::vector<double> qx, qw;
+    gauss_legendre(256, qx, qw);
+    const double alpha = (double)w * M_PI / (double)n;
+    std::vector<double> fac(p->N);
+    for (int64_t a = 0; a < p->N; a++) {
+        const double m = (double)(a - p->N / 2);
+        const double psi = alpha * es_ft(m * alpha, p->beta, qx, qw);
+        fac[a] = (2.0 * M_PI / (double)n) / psi;
+    }
+    // twiddles exp(-2 pi i q / n), interleaved
+    std::vector<double> tw(2 * (size_t)n);
+    for (int qq = 0; qq < n; qq++) {
+        tw[2 * qq] = std::cos(2.0 * M_PI * qq / n);
+        tw[2 * qq + 1] = -std::sin(2.0 * M_PI * qq / n);
+    }
+
+    // ---------------- upload
+    size_t acc = 0;
+    int rc;
+    CK(cudaMalloc((void **)&p->d_l0, l0s.size() * sizeof(int32_t) + 4));
+    CK(cudaMemcpy(p->d_l0, l0s.data(), l0s.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CK(cudaMalloc((void **)&p->d_perm, perm.size() * sizeof(int32_t) + 4));
+    CK(cudaMemcpy(p->d_perm, perm.data(), perm.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CK(cudaMalloc((void **)&p->d_mirror, mirror.size() * sizeof(int32_t) + 4));
+    CK(cudaMemcpy(p->d_mirror, mirror.data(), mirror.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    acc += (l0s.size() + perm.size() + mirror.size()) * 4;
+    if (p->prec == NLINT_FP32) {
+        if ((rc = upload<float>(&p->d_frac, frs, acc))) return rc;
+        if ((rc = upload<float>(&p->d_W, Ws, acc))) return rc;
+        if ((rc = upload<float>(&p->d_fac, fac, acc))) return rc;
+        if ((rc = upload<float>(&p->d_tw, tw, acc))) return rc;
+    } else {
+        if ((rc = upload<double>(&p->d_frac, frs, acc))) return rc;
+        if ((rc = upload<double>(&p->d_W, Ws, acc))) return rc;
+        if ((rc = upload<double>(&p->d_fac, fac, acc))) return rc;
+        if ((rc = upload<double>(&p->d_tw, tw, acc))) return rc;
+    }
+
+    // ---------------- pass descriptors and workspaces
+    const int64_t N = p->N, nh = n / 2 + 1;
+    const size_t cs = p->prec == NLINT_FP32 ? 8 : 16;
+    auto base = [&](PassDesc &pd, int sign) {
+        std::memset(&pd, 0, sizeof(pd));
+        pd.n = n;
+        make_radix(n, pd);
+        pd.sign = sign;
+        pd.N = (int)N;
+        pd.dim = d;
+        pd.fac = p->d_fac;
+    };
+    if (d == 3) {
+        base(p->P1, -1);
+        p->P1.in_kind = IN_REAL_MODES; p->P1.out_kind = OUT_CPLX_HALF;
+        p->P1.I = N * N; p->P1.n_outer = 1; p->P1.in_sa = N * N; p->P1.out_sa = N * N;
+        base(p->P2, -1);
+        p->P2.in_kind = IN_CPLX_MODES; p->P2.out_kind = OUT_CPLX_FULL;
+        p->P2.I = N; p->P2.n_outer = nh; p->P2.in_so = N * N; p->P2.in_sa = N;
+        p->P2.out_so = (int64_t)n * N; p->P2.out_sa = N;
+        base(p->P3, -1);
+        p->P3.in_kind = IN_CPLX_MODES; p->P3.out_kind = OUT_CPLX_FULL;
+        p->P3.I = nh * n; p->P3.in_so = N; p->P3.out_so = n;
+        base(p->Q1, +1);
+        p->Q1.in_kind = IN_CPLX_FOLD; p->Q1.out_kind = OUT_CPLX_MODES;
+        p->Q1.I = nh * n; p->Q1.out_so = N; p->Q1.fold_pad = p->pad;
+        p->Q1.fold_plane = (int64_t)n * n; p->Q1.fold_rows_per_plane = n;
+        base(p->Q2, +1);
+        p->Q2.in_kind = IN_CPLX_FULL; p->Q2.out_kind = OUT_CPLX_MODES;
+        p->Q2.I = N; p->Q2.n_outer = nh; p->Q2.in_so = (int64_t)n * N; p->Q2.in_sa = N;
+        p->Q2.out_so = N * N; p->Q2.out_sa = N;
+        base(p->Q3, +1);
+        p->Q3.in_kind = IN_CPLX_HERM; p->Q3.out_kind = OUT_REAL_MODES;
+        p->Q3.I = N * N; p->Q3.n_outer = 1; p->Q3.in_sa = N * N; p->Q3.out_sa = N * N;
+        p->bytes_A = (size_t)nh * N * N * cs;
+        p->bytes_B = (size_t)nh * n * N * cs;
+        p->bytes_G = (size_t)nh * n * n * cs;
+        p->bytes_Hext = (size_t)(nh + 2 * p->pad) * n * n * cs;
+    } else {
+        base(p->P1, -1);
+        p->P1.in_kind = IN_REAL_MODES; p->P1.out_kind = OUT_CPLX_HALF;
+        p->P1.I = N; p->P1.n_outer = 1; p->P1.in_sa = N; p->P1.out_sa = N;
+        base(p->P3, -1);
+        p->P3.in_kind = IN_CPLX_MODES; p->P3.out_kind = OUT_CPLX_FULL;
+        p->P3.I = nh; p->P3.in_so = N; p->P3.out_so = n;
+        base(p->Q1, +1);
+        p->Q1.in_kind = IN_CPLX_FOLD; p->Q1.out_kind = OUT_CPLX_MODES;
+        p->Q1.I = nh; p->Q1.out_so = N; p->Q1.fold_pad = p->pad;
+        p->Q1.fold_plane = n; p->Q1.fold_rows_per_plane = 1;
+        base(p->Q3, +1);
+        p->Q3.in_kind = IN_CPLX_HERM; p->Q3.out_kind = OUT_REAL_MODES;
+        p->Q3.I = N; p->Q3.n_outer = 1; p->Q3.in_sa = N; p->Q3.out_sa = N;
+        p->bytes_A = (size_t)nh * N * cs;
+        p->bytes_B = 0;
+        p->bytes_G = (size_t)nh * n * cs;
+        p->bytes_Hext = (size_t)(nh + 2 * p->pad) * n * cs;
+    }
+    if (p->P1.nrad < 0) return fail(NLINT_EUNSUPPORTED, "fine grid size is not 2^a 3^b");
+    config_pass(p->P1, p->prec, false);
+    config_pass(p->P3, p->prec, true);
+    config_pass(p->Q1, p->prec, true);
+    config_pass(p->Q3, p->prec, false);
+    if (d == 3) {
+        config_pass(p->P2, p->prec, false);
+        config_pass(p->Q2, p->prec, false);
+    }
+    for (PassDesc *pd : {&p->P1, &p->P3, &p->Q1, &p->Q3})
+        if (!pass_fits(*pd)) return fail(NLINT_EUNSUPPORTED, "internal: FFT pass does not fit");
+    if (d == 3 && (!pass_fits(p->P2) || !pass_fits(p->Q2)))
+        return fail(NLINT_EUNSUPPORTED, "internal: FFT pass does not fit");
+    p->n_partials = (int)pass_blocks(p->Q3, false);
+    p->bytes_c = (size_t)Mh * cs;
+    CK(cudaMalloc(&p->d_bufA, p->bytes_A));
+    if (p->bytes_B) CK(cudaMalloc(&p->d_bufB, p->bytes_B));
+    CK(cudaMalloc(&p->d_bufG, std::max(p->bytes_G, p->bytes_Hext)));
+    CK(cudaMalloc(&p->d_c, p->bytes_c + cs));
+    CK(cudaMalloc((void **)&p->d_partials, sizeof(double2) * (size_t)std::max(p->n_partials, 1024)));
+    CK(cudaMalloc((void **)&p->d_E, sizeof(double)));
+    acc += p->bytes_A + p->bytes_B + std::max(p->bytes_G, p->bytes_Hext) + p->bytes_c +
+           sizeof(double2) * (size_t)std::max(p->n_partials, 1024);
+    p->ws_bytes = acc;
+    return NLINT_OK;
+}
+
+// ------------------------------------------------------------------------- execution
+static void stage_mark(nlint_plan_s *p, cudaStream_t s, const char *name) {
+    if (!p->timing) return;
+    if (p->ev_used >= (int)p->ev.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        p->ev.push_back(e);
+        p->ev_names.push_back(name);
+    }
+    p->ev_names[p->ev_used] = name;
+    cudaEventRecord(p->ev[p->ev_used], s);
+    p->ev_used++;
+}
+
+template <typename T>
+static int run_type2(nlint_plan_s *p, const void *rho, cudaStream_t s) {
+    CK(launch_colpass<T>(p->P1, rho, p->d_bufA, p->d_tw, s));
+    if (p->d == 3) {
+        stage_mark(p, s, "fwd_fft_z");
+        CK(launch_colpass<T>(p->P2, p->d_bufA, p->d_bufB, p->d_tw, s));
+        stage_mark(p, s, "fwd_fft_y");
+        CK(launch_rowpass<T>(p->P3, p->d_bufB, p->d_bufG, p->d_tw, s));
+        stage_mark(p, s, "fwd_fft_x");
+    } else {
+        stage_mark(p, s, "fwd_fft_y");
+        CK(launch_rowpass<T>(p->P3, p->d_bufA, p->d_bufG, p->d_tw, s));
+        stage_mark(p, s, "fwd_fft_x");
+    }
+    return NLINT_OK;
+}
+
+static NodeDesc node_desc(nlint_plan_s *p) {
+    NodeDesc nd;
+    nd.d = p->d;
+    nd.M = p->Mh;
+    nd.n = p->n_fine;
+    nd.w = p->w;
+    nd.pad = p->pad;
+    nd.beta = p->beta;
+    nd.l0 = p->d_l0;
+    nd.frac = p->d_frac;
+    nd.W = p->d_W;
+    return nd;
+}
+
+template <typename T>
+static int run_type1(nlint_plan_s *p, void *u, const void *rho_energy, cudaStream_t s) {
+    CK(cudaMemsetAsync(p->d_bufG, 0, p->bytes_Hext, s));
+    CK(launch_spread<T>(node_desc(p), p->d_c, p->d_bufG, s));
+    stage_mark(p, s, "spread");
+    if (p->d == 3) {
+        CK(launch_rowpass<T>(p->Q1, p->d_bufG, p->d_bufB, p->d_tw, s));
+        stage_mark(p, s, "inv_fft_x");
+        CK(launch_colpass<T>(p->Q2, p->d_bufB, p->d_bufA, p->d_tw, s));
+        stage_mark(p, s, "inv_fft_y");
+    } else {
+        CK(launch_rowpass<T>(p->Q1, p->d_bufG, p->d_bufA, p->d_tw, s));
+        stage_mark(p, s, "inv_fft_x");
+    }
+    PassDesc q3 = p->Q3;
+    q3.rho = rho_energy;
+    q3.partials = rho_energy ? p->d_partials : nullptr;
+    CK(launch_colpass<T>(q3, p->d_bufA, u, p->d_tw, s));
+    stage_mark(p, s, p->d == 3 ? "inv_fft_z" : "inv_fft_y");
+    return NLINT_OK;
+}
+
+template <typename T>
+static int run_eval(nlint_plan_s *p, const void *rho, void *u, double lambda, double *E,
+                    cudaStream_t s) {
+    p->ev_used = 0;
+    stage_mark(p, s, "start");
+    int rc = run_type2<T>(p, rho, s);
+    if (rc) return rc;
+    CK(launch_interp<T>(node_desc(p), p->d_bufG, p->d_c, 1, s));
+    stage_mark(p, s, "interp");
+    rc = run_type1<T>(p, u, E ? rho : nullptr, s);
+    if (rc) return rc;
+    if (E) {
+        CK(launch_energy_final(p->d_partials, p->n_partials, 0.5 * lambda * std::pow(p->h, p->d), E, s));
+        stage_mark(p, s, "energy");
+    }
+    return NLINT_OK;
+}
+
+static int check_plan(nlint_plan p) {
+    if (!p) return fail(NLINT_EINVAL, "plan is NULL");
+    cudaError_t e = cudaSetDevice(p->device);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    return NLINT_OK;
+}
+
+}  // namespace nlint
+
+using namespace nlint;
+
+// =============================================================================== C-ABI
+extern "C" {
+
+void nlint_params_default(nlint_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->d = 3;
+    p->n = 32;
+    p->L = 16.0;
+    p->kernel = NLINT_COULOMB;
+    p->eps = 1e-6;
+    p->precision = -1;
+    p->device = -1;
+}
+
+int nlint_plan_create_ex(const nlint_params *prm, nlint_plan *out) {
+    if (!prm || !out) return fail(NLINT_EINVAL, "NULL argument");
+    *out = nullptr;
+    nlint_plan_s *p = new (std::nothrow) nlint_plan_s();
+    if (!p) return fail(NLINT_ENOMEM, "host allocation failed");
+    int rc;
+    try {
+        rc = build_plan(prm, p);
+    } catch (const std::bad_alloc &) {
+        rc = fail(NLINT_ENOMEM, "host allocation failed");
+    } catch (...) {
+        rc = fail(NLINT_EINVAL, "unexpected error while building the plan");
+    }
+    if (rc != NLINT_OK) {
+        plan_free(p);
+        delete p;
+        return rc;
+    }
+    g_err.clear();
+    *out = p;
+    return NLINT_OK;
+}
+
+int nlint_plan_create(int d, int64_t n, double L, int kernel, const double *dipole_axis,
+                      double eps, nlint_plan *out) {
+    nlint_params prm;
+    nlint_params_default(&prm);
+    prm.d = d;
+    prm.n = n;
+    prm.L = L;
+    prm.kernel = kernel;
+    prm.eps = eps;
+    if (kernel == NLINT_DIPOLE) {
+        if (!dipole_axis) return fail(NLINT_EINVAL, "dipole kernel needs an axis");
+        for (int a = 0; a < 3; a++) prm.axis[a] = dipole_axis[a];
+    }
+    return nlint_plan_create_ex(&prm, out);
+}
+
+void nlint_plan_destroy(nlint_plan p) {
+    if (!p) return;
+    cudaSetDevice(p->device);
+    cudaDeviceSynchronize();
+    plan_free(p);
+    delete p;
+}
+
+int nlint_plan_info(nlint_plan p, nlint_info *info) {
+    if (!p || !info) return fail(NLINT_EINVAL, "NULL argument");
+    info->d = p->d;
+    info->precision = p->prec;
+    info->w = p->w;
+    info->kernel = p->prm.kernel;
+    info->n = p->N;
+    info->n_fine = p->n_fine;
+    info->n_nodes = p->Nf;
+    info->n_half_nodes = p->Mh;
+    info->n_r = p->nr;
+    info->n_theta = p->d == 3 ? p->nt : 0;
+    info->n_phi = p->nphi;
+    info->L = p->L;
+    info->h = p->h;
+    info->P = p->P;
+    info->sigma = (double)p->n_fine / (double)p->N;
+    info->beta = p->beta;
+    info->workspace_bytes = p->ws_bytes;
+    return NLINT_OK;
+}
+
+int nlint_plan_nodes(nlint_plan p, double *k_host, double *W_host) {
+    if (!p) return fail(NLINT_EINVAL, "plan is NULL");
+    if (k_host) std::memcpy(k_host, p->k_canon.data(), p->k_canon.size() * sizeof(double));
+    if (W_host) std::memcpy(W_host, p->W_canon.data(), p->W_canon.size() * sizeof(double));
+    return NLINT_OK;
+}
+
+int nlint_eval(nlint_plan p, const void *rho, void *u, void *stream) {
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!rho || !u) return fail(NLINT_EINVAL, "NULL rho or u");
+    cudaStream_t s = (cudaStream_t)stream;
+    return p->prec == NLINT_FP32 ? run_eval<float>(p, rho, u, 0.0, nullptr, s)
+                                 : run_eval<double>(p, rho, u, 0.0, nullptr, s);
+}
+
+int nlint_eval_energy(nlint_plan p, const void *rho, void *u, double lambda, double *E_dev,
+                      void *stream) {
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!rho || !u) return fail(NLINT_EINVAL, "NULL rho or u");
+    cudaStream_t s = (cudaStream_t)stream;
+    double *E = E_dev ? E_dev : p->d_E;
+    return p->prec == NLINT_FP32 ? run_eval<float>(p, rho, u, lambda, E, s)
+                                 : run_eval<double>(p, rho, u, lambda, E, s);
+}
+
+int nlint_energy(nlint_plan p, const void *rho, const void *u, double lambda, double *E_dev,
+                 double *E_host, void *stream) {
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!rho || !u) return fail(NLINT_EINVAL, "NULL rho or u");
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t count = 1;
+    for (int a = 0; a < p->d; a++) count *= p->N;
+    const int nb = 1024;
+    if (p->prec == NLINT_FP32) CK(launch_energy_partials<float>(count, u, rho, p->d_partials, nb, s));
+    else CK(launch_energy_partials<double>(count, u, rho, p->d_partials, nb, s));
+    double *E = E_dev ? E_dev : p->d_E;
+    CK(launch_energy_final(p->d_partials, nb, 0.5 * lambda * std::pow(p->h, p->d), E, s));
+    if (E_host) {
+        CK(cudaMemcpyAsync(E_host, E, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return NLINT_OK;
+}
+
+int nlint_eval_host(nlint_plan p, const void *rho_host, void *u_host, double lambda,
+                    double *E_host, void *stream) {
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!rho_host || !u_host) return fail(NLINT_EINVAL, "NULL rho or u");
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t count = 1;
+    for (int a = 0; a < p->d; a++) count *= p->N;
+    const size_t bytes = (size_t)count * (p->prec == NLINT_FP32 ? 4 : 8);
+    if (!p->d_rho_io) CK(cudaMalloc(&p->d_rho_io, bytes));
+    if (!p->d_u_io) CK(cudaMalloc(&p->d_u_io, bytes));
+    CK(cudaMemcpyAsync(p->d_rho_io, rho_host, bytes, cudaMemcpyHostToDevice, s));
+    rc = p->prec == NLINT_FP32 ? run_eval<float>(p, p->d_rho_io, p->d_u_io, lambda, p->d_E, s)
+                               : run_eval<double>(p, p->d_rho_io, p->d_u_io, lambda, p->d_E, s);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(u_host, p->d_u_io, bytes, cudaMemcpyDeviceToHost, s));
+    if (E_host) CK(cudaMemcpyAsync(E_host, p->d_E, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return NLINT_OK;
+}
+
+int nlint_type2(nlint_plan p, const void *rho, void *rho_hat, void *stream) {
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!rho || !rho_hat) return fail(NLINT_EINVAL, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    p->ev_used = 0;
+    const double hd = std::pow(p->h, p->d);
+    if (p->prec == NLINT_FP32) {
+        if ((rc = run_type2<float>(p, rho, s))) return rc;
+        CK(launch_interp<float>(node_desc(p), p->d_bufG, p->d_c, 0, s));
+        CK(launch_scatter_canonical<float>(p->Mh, p->d_c, p->d_perm, p->d_mirror, hd, rho_hat, s));
+    } else {
+        if ((rc = run_type2<double>(p, rho, s))) return rc;
+        CK(launch_interp<double>(node_desc(p), p->d_bufG, p->d_c, 0, s));
+        CK(launch_scatter_canonical<double>(p->Mh, p->d_c, p->d_perm, p->d_mirror, hd, rho_hat, s));
+    }
+    return NLINT_OK;
+}
+
+int nlint_type1(nlint_plan p, const void *c, void *u, void *stream) {
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!c || !u) return fail(NLINT_EINVAL, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    p->ev_used = 0;
+    if (p->prec == NLINT_FP32) {
+        CK(launch_gather_canonical<float>(p->Mh, c, p->d_perm, p->d_mirror, p->d_c, s));
+        return run_type1<float>(p, u, nullptr, s);
+    }
+    CK(launch_gather_canonical<double>(p->Mh, c, p->d_perm, p->d_mirror, p->d_c, s));
+    return run_type1<double>(p, u, nullptr, s);
+}
+
+int nlint_set_stage_timing(nlint_plan p, int enable) {
+    if (!p) return fail(NLINT_EINVAL, "plan is NULL");
+    p->timing = enable != 0;
+    return NLINT_OK;
+}
+
+int nlint_stage_times(nlint_plan p, float *ms, const char **names, int max_stages, int *n_stages) {
+    if (!p) return fail(NLINT_EINVAL, "plan is NULL");
+    const int k = std::max(0, p->ev_used - 1);
+    if (n_stages) *n_stages = k;
+    if (k == 0) return NLINT_OK;
+    CK(cudaEventSynchronize(p->ev[p->ev_used - 1]));
+    for (int i = 0; i < k && i < max_stages; i++) {
+        float t = 0.0f;
+        CK(cudaEventElapsedTime(&t, p->ev[i], p->ev[i + 1]));
+        if (ms) ms[i] = t;
+        if (names) names[i] = p->ev_names[i + 1];
+    }
+    return NLINT_OK;
+}
+
+const char *nlint_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"
