@@ -1,0 +1,402 @@
+"""Throughput of the free-space convolution u = U * rho plus energy (Algorithm 1) on one GB300.
+
+One step = one full evaluation (type-2 NUFFT, multiply by W_j, type-1 NUFFT, energy) of the
+3D Coulomb workload on a 256^3 grid over [-16,16]^3 (rho = 16 seeded Gaussians, 160x160x320
+spherical nodes, FP32 path with FP64 nodes/weights and a compensated FP64 energy).  The metric
+is grid points per second per potential evaluation.  Beside it the line reports the same
+workload on the FP64 GPU path (speedup, and the FP32 result's error against it), the
+end-to-end rate through the host-buffer entry point, the roofline of the dominant kernel and
+the FP64 CPU oracle timed on this machine's host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: replicas only.  Each rank evaluates its own copy of the workload (independent
+densities; no collective on the data path); value = all ranks' points / max-over-ranks time.
+``--impl reference`` times the FP64 CPU oracle instead (rank 0 only), on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "grid points/s per potential eval (FP32 & batched vs FP64 GPU) at stated rel L-inf err"
+UNIT = "grid points/s"
+L2_FLUSH_BYTES = 256 << 20          # > 129 MB L2: written between timed steps
+
+# DRAM bytes per launch from an ncu capture of the kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum), keyed by stage name, with the hash of the kernel source the capture
+# was taken on: a changed source reports traffic null until it is captured again.
+TRAFFIC = {}
+
+
+def _src_hash(stage: str) -> str:
+    fname = "nufft_kernels.cu" if stage in ("interp", "spread") else "fft_passes.cu"
+    with open(os.path.join(ROOT, "paper_1311_4120_gb300", "csrc", fname), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self._t.join(timeout=2)
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": smax, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- byte model
+def stage_bytes(info: dict, stage: str) -> float:
+    """Algorithmic DRAM bytes of one launch of a stage (3D, sigma = 2 Hermitian layout).
+
+    s = real size, b = 2 s complex size, N grid, n fine grid, nh = n/2 + 1 stored planes,
+    M = half node count.  FFT passes read their input once and write their output once;
+    interp reads the ball |t| < pi (+ stencil) of the half grid once (pi/12 n^3 cells)
+    plus 7 node values and writes c; spread reads c and the node stream and writes the ball
+    once; the energy pass additionally reads rho.
+    """
+    s = 4.0 if info["precision"] == 0 else 8.0
+    b = 2 * s
+    N, n, M = info["n"], info["n_fine"], info["n_half_nodes"]
+    nh = n // 2 + 1
+    node = 3 * 4 + 3 * s + s            # l0 (int32 x3), frac x3, W
+    ball = (np.pi / 12.0) * n ** 3 * b
+    table = {
+        "fwd_fft_z": N ** 3 * s + nh * N * N * b,
+        "fwd_fft_y": nh * N * N * b + nh * n * N * b,
+        "fwd_fft_x": nh * n * N * b + nh * n * n * b,
+        "interp": ball + M * (node + b),
+        "spread": ball + M * (node - s + b),
+        "inv_fft_x": nh * n * n * b + nh * n * N * b,
+        "inv_fft_y": nh * n * N * b + nh * N * N * b,
+        "inv_fft_z": nh * N * N * b + 2 * N ** 3 * s,
+        "energy": 0.0,
+    }
+    return float(table[stage])
+
+
+def path_bytes(info: dict) -> float:
+    """Whole-path algorithmic bytes per evaluation: s (51.4 N^3 + 2 N_f) in 3D."""
+    s = 4.0 if info["precision"] == 0 else 8.0
+    return s * (51.4 * info["n"] ** 3 + 2 * info["n_nodes"])
+
+
+# ----------------------------------------------------------------------------- oracle arm
+CPU_SAMPLE_N = 128
+
+
+def cpu_sample_workload():
+    """Bounded sample of the benchmark workload for the CPU oracle: the same recipe (16
+    seeded Gaussians, centres in [-4,4]^3, widths [0.6,1.4], weights [0.5,1], same h-scaled
+    box [-8,8]^3 at h = 0.125) on a 128^3 grid with the default 96x96x192 node set."""
+    rng = np.random.default_rng(synth.SEED_MIX)
+    c, s, w = synth.mixture_params(rng, 16, 3, 4.0, 0.6, 1.4, 0.5, 1.0)
+    n, L = CPU_SAMPLE_N, 16.0
+    rho = synth.mixture(3, n, L, c, s, w)
+    return rho, L, synth.default_nodes(3, n)
+
+
+def time_oracle_once(rho, L, nodes):
+    from oracle import nufft, pipeline
+    t0 = time.perf_counter()
+    pipeline.oracle_eval(rho, L, nodes, "coulomb", setting="fp32ref")
+    return time.perf_counter() - t0, nufft.threads()
+
+
+def cpu_baseline_obj():
+    rho, L, nodes = cpu_sample_workload()
+    dt, cores = time_oracle_once(rho, L, nodes)
+    return {"value": rho.size / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"one FP64 oracle evaluation (Gaussian-gridding NUFFT, sigma=2, w=16) "
+                       f"of the same 16-Gaussian Coulomb recipe on a {CPU_SAMPLE_N}^3 grid with "
+                       f"{nodes[0]}x{nodes[1]}x{nodes[2]} nodes; {dt:.1f} s")}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    rho, L, nodes = cpu_sample_workload()
+    for _ in range(args.warmup):
+        time_oracle_once(rho, L, nodes)
+    times, cores = [], 1
+    for _ in range(args.steps):
+        dt, cores = time_oracle_once(rho, L, nodes)
+        times.append(dt)
+    tot = sum(times)
+    value = rho.size * args.steps / tot
+    sample = (f"per step one FP64 oracle evaluation (sigma=2, w=16) of the 16-Gaussian Coulomb "
+              f"recipe on a {CPU_SAMPLE_N}^3 grid, {nodes[0]}x{nodes[1]}x{nodes[2]} nodes")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "3D Coulomb 256^3 over [-16,16]^3, 16 seeded Gaussians, "
+                                   "160x160x320 nodes (CPU oracle on a bounded sample)",
+                       "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_1311_4120_gb300 as pkg
+    from paper_1311_4120_gb300 import build as nb
+
+    if rank == 0 or not os.path.exists(nb.LIB):
+        nb.build()
+    if world > 1:
+        torch.distributed.barrier()
+    pkg.load_library()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+
+    wl = synth.config4()
+    rho_np = wl.rho().astype(np.float32)
+    plan = pkg.Plan(wl.d, wl.n, wl.L, wl.kernel, nodes=wl.nodes, eps=1e-6, precision="fp32",
+                    device=local_rank)
+    info = plan.info
+    rho = torch.from_numpy(rho_np).to(dev)
+    u = torch.empty_like(rho)
+    E = torch.empty((), dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        plan.eval_energy(rho, lam=wl.lam, out=u, E_out=E)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, L2 flushed before each, per-step CUDA events on the stream
+    plan.set_stage_timing(True)
+    stage_ms = {}
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    launches0 = plan.launch_count()
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else
+                      int(os.environ["CUDA_VISIBLE_DEVICES"].split(",")[local_rank])) as clk:
+        t_wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            starts[k].record(stream)
+            plan.eval_energy(rho, lam=wl.lam, out=u, E_out=E)
+            ends[k].record(stream)
+            for name, ms in plan.stage_times():
+                stage_ms.setdefault(name, []).append(ms)
+        torch.cuda.synchronize()
+        barrier()
+        t_wall = time.perf_counter() - t_wall0
+    launches = plan.launch_count() - launches0
+    plan.set_stage_timing(False)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    t_dev = sum(step_ms) / 1e3
+    t_max = t_dev
+    if world > 1:
+        tt = torch.tensor([t_dev], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(tt.item())
+    points = wl.n_points * args.steps * world
+    value = points / t_max
+    E32 = float(E.item())
+    u32 = u.clone()
+
+    # ---- end to end through the host-buffer entry point (pinned host memory)
+    rho_h = torch.from_numpy(rho_np).pin_memory()
+    u_h = torch.empty(rho_h.shape, dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        plan.eval_host(rho_h, lam=wl.lam, u_host=u_h)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        plan.eval_host(rho_h, lam=wl.lam, u_host=u_h)
+    t_e2e = time.perf_counter() - t0
+    if world > 1:
+        tt = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+    e2e = {"value": points / t_e2e, "unit": UNIT, "h2d_bytes_per_step": rho_np.nbytes,
+           "d2h_bytes_per_step": rho_np.nbytes + 8}
+
+    # ---- the same workload on the FP64 GPU path: speedup and the FP32 result's error
+    plan64 = pkg.Plan(wl.d, wl.n, wl.L, wl.kernel, nodes=wl.nodes, eps=1e-12, precision="fp64",
+                      device=local_rank)
+    rho64 = torch.from_numpy(wl.rho()).to(dev)
+    u64 = torch.empty_like(rho64)
+    E64 = torch.empty((), dtype=torch.float64, device=dev)
+    for _ in range(2):
+        plan64.eval_energy(rho64, lam=wl.lam, out=u64, E_out=E64)
+    k64 = max(2, min(args.steps, 5))
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * k64)]
+    ms64 = []
+    for k in range(k64):
+        flush.fill_(float(k))
+        ev[2 * k].record(stream)
+        plan64.eval_energy(rho64, lam=wl.lam, out=u64, E_out=E64)
+        ev[2 * k + 1].record(stream)
+    torch.cuda.synchronize()
+    ms64 = [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(k64)]
+    rel = float((u32.double() - u64).abs().max() / u64.abs().max())
+    E64v = float(E64.item())
+    w64 = plan64.info["w"]
+    plan64.close()
+
+    if rank != 0:
+        return 0
+
+    # ---- roofline of the dominant kernel (stage events on the launch stream)
+    mean_stage = {k: sum(v) / len(v) for k, v in stage_ms.items()}
+    dom = max(mean_stage, key=mean_stage.get)
+    peak, peak_kind = peaks()
+    roof = {"bound": "hbm"}
+    ach = stage_bytes(info, dom) / (mean_stage[dom] / 1e3) / 1e9
+    tr = TRAFFIC.get(dom)
+    traffic = tr["bytes"] if (tr and tr.get("src") == _src_hash(dom)) else None
+    roof.update({"kernel": dom, "achieved": ach, "peak": peak, "peak_kind": peak_kind,
+                 "unit": "GB/s", "frac": ach / peak, "traffic": traffic,
+                 "algorithmic_bytes": stage_bytes(info, dom),
+                 "mean_ms": mean_stage[dom]})
+    ms_step = 1e3 * t_max / args.steps
+    path_gbs = path_bytes(info) / (ms_step / 1e3) / 1e9
+
+    cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline_obj()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "3D Coulomb 256^3 over [-16,16]^3, rho = 16 seeded Gaussians, "
+                               "160x160x320 spherical nodes, FP32 path (FP64 nodes/weights, "
+                               "compensated FP64 energy)",
+                   "w": info["w"], "sigma": info["sigma"], "n_fine": info["n_fine"],
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "rel_linf_vs_fp64_gpu": rel,
+        "energy": {"fp32": E32, "fp64_gpu": E64v},
+        "fp64_gpu": {"value": wl.n_points / (statistics.median(ms64) / 1e3), "unit": UNIT,
+                     "ms_per_step": statistics.median(ms64), "w": w64},
+        "speedup_fp32_vs_fp64_gpu": statistics.median(ms64) / ms_step,
+        "stages_ms": {k: round(v, 4) for k, v in mean_stage.items()},
+        "path_bytes_per_step": path_bytes(info),
+        "path_frac_of_hbm": path_gbs / peak,
+        "roofline": roof,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "wall_s_timed_region": t_wall,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        return run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

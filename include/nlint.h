@@ -78,6 +78,10 @@ typedef struct nlint_info {
     int64_t n_r, n_theta, n_phi;
     double L, h, P, sigma, beta;
     size_t workspace_bytes; /* device bytes owned by the plan */
+    int64_t n_bins;         /* non-empty bins of the sorted half node set              */
+    int64_t n_subproblems;  /* CTAs of one interpolation / spreading launch             */
+    int64_t n_crowd_bins;   /* bins whose tiles are summed in FP64 (FP32 plans)         */
+    int bin[3];             /* bin extent per array axis, in fine cells                 */
 } nlint_info;
 
 /* Fill *p with defaults (d = 3, Coulomb, eps = 1e-6, everything else automatic). */
@@ -131,6 +135,10 @@ int nlint_plan_nodes(nlint_plan plan, double *k_host, double *W_host);
 int nlint_set_stage_timing(nlint_plan plan, int enable);
 int nlint_stage_times(nlint_plan plan, float *ms, const char **names, int max_stages,
                       int *n_stages);
+
+/* Number of CUDA kernels this plan has launched so far, over all entry points (memsets and
+ * copies are not counted).  Host-side counter; no synchronisation. */
+int nlint_launch_count(nlint_plan plan, int64_t *count);
 
 /* Thread-local message for the last failed call on this thread ("" if none). */
 const char *nlint_last_error(void);

@@ -28,7 +28,7 @@ EXPORTED = [
     "nlint_params_default", "nlint_plan_create", "nlint_plan_create_ex", "nlint_plan_info",
     "nlint_plan_destroy", "nlint_eval", "nlint_eval_energy", "nlint_energy", "nlint_eval_host",
     "nlint_type2", "nlint_type1", "nlint_plan_nodes", "nlint_set_stage_timing",
-    "nlint_stage_times", "nlint_last_error",
+    "nlint_stage_times", "nlint_launch_count", "nlint_last_error",
 ]
 
 
@@ -53,7 +53,9 @@ class nlint_info(ctypes.Structure):
                 ("n_r", ctypes.c_int64), ("n_theta", ctypes.c_int64), ("n_phi", ctypes.c_int64),
                 ("L", ctypes.c_double), ("h", ctypes.c_double), ("P", ctypes.c_double),
                 ("sigma", ctypes.c_double), ("beta", ctypes.c_double),
-                ("workspace_bytes", ctypes.c_size_t)]
+                ("workspace_bytes", ctypes.c_size_t), ("n_bins", ctypes.c_int64),
+                ("n_subproblems", ctypes.c_int64), ("n_crowd_bins", ctypes.c_int64),
+                ("bin", ctypes.c_int * 3)]
 
 
 _lib = None
@@ -87,6 +89,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.nlint_set_stage_timing.argtypes = [vp, ci]
     lib.nlint_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float),
                                       ctypes.POINTER(ctypes.c_char_p), ci, ctypes.POINTER(ci)]
+    lib.nlint_launch_count.argtypes = [vp, ctypes.POINTER(i64)]
     lib.nlint_last_error.argtypes = []
     lib.nlint_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
@@ -153,6 +156,7 @@ class Plan:
         info = nlint_info()
         _check(lib.nlint_plan_info(h, ctypes.byref(info)))
         self.info = {f: getattr(info, f) for f, _ in nlint_info._fields_}
+        self.info["bin"] = tuple(info.bin)
         self.d, self.n, self.L = d, n, L
         self.device = int(device)
         self.precision = "fp32" if info.precision == NLINT_FP32 else "fp64"
@@ -251,6 +255,12 @@ class Plan:
         k = ctypes.c_int()
         _check(self._lib.nlint_stage_times(self._h, ms, names, 32, ctypes.byref(k)))
         return [(names[i].decode(), ms[i]) for i in range(k.value)]
+
+    def launch_count(self) -> int:
+        """Kernels this plan has launched so far (a host-side counter kept by the library)."""
+        c = ctypes.c_int64()
+        _check(self._lib.nlint_launch_count(self._h, ctypes.byref(c)))
+        return c.value
 
     def close(self):
         if getattr(self, "_h", None):

@@ -43,6 +43,42 @@ struct KSum {
         s = t;
     }
     __device__ __forceinline__ double value() const { return s + c; }
+    // absorb another compensated sum (its value s + c)
+    __device__ __forceinline__ void merge(double os, double oc) { add(os); add(oc); }
 };
+
+// Deterministic reduction of a compensated sum over a warp: a fixed butterfly of shuffles,
+// so the result depends only on the lane values, never on timing.
+__device__ __forceinline__ void ksum_warp(KSum &k) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const double os = __shfl_down_sync(0xffffffffu, k.s, off);
+        const double oc = __shfl_down_sync(0xffffffffu, k.c, off);
+        k.merge(os, oc);
+    }
+}
+
+// Deterministic CTA reduction (blockDim.x a multiple of 32, <= 1024); the total is valid in
+// thread 0.  `scratch` holds 2 doubles per warp.
+__device__ __forceinline__ KSum ksum_block(KSum k, double *scratch) {
+    ksum_warp(k);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) {
+        scratch[2 * wid] = k.s;
+        scratch[2 * wid + 1] = k.c;
+    }
+    __syncthreads();
+    KSum t;
+    t.init();
+    if (wid == 0) {
+        if (lane < nw) {
+            t.s = scratch[2 * lane];
+            t.c = scratch[2 * lane + 1];
+        }
+        ksum_warp(t);
+    }
+    return t;
+}
 
 }  // namespace nlint

@@ -76,7 +76,7 @@ __device__ __forceinline__ void fft_stage(cx_t<T> *buf, int n, int LD, int col, 
                                           int p, const cx_t<T> *__restrict__ tw, int sign) {
     using T2 = cx_t<T>;
     constexpr int MB = MaxB<R>::v;
-    const int nb = n / R;
+    const int nb = (tc < TPC) ? n / R : 0;  // threads past TPC (warp padding) only sync
     T2 v[MB][R];
 #pragma unroll
     for (int b = 0; b < MB; b++) {
@@ -129,23 +129,10 @@ __device__ __forceinline__ void fft_columns(cx_t<T> *buf, const PassDesc &p, int
         fft_stage<T, 3>(buf, p.n, p.LD, col, tc, p.TPC, pp, tw, p.sign);
 }
 
-// Deterministic CTA reduction of compensated sums; thread 0 writes the CTA's partial.
+// CTA reduction of the compensated energy sums; thread 0 writes the CTA's partial.
 __device__ __forceinline__ void block_reduce_ksum(KSum acc, double2 *out, void *scratch) {
-    double *sh = reinterpret_cast<double *>(scratch);
-    __syncthreads();
-    const int t = threadIdx.x;
-    sh[2 * t] = acc.s;
-    sh[2 * t + 1] = acc.c;
-    __syncthreads();
-    if (t == 0) {
-        KSum tot;
-        tot.init();
-        for (int q = 0; q < (int)blockDim.x; q++) {
-            tot.add(sh[2 * q]);
-            tot.add(sh[2 * q + 1]);
-        }
-        *out = make_double2(tot.s, tot.c);
-    }
+    KSum tot = ksum_block(acc, reinterpret_cast<double *>(scratch));
+    if (threadIdx.x == 0) *out = make_double2(tot.s, tot.c);
 }
 
 // --------------------------------------------------------------------------- column pass
@@ -194,7 +181,7 @@ __global__ void __launch_bounds__(256) colpass_kernel(PassDesc p, const void *__
         }
     }
     __syncthreads();
-    fft_columns<T>(buf, p, col, tc < p.TPC ? tc : p.TPC, tw);
+    fft_columns<T>(buf, p, col, tc, tw);
 
     KSum acc;
     acc.init();
@@ -238,9 +225,9 @@ __global__ void __launch_bounds__(256) rowpass_kernel(PassDesc p, const void *__
     const int64_t q0 = (int64_t)blockIdx.x * p.B;
     const T2 *in = reinterpret_cast<const T2 *>(vin);
     T2 *out = reinterpret_cast<T2 *>(vout);
-    const int nthr = p.B * p.TPC;
+    const int nthr = p.B * p.TPC;  // threads past nthr (warp padding) only take part in syncs
 
-    for (int idx = threadIdx.x; idx < p.B * n; idx += nthr) {
+    for (int idx = threadIdx.x; idx < p.B * n && threadIdx.x < nthr; idx += nthr) {
         const int row = idx / n, r = idx % n;
         const int64_t q = q0 + row;
         T2 v = czero<T2>();
@@ -270,7 +257,7 @@ __global__ void __launch_bounds__(256) rowpass_kernel(PassDesc p, const void *__
     fft_columns<T>(buf, p, col, tc, tw);
 
     const int out_len = (p.out_kind == OUT_CPLX_MODES) ? N : n;
-    for (int idx = threadIdx.x; idx < p.B * out_len; idx += nthr) {
+    for (int idx = threadIdx.x; idx < p.B * out_len && threadIdx.x < nthr; idx += nthr) {
         const int row = idx / out_len, a = idx % out_len;
         const int64_t q = q0 + row;
         if (q >= p.I) continue;
@@ -306,8 +293,11 @@ bool pass_fits(const PassDesc &p) {
         const int nb = p.n / R;
         if ((nb + p.TPC - 1) / p.TPC > mb) return false;
     }
-    return p.nrad > 0 && p.B * p.TPC <= 1024;
+    return p.nrad > 0 && pass_threads(p) <= 256;  // the kernels are compiled for <= 256 threads
 }
+
+// Threads per CTA: B lines x TPC threads, rounded up to whole warps.
+int pass_threads(const PassDesc &p) { return (p.B * p.TPC + 31) / 32 * 32; }
 
 int64_t pass_blocks(const PassDesc &p, bool row) {
     if (row) return (p.I + p.B - 1) / p.B;
@@ -317,7 +307,7 @@ int64_t pass_blocks(const PassDesc &p, bool row) {
 size_t pass_smem(const PassDesc &p, int prec) {
     const size_t cs = (prec == NLINT_FP32) ? 8 : 16;
     size_t s = (size_t)p.n * p.LD * cs;
-    const size_t red = (size_t)p.B * p.TPC * 16;  // energy reduction scratch
+    const size_t red = 64 * sizeof(double);  // energy reduction scratch (2 doubles per warp)
     return s > red ? s : red;
 }
 
@@ -329,7 +319,7 @@ cudaError_t launch_colpass(const PassDesc &p, const void *in, void *out, const v
     cudaError_t e = cudaFuncSetAttribute(colpass_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t nb = pass_blocks(p, false);
-    colpass_kernel<T><<<(unsigned)nb, p.B * p.TPC, smem, s>>>(p, in, out, reinterpret_cast<const cx_t<T> *>(tw));
+    colpass_kernel<T><<<(unsigned)nb, pass_threads(p), smem, s>>>(p, in, out, reinterpret_cast<const cx_t<T> *>(tw));
     return cudaGetLastError();
 }
 
@@ -341,7 +331,7 @@ cudaError_t launch_rowpass(const PassDesc &p, const void *in, void *out, const v
     cudaError_t e = cudaFuncSetAttribute(rowpass_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t nb = pass_blocks(p, true);
-    rowpass_kernel<T><<<(unsigned)nb, p.B * p.TPC, smem, s>>>(p, in, out, reinterpret_cast<const cx_t<T> *>(tw));
+    rowpass_kernel<T><<<(unsigned)nb, pass_threads(p), smem, s>>>(p, in, out, reinterpret_cast<const cx_t<T> *>(tw));
     return cudaGetLastError();
 }
 

@@ -52,6 +52,7 @@ struct PassDesc {
 
 void make_radix(int n, PassDesc &p);
 int64_t pass_blocks(const PassDesc &p, bool row);
+int pass_threads(const PassDesc &p);
 size_t pass_smem(const PassDesc &p, int prec);
 void config_pass(PassDesc &p, int prec, bool row);
 bool pass_fits(const PassDesc &p);
@@ -64,6 +65,11 @@ cudaError_t launch_rowpass(const PassDesc &p, const void *in, void *out, const v
                            cudaStream_t s);
 
 // ---------------------------------------------------------------------------- NUFFT kernels
+// The half node set, sorted by bin.  A bin is a box of B[0] x B[1] (x B[2]) stencil-origin
+// cells; the union of its nodes' stencils lies in a tile of T[a] = B[a] + w - 1 cells per axis
+// starting at the bin's origin.  A subproblem is a run of at most a few hundred nodes of one
+// bin and is processed by one CTA on a shared-memory copy of the tile.  Axis 0 is the half
+// (slowest) axis; in 2D only axes 0 and 1 are used.
 struct NodeDesc {
     int d;
     int64_t M;           // number of nodes (half set)
@@ -74,13 +80,25 @@ struct NodeDesc {
     const int32_t *l0;   // d x M, first stencil cell per axis (array-axis order)
     const void *frac;    // d x M, g - l0 per axis (plan precision)
     const void *W;       // M, h^d W_j (plan precision), may be NULL (type-2 only)
+    int B[3], T[3];      // bin and tile extents per array axis
+    int64_t nsub;        // number of subproblems
+    const int4 *subs;    // per subproblem {first node, node count, bin, 0}
+    const int4 *bins;    // per bin {origin axis 0, axis 1, axis 2, crowd slot or -1}
+    int ncrowd;          // crowded bins (FP32 plans): their tiles are summed in FP64
+    double2 *crowd;      // ncrowd tiles of complex doubles
+    const int32_t *crowd_bin;  // bin of each crowd slot
 };
+
+int tile_cells(const NodeDesc &nd);
+size_t node_smem(const NodeDesc &nd, int prec);
 
 template <typename T>
 cudaError_t launch_interp(const NodeDesc &nd, const void *G, void *c_out, int apply_W,
                           cudaStream_t s);
 template <typename T>
 cudaError_t launch_spread(const NodeDesc &nd, const void *c_in, void *Hext, cudaStream_t s);
+template <typename T>
+cudaError_t launch_crowd_merge(const NodeDesc &nd, void *Hext, cudaStream_t s);
 template <typename T>
 cudaError_t launch_scatter_canonical(int64_t M, const void *vals, const int32_t *perm,
                                      const int32_t *mirror, double scale, void *out,

@@ -59,10 +59,11 @@ static void gauss_legendre(int m, std::vector<double> &x, std::vector<double> &w
             p0 = p1;
             p1 = p2;
         }
-        dp = m * (z * p1 - p0) / (z * z - 1.0);
+        // (1 - z)(1 + z) in place of 1 - z^2: no cancellation next to the ends of [-1, 1]
+        dp = m * (p0 - z * p1) / ((1.0 - z) * (1.0 + z));
         x[i] = -z;
         x[m - 1 - i] = z;
-        w[i] = w[m - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+        w[i] = w[m - 1 - i] = 2.0 / ((1.0 - z) * (1.0 + z) * dp * dp);
     }
 }
 
@@ -87,6 +88,13 @@ struct nlint_plan_s {
     int32_t *d_l0 = nullptr;
     void *d_frac = nullptr, *d_W = nullptr, *d_fac = nullptr, *d_tw = nullptr;
     int32_t *d_perm = nullptr, *d_mirror = nullptr;
+    int4 *d_subs = nullptr, *d_bins = nullptr;
+    int32_t *d_crowd_bin = nullptr;
+    double2 *d_crowd = nullptr;
+    int B[3], T[3];
+    int64_t nsub = 0, nbins = 0;
+    int ncrowd = 0;
+    size_t bytes_crowd = 0;
     void *d_bufA = nullptr, *d_bufB = nullptr, *d_bufG = nullptr, *d_c = nullptr;
     double2 *d_partials = nullptr;
     double *d_E = nullptr;
@@ -102,6 +110,7 @@ struct nlint_plan_s {
     std::vector<cudaEvent_t> ev;
     std::vector<const char *> ev_names;
     int ev_used = 0;
+    int64_t launches = 0;  // kernels this plan has launched (all entry points)
 };
 
 namespace nlint {
@@ -157,6 +166,7 @@ static int upload(void **dst, const std::vector<double> &v, size_t &acc) {
 
 static void plan_free(nlint_plan_s *p) {
     void *ptrs[] = {p->d_l0, p->d_frac, p->d_W, p->d_fac, p->d_tw, p->d_perm, p->d_mirror,
+                    p->d_subs, p->d_bins, p->d_crowd_bin, p->d_crowd,
                     p->d_bufA, p->d_bufB, p->d_bufG, p->d_c, p->d_partials, p->d_E,
                     p->d_rho_io, p->d_u_io};
     for (void *q : ptrs)
@@ -286,12 +296,9 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
     const double gscale = p->h * (double)n / (2.0 * M_PI);
     std::vector<int32_t> l0((size_t)d * Mh);
     std::vector<double> fr((size_t)d * Mh);
-    std::vector<int64_t> tile(Mh);
-    const int TS = 8;
-    const int64_t ntile = (n + TS - 1) / TS + 2;
+    int32_t lo[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, hi[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
     for (int64_t o = 0; o < Mh; o++) {
         const int64_t j = half[o];
-        int64_t tkey = 0;
         for (int ax = 0; ax < d; ax++) {
             // array axis ax pairs with node component d-1-ax (axis 0 is k_z in 3D, k_y in 2D)
             const double g = p->k_canon[(size_t)j * d + (d - 1 - ax)] * gscale;
@@ -300,13 +307,32 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
             fr[(size_t)ax * Mh + o] = g - (double)l;
             if (ax == 0 && (l < -p->pad || l + w - 1 > n / 2 + p->pad))
                 return fail(NLINT_EINVAL, "internal: node stencil outside the stored half grid");
-            tkey = tkey * ntile + ((int64_t)l + n + TS) / TS;
+            lo[ax] = std::min(lo[ax], l);
+            hi[ax] = std::max(hi[ax], l);
         }
-        tile[o] = tkey;
+    }
+    // bins: boxes of B[ax] stencil-origin cells starting at lo[ax]; tile = B + w - 1
+    for (int ax = 0; ax < 3; ax++) {
+        p->B[ax] = 1;
+        p->T[ax] = 1;
+    }
+    for (int ax = 0; ax < d; ax++) {
+        int b = (d == 3) ? 8 : 16;
+        if (d == 3 && ax == 0 && p->prec == NLINT_FP64 && w >= 10) b = 4;  // FP64 tile <= 100 KB
+        p->B[ax] = b;
+        p->T[ax] = b + w - 1;
+    }
+    int64_t nbin[3] = {1, 1, 1};
+    for (int ax = 0; ax < d; ax++) nbin[ax] = (Mh ? (hi[ax] - lo[ax]) / p->B[ax] + 1 : 1);
+    std::vector<int64_t> key(Mh);
+    for (int64_t o = 0; o < Mh; o++) {
+        int64_t kk = 0;
+        for (int ax = 0; ax < d; ax++) kk = kk * nbin[ax] + (l0[(size_t)ax * Mh + o] - lo[ax]) / p->B[ax];
+        key[o] = kk;
     }
     std::vector<int64_t> ord(Mh);
     std::iota(ord.begin(), ord.end(), 0);
-    std::stable_sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) { return tile[a] < tile[b]; });
+    std::stable_sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) { return key[a] < key[b]; });
     std::vector<int32_t> l0s((size_t)d * Mh), perm(Mh), mirror(Mh);
     std::vector<double> frs((size_t)d * Mh), Ws(Mh);
     const double hd = std::pow(p->h, d);
@@ -320,6 +346,43 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
         mirror[o] = (int32_t)mir[s];
         Ws[o] = hd * p->W_canon[half[s]];
     }
+    // non-empty bins and their subproblems; crowded bins (FP32 plans) are summed in FP64
+    const int max_sub = (p->prec == NLINT_FP32) ? 1024 : 512;
+    const int max_sub_crowd = 512;
+    const int64_t crowd_min = 4096;
+    std::vector<int4> bins, subs;
+    std::vector<int32_t> crowd_bin;
+    for (int64_t o = 0; o < Mh;) {
+        int64_t e = o;
+        while (e < Mh && key[ord[e]] == key[ord[o]]) e++;
+        int4 b;
+        const int64_t kk = key[ord[o]];
+        int64_t rem = kk;
+        int org[3] = {0, 0, 0};
+        for (int ax = d - 1; ax >= 0; ax--) {
+            org[ax] = lo[ax] + (int)(rem % nbin[ax]) * p->B[ax];
+            rem /= nbin[ax];
+        }
+        b.x = org[0];
+        b.y = org[1];
+        b.z = org[2];
+        const bool crowd = (p->prec == NLINT_FP32) && (e - o > crowd_min);
+        b.w = crowd ? (int)crowd_bin.size() : -1;
+        const int bi = (int)bins.size();
+        if (crowd) crowd_bin.push_back(bi);
+        bins.push_back(b);
+        const int cap = crowd ? max_sub_crowd : max_sub;
+        const int64_t nsub = (e - o + cap - 1) / cap;
+        for (int64_t q = 0; q < nsub; q++) {
+            const int64_t a = o + (e - o) * q / nsub, z = o + (e - o) * (q + 1) / nsub;
+            subs.push_back(make_int4((int)a, (int)(z - a), bi, 0));
+        }
+        o = e;
+    }
+    p->nsub = (int64_t)subs.size();
+    p->nbins = (int64_t)bins.size();
+    p->ncrowd = (int)crowd_bin.size();
+    if (p->nsub > (int64_t)INT32_MAX) return fail(NLINT_EUNSUPPORTED, "too many subproblems");
 
     // ---------------- deconvolution factors f[m'] = (2 pi / n) / psi_hat(m), m = m' - N/2
     std::vector<double> qx, qw;
@@ -348,6 +411,23 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
     CK(cudaMalloc((void **)&p->d_mirror, mirror.size() * sizeof(int32_t) + 4));
     CK(cudaMemcpy(p->d_mirror, mirror.data(), mirror.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     acc += (l0s.size() + perm.size() + mirror.size()) * 4;
+    CK(cudaMalloc((void **)&p->d_subs, sizeof(int4) * std::max<size_t>(subs.size(), 1)));
+    if (!subs.empty()) CK(cudaMemcpy(p->d_subs, subs.data(), sizeof(int4) * subs.size(), cudaMemcpyHostToDevice));
+    CK(cudaMalloc((void **)&p->d_bins, sizeof(int4) * std::max<size_t>(bins.size(), 1)));
+    if (!bins.empty()) CK(cudaMemcpy(p->d_bins, bins.data(), sizeof(int4) * bins.size(), cudaMemcpyHostToDevice));
+    CK(cudaMalloc((void **)&p->d_crowd_bin, sizeof(int32_t) * std::max<size_t>(crowd_bin.size(), 1)));
+    if (!crowd_bin.empty())
+        CK(cudaMemcpy(p->d_crowd_bin, crowd_bin.data(), sizeof(int32_t) * crowd_bin.size(), cudaMemcpyHostToDevice));
+    acc += sizeof(int4) * (subs.size() + bins.size()) + 4 * crowd_bin.size();
+    {
+        int64_t cells = 1;
+        for (int ax = 0; ax < d; ax++) cells *= p->T[ax];
+        p->bytes_crowd = sizeof(double2) * (size_t)cells * (size_t)p->ncrowd;
+        if (p->bytes_crowd) {
+            CK(cudaMalloc((void **)&p->d_crowd, p->bytes_crowd));
+            acc += p->bytes_crowd;
+        }
+    }
     if (p->prec == NLINT_FP32) {
         if ((rc = upload<float>(&p->d_frac, frs, acc))) return rc;
         if ((rc = upload<float>(&p->d_W, Ws, acc))) return rc;
@@ -461,6 +541,7 @@ static void stage_mark(nlint_plan_s *p, cudaStream_t s, const char *name) {
 template <typename T>
 static int run_type2(nlint_plan_s *p, const void *rho, cudaStream_t s) {
     CK(launch_colpass<T>(p->P1, rho, p->d_bufA, p->d_tw, s));
+    p->launches += (p->d == 3) ? 3 : 2;
     if (p->d == 3) {
         stage_mark(p, s, "fwd_fft_z");
         CK(launch_colpass<T>(p->P2, p->d_bufA, p->d_bufB, p->d_tw, s));
@@ -486,13 +567,29 @@ static NodeDesc node_desc(nlint_plan_s *p) {
     nd.l0 = p->d_l0;
     nd.frac = p->d_frac;
     nd.W = p->d_W;
+    for (int a = 0; a < 3; a++) {
+        nd.B[a] = p->B[a];
+        nd.T[a] = p->T[a];
+    }
+    nd.nsub = p->nsub;
+    nd.subs = p->d_subs;
+    nd.bins = p->d_bins;
+    nd.ncrowd = p->ncrowd;
+    nd.crowd = p->d_crowd;
+    nd.crowd_bin = p->d_crowd_bin;
     return nd;
 }
 
 template <typename T>
 static int run_type1(nlint_plan_s *p, void *u, const void *rho_energy, cudaStream_t s) {
     CK(cudaMemsetAsync(p->d_bufG, 0, p->bytes_Hext, s));
+    if (p->ncrowd) CK(cudaMemsetAsync(p->d_crowd, 0, p->bytes_crowd, s));
     CK(launch_spread<T>(node_desc(p), p->d_c, p->d_bufG, s));
+    if (p->ncrowd) {
+        CK(launch_crowd_merge<T>(node_desc(p), p->d_bufG, s));
+        p->launches += 1;
+    }
+    p->launches += (p->d == 3) ? 4 : 3;
     stage_mark(p, s, "spread");
     if (p->d == 3) {
         CK(launch_rowpass<T>(p->Q1, p->d_bufG, p->d_bufB, p->d_tw, s));
@@ -519,11 +616,13 @@ static int run_eval(nlint_plan_s *p, const void *rho, void *u, double lambda, do
     int rc = run_type2<T>(p, rho, s);
     if (rc) return rc;
     CK(launch_interp<T>(node_desc(p), p->d_bufG, p->d_c, 1, s));
+    p->launches += 1;
     stage_mark(p, s, "interp");
     rc = run_type1<T>(p, u, E ? rho : nullptr, s);
     if (rc) return rc;
     if (E) {
         CK(launch_energy_final(p->d_partials, p->n_partials, 0.5 * lambda * std::pow(p->h, p->d), E, s));
+        p->launches += 1;
         stage_mark(p, s, "energy");
     }
     return NLINT_OK;
@@ -621,6 +720,10 @@ int nlint_plan_info(nlint_plan p, nlint_info *info) {
     info->sigma = (double)p->n_fine / (double)p->N;
     info->beta = p->beta;
     info->workspace_bytes = p->ws_bytes;
+    info->n_bins = p->nbins;
+    info->n_subproblems = p->nsub;
+    info->n_crowd_bins = p->ncrowd;
+    for (int a = 0; a < 3; a++) info->bin[a] = p->B[a];
     return NLINT_OK;
 }
 
@@ -664,6 +767,7 @@ int nlint_energy(nlint_plan p, const void *rho, const void *u, double lambda, do
     else CK(launch_energy_partials<double>(count, u, rho, p->d_partials, nb, s));
     double *E = E_dev ? E_dev : p->d_E;
     CK(launch_energy_final(p->d_partials, nb, 0.5 * lambda * std::pow(p->h, p->d), E, s));
+    p->launches += 2;
     if (E_host) {
         CK(cudaMemcpyAsync(E_host, E, sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -703,10 +807,12 @@ int nlint_type2(nlint_plan p, const void *rho, void *rho_hat, void *stream) {
         if ((rc = run_type2<float>(p, rho, s))) return rc;
         CK(launch_interp<float>(node_desc(p), p->d_bufG, p->d_c, 0, s));
         CK(launch_scatter_canonical<float>(p->Mh, p->d_c, p->d_perm, p->d_mirror, hd, rho_hat, s));
+        p->launches += 2;
     } else {
         if ((rc = run_type2<double>(p, rho, s))) return rc;
         CK(launch_interp<double>(node_desc(p), p->d_bufG, p->d_c, 0, s));
         CK(launch_scatter_canonical<double>(p->Mh, p->d_c, p->d_perm, p->d_mirror, hd, rho_hat, s));
+        p->launches += 2;
     }
     return NLINT_OK;
 }
@@ -717,6 +823,7 @@ int nlint_type1(nlint_plan p, const void *c, void *u, void *stream) {
     if (!c || !u) return fail(NLINT_EINVAL, "NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
     p->ev_used = 0;
+    p->launches += 1;
     if (p->prec == NLINT_FP32) {
         CK(launch_gather_canonical<float>(p->Mh, c, p->d_perm, p->d_mirror, p->d_c, s));
         return run_type1<float>(p, u, nullptr, s);
@@ -743,6 +850,12 @@ int nlint_stage_times(nlint_plan p, float *ms, const char **names, int max_stage
         if (ms) ms[i] = t;
         if (names) names[i] = p->ev_names[i + 1];
     }
+    return NLINT_OK;
+}
+
+int nlint_launch_count(nlint_plan p, int64_t *count) {
+    if (!p || !count) return fail(NLINT_EINVAL, "NULL argument");
+    *count = p->launches;
     return NLINT_OK;
 }
 

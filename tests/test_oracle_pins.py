@@ -31,6 +31,21 @@ def test_gauss_legendre_exact_on_polynomials():
         assert abs(np.sum(w * x ** deg) - P ** (deg + 1) / (deg + 1)) <= 1e-12 * P ** (deg + 1)
 
 
+@pytest.mark.parametrize("m", [32, 128, 320])
+def test_gauss_legendre_against_high_precision_rule(m):
+    # Nodes are the roots of P_m found to 40 digits; weights 2 (1 - t^2) / (m P_{m-1}(t))^2.
+    # Near the ends a node is only representable to ~5e-17 absolute, which moves the exact
+    # weight at that double by up to ~2e-12 relative at m = 320 (the bound used here).
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    x, w = quadrature.gauss_legendre(m, -1.0, 1.0)
+    for i in (0, 1, 3, m // 3, m // 2):
+        t = mp.findroot(lambda s: mp.legendre(m, s), mp.mpf(x[i]))
+        wt = 2 * (1 - t ** 2) / (m ** 2 * mp.legendre(m - 1, t) ** 2)
+        assert abs(float(x[i] - t)) <= 1e-16
+        assert abs(float((w[i] - wt) / wt)) <= 5e-12
+
+
 def test_weight_sums_closed_form_3d_2d():
     # Coulomb: |k|^{d-1} U_hat = 1, so sum_j W_j = (2 pi)^{-d} * measure of the ball in (r, angles)
     n, L = 16, 8.0
