@@ -89,6 +89,17 @@ struct NodeDesc {
     const int32_t *crowd_bin;  // bin of each crowd slot
 };
 
+// Bin extent (stencil-origin cells) along array axis `axis`; the same rule is compiled into
+// the kernels, so a plan's bins always match the tile geometry of its kernels.  3D: 8^3 bins,
+// except 4 x 8 x 8 for FP64 stencils of width >= 10 (tile <= 100 KB of shared memory);
+// 2D: 16 x 16 bins.
+__host__ __device__ constexpr int bin_extent(bool fp64, int d, int w, int axis) {
+    return d == 3 ? ((axis == 0 && fp64 && w >= 10) ? 4 : 8) : (axis < 2 ? 16 : 1);
+}
+
+static constexpr int NODE_MAXW = 16;     // widest stencil
+static constexpr int NODE_THREADS = 256;  // threads per interpolation / spreading CTA
+
 int tile_cells(const NodeDesc &nd);
 size_t node_smem(const NodeDesc &nd, int prec);
 
@@ -99,6 +110,14 @@ template <typename T>
 cudaError_t launch_spread(const NodeDesc &nd, const void *c_in, void *Hext, cudaStream_t s);
 template <typename T>
 cudaError_t launch_crowd_merge(const NodeDesc &nd, void *Hext, cudaStream_t s);
+// per (precision, dimension) launchers, one translation unit each (width dispatch inside)
+template <typename T, int D>
+cudaError_t launch_interp_d(const NodeDesc &nd, const void *G, void *c_out, int apply_W,
+                            cudaStream_t s);
+template <typename T, int D>
+cudaError_t launch_spread_d(const NodeDesc &nd, const void *c_in, void *Hext, cudaStream_t s);
+template <typename T, int D>
+cudaError_t launch_crowd_merge_d(const NodeDesc &nd, void *Hext, cudaStream_t s);
 template <typename T>
 cudaError_t launch_scatter_canonical(int64_t M, const void *vals, const int32_t *perm,
                                      const int32_t *mirror, double scale, void *out,

@@ -1,0 +1,370 @@
+// Type-2 interpolation with the multiply by W_j, and type-1 spreading (steps a3, a4 and a5 of
+// the path; Algorithm 1, eq. 3.2 and eq. 3.7), templated on the stencil width so that every
+// loop over the stencil is unrolled and every tile index is a compile-time product.
+//
+// Spreading function: the "exponential of semicircle" of Barnett, Magland and af Klinteberg
+// (SIAM J. Sci. Comput. 2019), phi(z) = exp(beta (sqrt(1 - z^2) - 1)) on |z| <= 1, with
+// z = (l - g) / (w/2) for fine cell l and node position g in fine-cell units.
+//
+// Only the half node set (k on the non-negative side of array axis 0) is processed:
+// rho_hat(-k) = conj(rho_hat(k)) for a real density, and the mirrored nodes' spreading is
+// restored by the fold in the first inverse FFT pass.  The fine grid G holds the planes
+// 0..n/2 of axis 0; other planes are read as conj(G[-l]).  The spread grid H+ is stored on
+// planes -pad..n/2+pad of axis 0.
+//
+// Work decomposition: one CTA per subproblem (a run of nodes of one bin).  The CTA stages its
+// bin's tile (bin + w - 1 cells per axis) in shared memory as separate real and imaginary
+// planes.  A warp takes one node at a time; in 3D its lanes own (axis 1, axis 2) stencil
+// columns and run along axis 0 with the axis-0 kernel values in registers, in 2D they own
+// stencil cells.  Interpolation sums the lanes with a shuffle tree; spreading adds into the
+// tile with shared atomics (the lanes of one node touch distinct cells) and then adds the
+// tile's nonzero cells to H+ with global atomics, or, for crowded bins, to an FP64 tile.
+#pragma once
+#include "common.cuh"
+#include "internal.h"
+
+namespace nlint {
+
+static constexpr int MAXW = NODE_MAXW;
+static constexpr int SUB_THREADS = NODE_THREADS;
+
+template <typename T, int D, int W>
+struct Geo {
+    static constexpr bool F64 = sizeof(T) == 8;
+    static constexpr int B0 = bin_extent(F64, D, W, 0), B1 = bin_extent(F64, D, W, 1);
+    static constexpr int B2 = (D == 3) ? bin_extent(F64, D, W, 2) : 1;
+    static constexpr int T0 = B0 + W - 1, T1 = B1 + W - 1, T2 = (D == 3) ? B2 + W - 1 : 1;
+    static constexpr int NCELL = T0 * T1 * T2;
+    static constexpr int PAIRS = W * W;           // lane work items per node
+    static constexpr int PASSES = (PAIRS + 31) / 32;
+};
+
+template <typename T>
+__device__ __forceinline__ T es_kernel(T z, T beta) {
+    const T s = T(1) - z * z;
+    return s > T(0) ? exp(beta * (sqrt(s) - T(1))) : T(0);
+}
+
+// l mod n for l in [-n, 2n)
+__device__ __forceinline__ int wrap1(int l, int n) { return l < 0 ? l + n : (l >= n ? l - n : l); }
+
+__device__ __forceinline__ int wrapn(int l, int n) {
+    int r = l % n;
+    return r < 0 ? r + n : r;
+}
+
+// G at (l0, l1[, l2]) of the full periodic fine grid from its stored half (planes 0..n/2 of
+// axis 0), using G[-l] = conj(G[l]) for the other half.
+template <typename T, int D>
+__device__ __forceinline__ cx_t<T> fetch_half(const cx_t<T> *__restrict__ G, int n, int l0, int l1,
+                                              int l2) {
+    const int z = wrapn(l0, n);
+    if (z <= n / 2) {
+        if (D == 3) return G[((int64_t)z * n + wrapn(l1, n)) * n + wrapn(l2, n)];
+        return G[(int64_t)z * n + wrapn(l1, n)];
+    }
+    const int mz = n - z;
+    if (D == 3) return cconj(G[((int64_t)mz * n + wrapn(-l1, n)) * n + wrapn(-l2, n)]);
+    return cconj(G[(int64_t)mz * n + wrapn(-l1, n)]);
+}
+
+// Kernel values of one node into ker[a*MAXW + q] = phi((q - frac_a) / (w/2)), stencil cell q
+// of axis a, computed by the lanes of the warp (D*W values, some lanes take two).
+template <typename T, int D, int W>
+__device__ __forceinline__ void warp_kernel_values(const NodeDesc &nd, int64_t j, int lane, T *ker) {
+    const T inv_half = T(2) / T(W);
+    const T beta = T(nd.beta);
+#pragma unroll
+    for (int t0 = 0; t0 < D * W; t0 += 32) {
+        const int t = t0 + lane;
+        if (t < D * W) {
+            const int a = t / W, q = t - a * W;
+            const T fr = reinterpret_cast<const T *>(nd.frac)[a * nd.M + j];
+            ker[a * MAXW + q] = es_kernel<T>((T(q) - fr) * inv_half, beta);
+        }
+    }
+}
+
+// Decompose a tile cell into its per-axis offsets.
+template <typename G_>
+__device__ __forceinline__ void cell_coords(int cell, int &a0, int &a1, int &a2) {
+    a0 = cell / (G_::T1 * G_::T2);
+    const int rem = cell - a0 * (G_::T1 * G_::T2);
+    a1 = rem / G_::T2;
+    a2 = rem - a1 * G_::T2;
+}
+
+template <typename T, int D, int W>
+__global__ void __launch_bounds__(SUB_THREADS) interp_sub_kernel(NodeDesc nd,
+                                                                const cx_t<T> *__restrict__ G,
+                                                                cx_t<T> *__restrict__ c_out,
+                                                                int apply_W) {
+    using T2 = cx_t<T>;
+    using G_ = Geo<T, D, W>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *tr = reinterpret_cast<T *>(smem_raw);
+    T *ti = tr + G_::NCELL;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    T *ker = ti + G_::NCELL + wid * 3 * MAXW;
+    const int4 sb = nd.subs[blockIdx.x];
+    const int4 bo = nd.bins[sb.z];
+    const int n = nd.n;
+
+    // stage the tile; the common case (axis-0 planes inside the stored half) needs no mirror
+    const bool inside = bo.x >= 0 && bo.x + G_::T0 - 1 <= n / 2;
+    for (int cell = threadIdx.x; cell < G_::NCELL; cell += blockDim.x) {
+        int a0, a1, a2;
+        cell_coords<G_>(cell, a0, a1, a2);
+        T2 v;
+        if (inside) {
+            const int l0 = bo.x + a0, l1 = wrap1(bo.y + a1, n);
+            v = (D == 3) ? G[((int64_t)l0 * n + l1) * n + wrap1(bo.z + a2, n)] : G[(int64_t)l0 * n + l1];
+        } else {
+            v = fetch_half<T, D>(G, n, bo.x + a0, bo.y + a1, bo.z + a2);
+        }
+        tr[cell] = v.x;
+        ti[cell] = v.y;
+    }
+    __syncthreads();
+
+    const int64_t M = nd.M;
+    for (int i = wid; i < sb.y; i += nw) {
+        const int64_t j = (int64_t)sb.x + i;
+        warp_kernel_values<T, D, W>(nd, j, lane, ker);
+        const int r0 = nd.l0[j] - bo.x, r1 = nd.l0[M + j] - bo.y;
+        const int r2 = (D == 3) ? nd.l0[2 * M + j] - bo.z : 0;
+        __syncwarp();
+        T accr = T(0), acci = T(0);
+        if constexpr (D == 3) {
+            T k0[W];
+#pragma unroll
+            for (int q = 0; q < W; q++) k0[q] = ker[q];
+#pragma unroll
+            for (int ps = 0; ps < G_::PASSES; ps++) {
+                const int p = lane + 32 * ps;
+                if (p < G_::PAIRS) {
+                    const int q1 = p / W, q2 = p - q1 * W;
+                    const int idx = (r0 * G_::T1 + r1 + q1) * G_::T2 + r2 + q2;
+                    T sr = T(0), si = T(0);
+#pragma unroll
+                    for (int q0 = 0; q0 < W; q0++) {
+                        sr += k0[q0] * tr[idx + q0 * G_::T1 * G_::T2];
+                        si += k0[q0] * ti[idx + q0 * G_::T1 * G_::T2];
+                    }
+                    const T k12 = ker[MAXW + q1] * ker[2 * MAXW + q2];
+                    accr += k12 * sr;
+                    acci += k12 * si;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int ps = 0; ps < G_::PASSES; ps++) {
+                const int p = lane + 32 * ps;
+                if (p < G_::PAIRS) {
+                    const int q0 = p / W, q1 = p - q0 * W;
+                    const int idx = (r0 + q0) * G_::T1 + r1 + q1;
+                    const T k = ker[q0] * ker[MAXW + q1];
+                    accr += k * tr[idx];
+                    acci += k * ti[idx];
+                }
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            accr += __shfl_xor_sync(0xffffffffu, accr, off);
+            acci += __shfl_xor_sync(0xffffffffu, acci, off);
+        }
+        if (lane == 0) {
+            const T sc = apply_W ? reinterpret_cast<const T *>(nd.W)[j] : T(1);
+            c_out[j] = cmake<T2>(accr * sc, acci * sc);
+        }
+        __syncwarp();
+    }
+}
+
+__device__ __forceinline__ void atomic_add_cx(float2 *p, float re, float im) {
+    atomicAdd(p, make_float2(re, im));
+}
+__device__ __forceinline__ void atomic_add_cx(double2 *p, double re, double im) {
+    atomicAdd(&p->x, re);
+    atomicAdd(&p->y, im);
+}
+
+template <typename T, int D, int W>
+__global__ void __launch_bounds__(SUB_THREADS) spread_sub_kernel(NodeDesc nd,
+                                                                const cx_t<T> *__restrict__ c_in,
+                                                                cx_t<T> *__restrict__ H) {
+    using T2 = cx_t<T>;
+    using G_ = Geo<T, D, W>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *tr = reinterpret_cast<T *>(smem_raw);
+    T *ti = tr + G_::NCELL;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    T *ker = ti + G_::NCELL + wid * 3 * MAXW;
+    const int4 sb = nd.subs[blockIdx.x];
+    const int4 bo = nd.bins[sb.z];
+    const int n = nd.n, pad = nd.pad;
+
+    for (int cell = threadIdx.x; cell < G_::NCELL; cell += blockDim.x) {
+        tr[cell] = T(0);
+        ti[cell] = T(0);
+    }
+    __syncthreads();
+
+    const int64_t M = nd.M;
+    for (int i = wid; i < sb.y; i += nw) {
+        const int64_t j = (int64_t)sb.x + i;
+        warp_kernel_values<T, D, W>(nd, j, lane, ker);
+        const int r0 = nd.l0[j] - bo.x, r1 = nd.l0[M + j] - bo.y;
+        const int r2 = (D == 3) ? nd.l0[2 * M + j] - bo.z : 0;
+        const T2 c = c_in[j];
+        __syncwarp();
+        if constexpr (D == 3) {
+            T k0[W];
+#pragma unroll
+            for (int q = 0; q < W; q++) k0[q] = ker[q];
+#pragma unroll
+            for (int ps = 0; ps < G_::PASSES; ps++) {
+                const int p = lane + 32 * ps;
+                if (p < G_::PAIRS) {
+                    const int q1 = p / W, q2 = p - q1 * W;
+                    const T k12 = ker[MAXW + q1] * ker[2 * MAXW + q2];
+                    const T cr = c.x * k12, ci = c.y * k12;
+                    const int idx = (r0 * G_::T1 + r1 + q1) * G_::T2 + r2 + q2;
+#pragma unroll
+                    for (int q0 = 0; q0 < W; q0++) {
+                        atomicAdd(tr + idx + q0 * G_::T1 * G_::T2, cr * k0[q0]);
+                        atomicAdd(ti + idx + q0 * G_::T1 * G_::T2, ci * k0[q0]);
+                    }
+                }
+            }
+        } else {
+#pragma unroll
+            for (int ps = 0; ps < G_::PASSES; ps++) {
+                const int p = lane + 32 * ps;
+                if (p < G_::PAIRS) {
+                    const int q0 = p / W, q1 = p - q0 * W;
+                    const int idx = (r0 + q0) * G_::T1 + r1 + q1;
+                    const T k = ker[q0] * ker[MAXW + q1];
+                    atomicAdd(tr + idx, c.x * k);
+                    atomicAdd(ti + idx, c.y * k);
+                }
+            }
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+
+    const int slot = bo.w;
+    const int nplanes = n / 2 + 1 + 2 * pad;
+    for (int cell = threadIdx.x; cell < G_::NCELL; cell += blockDim.x) {
+        const T vr = tr[cell], vi = ti[cell];
+        if (vr == T(0) && vi == T(0)) continue;
+        if (slot >= 0) {
+            atomic_add_cx(nd.crowd + (int64_t)slot * G_::NCELL + cell, (double)vr, (double)vi);
+            continue;
+        }
+        int a0, a1, a2;
+        cell_coords<G_>(cell, a0, a1, a2);
+        const int pl = bo.x + a0 + pad;
+        if (pl < 0 || pl >= nplanes) continue;  // outside every stencil: the cell is zero
+        const int64_t g = (D == 3)
+            ? ((int64_t)pl * n + wrap1(bo.y + a1, n)) * n + wrap1(bo.z + a2, n)
+            : (int64_t)pl * n + wrap1(bo.y + a1, n);
+        atomic_add_cx(H + g, vr, vi);
+    }
+}
+
+template <typename T, int D, int W>
+static cudaError_t launch_interp_w(const NodeDesc &nd, const void *G, void *c_out, int apply_W,
+                                   size_t smem, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(interp_sub_kernel<T, D, W>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    interp_sub_kernel<T, D, W><<<(unsigned)nd.nsub, SUB_THREADS, smem, s>>>(
+        nd, (const cx_t<T> *)G, (cx_t<T> *)c_out, apply_W);
+    return cudaGetLastError();
+}
+
+template <typename T, int D, int W>
+static cudaError_t launch_spread_w(const NodeDesc &nd, const void *c_in, void *H, size_t smem,
+                                   cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(spread_sub_kernel<T, D, W>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    spread_sub_kernel<T, D, W><<<(unsigned)nd.nsub, SUB_THREADS, smem, s>>>(
+        nd, (const cx_t<T> *)c_in, (cx_t<T> *)H);
+    return cudaGetLastError();
+}
+
+// Adds the FP64 tiles of the crowded bins into the extended spread grid (one CTA per tile).
+template <typename T, int D>
+__global__ void __launch_bounds__(SUB_THREADS) crowd_merge_kernel(NodeDesc nd, cx_t<T> *__restrict__ H) {
+    const int T1 = nd.T[1], T2n = (D == 3) ? nd.T[2] : 1;
+    const int ncell = nd.T[0] * T1 * T2n;
+    const int slot = blockIdx.x;
+    const int4 bo = nd.bins[nd.crowd_bin[slot]];
+    const int n = nd.n, pad = nd.pad;
+    const int nplanes = n / 2 + 1 + 2 * pad;
+    const double2 *src = nd.crowd + (int64_t)slot * ncell;
+    for (int cell = threadIdx.x; cell < ncell; cell += blockDim.x) {
+        const double2 v = src[cell];
+        if (v.x == 0.0 && v.y == 0.0) continue;
+        const int a0 = cell / (T1 * T2n), rem = cell - a0 * T1 * T2n;
+        const int a1 = rem / T2n, a2 = rem - a1 * T2n;
+        const int pl = bo.x + a0 + pad;
+        if (pl < 0 || pl >= nplanes) continue;
+        const int64_t g = (D == 3)
+            ? ((int64_t)pl * n + wrap1(bo.y + a1, n)) * n + wrap1(bo.z + a2, n)
+            : (int64_t)pl * n + wrap1(bo.y + a1, n);
+        atomic_add_cx(H + g, (T)v.x, (T)v.y);
+    }
+}
+
+template <typename T, int D>
+cudaError_t launch_crowd_merge_d(const NodeDesc &nd, void *H, cudaStream_t s) {
+    if (nd.ncrowd == 0) return cudaSuccess;
+    crowd_merge_kernel<T, D><<<(unsigned)nd.ncrowd, SUB_THREADS, 0, s>>>(nd, (cx_t<T> *)H);
+    return cudaGetLastError();
+}
+
+#define NLINT_W_SWITCH(CALL)                                                   \
+    switch (nd.w) {                                                            \
+        case 2: return CALL(2);   case 3: return CALL(3);                      \
+        case 4: return CALL(4);   case 5: return CALL(5);                      \
+        case 6: return CALL(6);   case 7: return CALL(7);                      \
+        case 8: return CALL(8);   case 9: return CALL(9);                      \
+        case 10: return CALL(10); case 11: return CALL(11);                    \
+        case 12: return CALL(12); case 13: return CALL(13);                    \
+        case 14: return CALL(14); case 15: return CALL(15);                    \
+        case 16: return CALL(16);                                              \
+        default: return cudaErrorInvalidValue;                                 \
+    }
+
+template <typename T, int D>
+cudaError_t launch_interp_d(const NodeDesc &nd, const void *G, void *c_out, int apply_W,
+                            cudaStream_t s) {
+    if (nd.nsub == 0) return cudaSuccess;
+    const size_t sm = node_smem(nd, sizeof(T) == 4 ? NLINT_FP32 : NLINT_FP64);
+#define NLINT_CALL_I(WW) launch_interp_w<T, D, WW>(nd, G, c_out, apply_W, sm, s)
+    NLINT_W_SWITCH(NLINT_CALL_I)
+#undef NLINT_CALL_I
+}
+
+template <typename T, int D>
+cudaError_t launch_spread_d(const NodeDesc &nd, const void *c_in, void *H, cudaStream_t s) {
+    if (nd.nsub == 0) return cudaSuccess;
+    const size_t sm = node_smem(nd, sizeof(T) == 4 ? NLINT_FP32 : NLINT_FP64);
+#define NLINT_CALL_S(WW) launch_spread_w<T, D, WW>(nd, c_in, H, sm, s)
+    NLINT_W_SWITCH(NLINT_CALL_S)
+#undef NLINT_CALL_S
+}
+
+#define NLINT_NODE_KERNELS_INSTANTIATE(T, D)                                                    \
+    template cudaError_t launch_interp_d<T, D>(const NodeDesc &, const void *, void *, int,      \
+                                               cudaStream_t);                                  \
+    template cudaError_t launch_spread_d<T, D>(const NodeDesc &, const void *, void *,           \
+                                               cudaStream_t);                                  \
+    template cudaError_t launch_crowd_merge_d<T, D>(const NodeDesc &, void *, cudaStream_t);
+
+}  // namespace nlint

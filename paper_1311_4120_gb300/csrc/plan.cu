@@ -317,8 +317,7 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
         p->T[ax] = 1;
     }
     for (int ax = 0; ax < d; ax++) {
-        int b = (d == 3) ? 8 : 16;
-        if (d == 3 && ax == 0 && p->prec == NLINT_FP64 && w >= 10) b = 4;  // FP64 tile <= 100 KB
+        const int b = bin_extent(p->prec == NLINT_FP64, d, w, ax);
         p->B[ax] = b;
         p->T[ax] = b + w - 1;
     }
