@@ -136,6 +136,23 @@ int nlint_set_stage_timing(nlint_plan plan, int enable);
 int nlint_stage_times(nlint_plan plan, float *ms, const char **names, int max_stages,
                       int *n_stages);
 
+/* Energy E = (lambda/2) h^d sum_i u_i rho_i (h = L/n) of caller-owned device arrays, written
+ * to the device double E_dev, for callers that cannot allocate device memory when they need
+ * it (a framework that owns the whole device through its own pool, a thread that must not
+ * call cudaMalloc/cudaFree because they synchronise the device, a fixed memory budget).  The
+ * paper has no counterpart: it is a deployment variant of nlint_energy that needs no plan.
+ *   d = 2 or 3; n points per axis; precision NLINT_FP32 (float arrays) or NLINT_FP64;
+ *   rho_dev, u_dev: n^d values each on the current device; E_dev: one device double.
+ * It allocates nothing: its scratch is a 1 MiB array in the library's device memory, held on
+ * every device that loads the library until the process exits.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress) with the device current; make
+ * that first call before any stream capture.  Grids above 268435456 points (65536 partial
+ * sums of 4096 points) are rejected with NLINT_EINVAL.  Every call reuses the same scratch:
+ * calls that overlap on the GPU (other streams or host threads) race; serialise them.
+ * Summation order is fixed by the inputs (deterministic), partial sums compensated in FP64. */
+int nlint_energy_noalloc(int d, int64_t n, double L, int precision, const void *rho_dev,
+                         const void *u_dev, double lambda, double *E_dev, void *stream);
+
 /* Number of CUDA kernels this plan has launched so far, over all entry points (memsets and
  * copies are not counted).  Host-side counter; no synchronisation. */
 int nlint_launch_count(nlint_plan plan, int64_t *count);

@@ -28,7 +28,7 @@ EXPORTED = [
     "nlint_params_default", "nlint_plan_create", "nlint_plan_create_ex", "nlint_plan_info",
     "nlint_plan_destroy", "nlint_eval", "nlint_eval_energy", "nlint_energy", "nlint_eval_host",
     "nlint_type2", "nlint_type1", "nlint_plan_nodes", "nlint_set_stage_timing",
-    "nlint_stage_times", "nlint_launch_count", "nlint_last_error",
+    "nlint_stage_times", "nlint_launch_count", "nlint_energy_noalloc", "nlint_last_error",
 ]
 
 
@@ -90,6 +90,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.nlint_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float),
                                       ctypes.POINTER(ctypes.c_char_p), ci, ctypes.POINTER(ci)]
     lib.nlint_launch_count.argtypes = [vp, ctypes.POINTER(i64)]
+    lib.nlint_energy_noalloc.argtypes = [ci, i64, dbl, ci, vp, vp, dbl, vp, vp]
     lib.nlint_last_error.argtypes = []
     lib.nlint_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:

@@ -10,6 +10,9 @@
 
 namespace nlint {
 
+// Sets the calling thread's nlint_last_error message and returns `code`.
+int report_error(int code, const char *msg);
+
 // ---------------------------------------------------------------------------- FFT passes
 // One pass transforms every line along one axis of a 2D/3D array.  A "column" pass works
 // on an axis that is not contiguous (the batch index is contiguous); a "row" pass works on

@@ -21,6 +21,9 @@ static int fail(int code, const std::string &msg) {
     g_err = msg;
     return code;
 }
+// Records a failure message for nlint_last_error from other translation units.
+int report_error(int code, const char *msg) { return fail(code, msg); }
+
 static int cuda_fail(cudaError_t e, const char *where) {
     g_err = std::string(where) + ": " + cudaGetErrorString(e);
     return NLINT_ECUDA;
