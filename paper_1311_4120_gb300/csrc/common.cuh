@@ -32,6 +32,16 @@ __device__ __forceinline__ float2 cmuli(float2 a, int s) { return make_float2(-s
 __device__ __forceinline__ double2 cmuli(double2 a, int s) { return make_double2(-s * a.y, s * a.x); }
 template <typename T2> __device__ __forceinline__ T2 czero() { T2 r; r.x = 0; r.y = 0; return r; }
 
+// Compile-time loop: f(IntC<B>{}), f(IntC<B+1>{}), ..., f(IntC<E-1>{}).
+template <int V> struct IntC { static constexpr int value = V; };
+template <int B, int E, typename F>
+__device__ __forceinline__ void static_for(F &&f) {
+    if constexpr (B < E) {
+        f(IntC<B>{});
+        static_for<B + 1, E>(f);
+    }
+}
+
 // Neumaier-compensated FP64 accumulator: s + c carries the sum.
 struct KSum {
     double s, c;
@@ -79,6 +89,75 @@ __device__ __forceinline__ KSum ksum_block(KSum k, double *scratch) {
         ksum_warp(t);
     }
     return t;
+}
+
+// Energy accumulator of one thread: sum of u*rho products.  FP32 inputs: the exact product
+// p + e (p = u*rho rounded, e = fma(u, rho, -p)) is summed in FP32 with Kahan compensation, so
+// no FP64 instruction runs per grid point (FP64 throughput is a small fraction of FP32 on this
+// GPU); FP64 inputs: FP64 FMA into a running sum.
+template <typename T> struct EAcc;
+template <> struct EAcc<float> {
+    float s = 0.f, c = 0.f, e = 0.f;
+    __device__ __forceinline__ void add(float u, float r) {
+        const float p = u * r;
+        e += fmaf(u, r, -p);
+        const float y = p - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    // (hi, lo) with hi + lo the compensated sum
+    __device__ __forceinline__ float hi() const { return s; }
+    __device__ __forceinline__ float lo() const { return e - c; }
+};
+template <> struct EAcc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double u, double r) { s = fma(u, r, s); }
+};
+
+// Float-float addition (TwoSum): (a_hi + a_lo) + (b_hi + b_lo) to about 2^-44 relative.
+__device__ __forceinline__ void ff_add(float &hi, float &lo, float bhi, float blo) {
+    const float s = hi + bhi;
+    const float bb = s - hi;
+    const float err = (hi - (s - bb)) + (bhi - bb);
+    const float l = lo + blo + err;
+    hi = s + l;
+    lo = l - (hi - s);
+}
+
+// CTA sum of the threads' energy accumulators into one compensated FP64 partial (valid in
+// thread 0).  FP32: a float-float shuffle tree per warp, then one warp folds the warp sums in
+// FP64; FP64: the compensated FP64 tree.  The order is fixed, so results are reproducible.
+// `scratch` holds 2 doubles per warp; blockDim.x must be a multiple of 32.
+__device__ __forceinline__ double2 energy_block_sum(const EAcc<float> &a, double *scratch) {
+    float hi = a.hi(), lo = a.lo();
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const float ohi = __shfl_down_sync(0xffffffffu, hi, off);
+        const float olo = __shfl_down_sync(0xffffffffu, lo, off);
+        ff_add(hi, lo, ohi, olo);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) {
+        scratch[2 * wid] = (double)hi;
+        scratch[2 * wid + 1] = (double)lo;
+    }
+    __syncthreads();
+    KSum t;
+    t.init();
+    if (wid == 0) {
+        if (lane < nw) t.merge(scratch[2 * lane], scratch[2 * lane + 1]);
+        ksum_warp(t);
+    }
+    return make_double2(t.s, t.c);
+}
+__device__ __forceinline__ double2 energy_block_sum(const EAcc<double> &a, double *scratch) {
+    KSum k;
+    k.init();
+    k.add(a.s);
+    KSum t = ksum_block(k, scratch);
+    return make_double2(t.s, t.c);
 }
 
 }  // namespace nlint

@@ -1,0 +1,362 @@
+// Oversampled-grid FFT passes (eq. fft; steps a1/a2 and a6/a7/a8 of the path).
+//
+// A pass transforms every line along one axis of a 2D/3D array with one HBM read and one HBM
+// write.  The FFT length n is a template parameter (n = 2^a or 3*2^a, 16..2048), so the radix
+// schedule (radix 8 stages, then one radix 4 or 2, then one radix 3) and every stride are
+// compile-time constants.  Each thread owns VPT values of its line per stage: the first stage
+// reads its butterflies straight from global memory (coalesced across the lines of the CTA
+// in a column pass, along the line in a row pass), the middle stages exchange through shared
+// memory (Stockham autosort), and the last stage writes straight to global memory.
+//
+// Pruning: mode-centred inputs read only the N nonzero entries (mode m at FFT index m mod n);
+// Hermitian inputs read n/2+1 entries and form the rest by conjugate symmetry; half and mode
+// outputs write only the entries later stages use.  The first forward pass multiplies the
+// density by the deconvolution product (type-2 pre-correction); the last inverse pass applies
+// the type-1 post-correction, takes the real part and adds u*rho into an FP64 energy partial
+// per CTA (Remark 3.3).
+#pragma once
+#include "common.cuh"
+#include "internal.h"
+
+namespace nlint {
+
+// ------------------------------------------------------------------ compile-time schedule
+__host__ __device__ constexpr bool fft_has3(int n) { return n % 3 == 0; }
+__host__ __device__ constexpr int fft_log2(int m) { return m <= 1 ? 0 : 1 + fft_log2(m / 2); }
+__host__ __device__ constexpr int fft_pow2(int n) { return fft_log2(fft_has3(n) ? n / 3 : n); }
+__host__ __device__ constexpr int fft_eights(int n) { return fft_pow2(n) / 3; }
+__host__ __device__ constexpr int fft_tail(int n) {  // 4, 2 or 1 after the radix-8 stages
+    return fft_pow2(n) % 3 == 2 ? 4 : (fft_pow2(n) % 3 == 1 ? 2 : 1);
+}
+__host__ __device__ constexpr int fft_nstages(int n) {
+    return fft_eights(n) + (fft_tail(n) > 1 ? 1 : 0) + (fft_has3(n) ? 1 : 0);
+}
+__host__ __device__ constexpr int fft_radix(int n, int s) {
+    return s < fft_eights(n) ? 8 : (s == fft_eights(n) && fft_tail(n) > 1) ? fft_tail(n) : 3;
+}
+__host__ __device__ constexpr int fft_pprod(int n, int s) {  // product of the radices before s
+    return s == 0 ? 1 : fft_pprod(n, s - 1) * fft_radix(n, s - 1);
+}
+__host__ __device__ constexpr int fft_vpt(int n) { return fft_has3(n) ? 24 : (n <= 512 ? 16 : 32); }
+__host__ __device__ constexpr int fft_tpl(int n) { return n / fft_vpt(n); }  // a power of 2
+__host__ __device__ constexpr int fft_row_ld(int n) { return n + n / 16; }  // padded row line
+// Lines per CTA.  Column pass: 128-byte rows (16 FP32 / 8 FP64 complex), fewer for the
+// longest lines (shared memory <= 192 KB), at least one warp.
+// Row pass: about 512 threads, at most 96 KB of shared memory, whole warps where possible.
+__host__ __device__ constexpr int fft_pow2_floor(int m) { return m < 2 ? 1 : 2 * fft_pow2_floor(m / 2); }
+__host__ __device__ constexpr int fft_col_b_raw(int n, int cs) {  // <= 192 KB of shared memory
+    return (128 / cs) < fft_pow2_floor(196608 / (n * cs)) ? 128 / cs : fft_pow2_floor(196608 / (n * cs));
+}
+__host__ __device__ constexpr int fft_col_b(int n, int cs) {
+    return fft_col_b_raw(n, cs) * fft_tpl(n) >= 32 ? fft_col_b_raw(n, cs) : 32 / fft_tpl(n);
+}
+__host__ __device__ constexpr int fft_row_b_raw(int n, int cs) {
+    return (512 / fft_tpl(n)) < (96 * 1024) / (fft_row_ld(n) * cs) ? 512 / fft_tpl(n)
+                                                                    : (96 * 1024) / (fft_row_ld(n) * cs);
+}
+__host__ __device__ constexpr int fft_row_b(int n, int cs) {
+    return fft_row_b_raw(n, cs) < 1 ? 1
+         : (fft_tpl(n) < 32 && fft_row_b_raw(n, cs) >= 32 / fft_tpl(n))
+               ? fft_row_b_raw(n, cs) / (32 / fft_tpl(n)) * (32 / fft_tpl(n))
+               : fft_row_b_raw(n, cs);
+}
+
+template <typename T, int NF>
+struct FftCfg {
+    static constexpr int CS = (int)(2 * sizeof(T));
+    static constexpr int TPL = fft_tpl(NF);  // threads per line
+    static constexpr int NST = fft_nstages(NF);
+    static constexpr int COL_B = fft_col_b(NF, CS);
+    static constexpr int ROW_B = fft_row_b(NF, CS);
+    static constexpr int ROW_LD = fft_row_ld(NF);
+    static constexpr int threads(bool row) { return (row ? ROW_B : COL_B) * TPL; }
+};
+
+// ------------------------------------------------------------------ butterflies
+template <typename T, int R>
+__device__ __forceinline__ void dft_small(cx_t<T> *v, int sign) {
+    using T2 = cx_t<T>;
+    if constexpr (R == 2) {
+        T2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    } else if constexpr (R == 3) {
+        const T c = T(-0.5);
+        const T s = T(sign) * T(0.86602540378443864676);  // sign * sqrt(3)/2
+        T2 a = v[0], b = v[1], d = v[2];
+        T2 sum = cadd(b, d), dif = csub(b, d);
+        T2 m = cadd(a, cscale(sum, c));
+        T2 rot = cmake<T2>(-s * dif.y, s * dif.x);  // i s (b - d)
+        v[0] = cadd(a, sum);
+        v[1] = cadd(m, rot);
+        v[2] = csub(m, rot);
+    } else if constexpr (R == 4) {
+        T2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+        T2 t2 = cadd(v[1], v[3]), t3 = cmuli(csub(v[1], v[3]), sign);
+        v[0] = cadd(t0, t2);
+        v[2] = csub(t0, t2);
+        v[1] = cadd(t1, t3);
+        v[3] = csub(t1, t3);
+    } else if constexpr (R == 8) {
+        T2 e[4] = {v[0], v[2], v[4], v[6]};
+        T2 o[4] = {v[1], v[3], v[5], v[7]};
+        dft_small<T, 4>(e, sign);
+        dft_small<T, 4>(o, sign);
+        const T h = T(0.70710678118654752440);
+        T2 o1 = cmul(o[1], cmake<T2>(h, T(sign) * h));  // W8^k = exp(sign i pi k / 4)
+        T2 o2 = cmuli(o[2], sign);
+        T2 o3 = cmul(o[3], cmake<T2>(-h, T(sign) * h));
+        v[0] = cadd(e[0], o[0]);
+        v[4] = csub(e[0], o[0]);
+        v[1] = cadd(e[1], o1);
+        v[5] = csub(e[1], o1);
+        v[2] = cadd(e[2], o2);
+        v[6] = csub(e[2], o2);
+        v[3] = cadd(e[3], o3);
+        v[7] = csub(e[3], o3);
+    }
+}
+
+// ------------------------------------------------------------------ line input
+// Per-line context: where its input and output live and how its entries map to FFT indices.
+template <typename T>
+struct LineIO {
+    using T2 = cx_t<T>;
+    int n, h, kind;
+    const T *fac;
+    bool valid;
+    int64_t in_base, out_base;  // element offsets of entry 0
+    int64_t in_st, out_st;      // element stride along the line
+    T bfac;                     // deconvolution product over the other axes
+    int64_t mirror_base;        // fold: the mirrored line of H+, or -1
+
+    // FFT-index entry e of the input line (zero outside the stored modes)
+    __device__ __forceinline__ T2 load(int e, const void *vin) const {
+        T2 v = czero<T2>();
+        if (!valid) return v;
+        switch (kind) {
+            case IN_REAL_MODES:
+            case IN_CPLX_MODES: {
+                const int m = e < n / 2 ? e : e - n;
+                if (m >= -h && m < h) {
+                    const int a = m + h;
+                    if (kind == IN_REAL_MODES) {
+                        v.x = reinterpret_cast<const T *>(vin)[in_base + a * in_st] * fac[a] * bfac;
+                    } else {
+                        v = reinterpret_cast<const T2 *>(vin)[in_base + a * in_st];
+                    }
+                }
+                break;
+            }
+            case IN_CPLX_FULL:
+                v = reinterpret_cast<const T2 *>(vin)[in_base + e * in_st];
+                break;
+            case IN_CPLX_HERM:
+                v = (e <= n / 2) ? reinterpret_cast<const T2 *>(vin)[in_base + e * in_st]
+                                 : cconj(reinterpret_cast<const T2 *>(vin)[in_base + (n - e) * in_st]);
+                break;
+            default: {  // IN_CPLX_FOLD: H[l] = H+[l] + conj(H+[-l])
+                const T2 *in = reinterpret_cast<const T2 *>(vin);
+                v = in[in_base + e];
+                if (mirror_base >= 0) v = cadd(v, cconj(in[mirror_base + (e == 0 ? 0 : n - e)]));
+            }
+        }
+        return v;
+    }
+};
+
+// ------------------------------------------------------------------ the pass kernel
+// ROW = false: column pass, the CTA's COL_B lines are adjacent in memory (128-byte rows);
+// ROW = true: row pass, each line is contiguous (ROW_B lines per CTA).
+template <typename T, int NF, bool ROW>
+__global__ void __launch_bounds__(FftCfg<T, NF>::threads(ROW)) fft_pass_kernel(
+    PassDesc P, const void *__restrict__ vin, void *__restrict__ vout, const cx_t<T> *__restrict__ tw) {
+    using T2 = cx_t<T>;
+    using C = FftCfg<T, NF>;
+    constexpr int B = ROW ? C::ROW_B : C::COL_B;
+    constexpr int TPL = C::TPL;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T2 *buf = reinterpret_cast<T2 *>(smem_raw);
+
+    const int ll = ROW ? (int)threadIdx.x / TPL : (int)threadIdx.x % B;  // line within the CTA
+    const int t = ROW ? (int)threadIdx.x % TPL : (int)threadIdx.x / B;   // thread within the line
+    const int sign = P.sign;
+    const int N = P.N, h = N / 2;
+
+    // ---- line context
+    LineIO<T> io;
+    io.n = P.n;
+    io.h = h;
+    io.kind = P.in_kind;
+    io.fac = reinterpret_cast<const T *>(P.fac);
+    io.mirror_base = -1;
+    io.bfac = T(1);
+    if (!ROW) {
+        const int64_t tiles = (P.I + B - 1) / B;
+        const int64_t o = blockIdx.x / tiles;
+        const int64_t i = (blockIdx.x % tiles) * B + ll;
+        io.valid = i < P.I;
+        io.in_base = o * P.in_so + i;
+        io.out_base = o * P.out_so + i;
+        io.in_st = P.in_sa;
+        io.out_st = P.out_sa;
+        if (io.valid && (P.in_kind == IN_REAL_MODES || P.out_kind == OUT_REAL_MODES)) {
+            const T *fac = reinterpret_cast<const T *>(P.fac);
+            io.bfac = (P.dim == 3) ? fac[i / N] * fac[i % N] : fac[i];
+        }
+    } else {
+        const int64_t q = (int64_t)blockIdx.x * B + ll;
+        io.valid = q < P.I;
+        io.in_st = 1;
+        io.out_st = 1;
+        io.out_base = q * P.out_so;
+        if (P.in_kind == IN_CPLX_FOLD) {
+            const int n = P.n;
+            const int64_t lz = q / P.fold_rows_per_plane, ly = q % P.fold_rows_per_plane;
+            io.in_base = (lz + P.fold_pad) * P.fold_plane + ly * n;
+            if (lz <= P.fold_pad || lz >= n / 2 - P.fold_pad) {
+                const int64_t mz = (lz <= P.fold_pad) ? -lz : n - lz;
+                const int64_t my = (P.fold_rows_per_plane == 1 || ly == 0) ? 0 : n - ly;
+                io.mirror_base = (mz + P.fold_pad) * P.fold_plane + my * n;
+            }
+        } else {
+            io.in_base = q * P.in_so;
+        }
+    }
+
+    auto sidx = [&](int e) -> int { return ROW ? ll * C::ROW_LD + e + (e >> 4) : e * B + ll; };
+
+    // ---- stage 0: global -> registers -> DFT -> shared
+    {
+        constexpr int R = fft_radix(NF, 0);
+        constexpr int NB = NF / R;
+        constexpr int MB = NB / TPL;
+        T2 v[MB][R];
+#pragma unroll
+        for (int b = 0; b < MB; b++)
+#pragma unroll
+            for (int r = 0; r < R; r++) v[b][r] = io.load(t + b * TPL + r * NB, vin);
+#pragma unroll
+        for (int b = 0; b < MB; b++) {
+            dft_small<T, R>(v[b], sign);
+            const int i = t + b * TPL;
+#pragma unroll
+            for (int r = 0; r < R; r++) buf[sidx(i * R + r)] = v[b][r];
+        }
+    }
+    __syncthreads();
+
+    // ---- stages 1 .. NST-1; the last one writes the output
+    EAcc<T> eacc;  // this thread's u*rho products
+    auto stage = [&](auto S_) {
+        constexpr int S = decltype(S_)::value;
+        constexpr int R = fft_radix(NF, S);
+        constexpr int NB = NF / R;
+        constexpr int MB = NB / TPL;
+        constexpr int PP = fft_pprod(NF, S);
+        constexpr int STEP = NF / (PP * R);
+        constexpr bool LAST = (S == C::NST - 1);
+        T2 v[MB][R];
+#pragma unroll
+        for (int b = 0; b < MB; b++)
+#pragma unroll
+            for (int r = 0; r < R; r++) v[b][r] = buf[sidx(t + b * TPL + r * NB)];
+        if constexpr (!LAST) __syncthreads();
+#pragma unroll
+        for (int b = 0; b < MB; b++) {
+            const int i = t + b * TPL;
+            const int k = i % PP;
+#pragma unroll
+            for (int r = 1; r < R; r++) {
+                T2 w = tw[r * k * STEP];
+                if (sign > 0) w = cconj(w);
+                v[b][r] = cmul(v[b][r], w);
+            }
+            dft_small<T, R>(v[b], sign);
+            if constexpr (!LAST) {
+                const int j = (i - k) * R + k;
+#pragma unroll
+                for (int r = 0; r < R; r++) buf[sidx(j + r * PP)] = v[b][r];
+            } else if (io.valid) {
+                // output entry e = i + r PP (here PP R = n and k = i)
+#pragma unroll
+                for (int r = 0; r < R; r++) {
+                    const int e = i + r * PP;
+                    const T2 x = v[b][r];
+                    switch (P.out_kind) {
+                        case OUT_CPLX_FULL:
+                            reinterpret_cast<T2 *>(vout)[io.out_base + e * io.out_st] = x;
+                            break;
+                        case OUT_CPLX_HALF:
+                            if (e <= NF / 2) reinterpret_cast<T2 *>(vout)[io.out_base + e * io.out_st] = x;
+                            break;
+                        case OUT_CPLX_MODES: {
+                            const int m = e < NF / 2 ? e : e - NF;
+                            if (m >= -h && m < h)
+                                reinterpret_cast<T2 *>(vout)[io.out_base + (m + h) * io.out_st] = x;
+                            break;
+                        }
+                        default: {  // OUT_REAL_MODES (+ energy)
+                            const int m = e < NF / 2 ? e : e - NF;
+                            if (m >= -h && m < h) {
+                                const int a = m + h;
+                                const T *fac = reinterpret_cast<const T *>(P.fac);
+                                const int64_t idx = io.out_base + a * io.out_st;
+                                const T val = x.x * fac[a] * io.bfac;
+                                reinterpret_cast<T *>(vout)[idx] = val;
+                                if (P.rho)
+                                    eacc.add(val, reinterpret_cast<const T *>(P.rho)[idx]);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        if constexpr (!LAST) __syncthreads();
+    };
+    static_for<1, C::NST>(stage);
+
+    if (P.out_kind == OUT_REAL_MODES && P.partials) {
+        __syncthreads();  // the shared buffer becomes the reduction scratch
+        const double2 tot = energy_block_sum(eacc, reinterpret_cast<double *>(smem_raw));
+        if (threadIdx.x == 0) P.partials[blockIdx.x] = tot;
+    }
+}
+
+// ------------------------------------------------------------------ launchers
+template <typename T, int NF, bool ROW>
+cudaError_t launch_nf(const PassDesc &p, const void *in, void *out, const void *tw, cudaStream_t s) {
+    const size_t smem = pass_smem(p, sizeof(T) == 4 ? NLINT_FP32 : NLINT_FP64);
+    cudaError_t e = cudaFuncSetAttribute(fft_pass_kernel<T, NF, ROW>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t nb = pass_blocks(p, ROW);
+    if (nb == 0) return cudaSuccess;
+    fft_pass_kernel<T, NF, ROW><<<(unsigned)nb, FftCfg<T, NF>::threads(ROW), smem, s>>>(
+        p, in, out, reinterpret_cast<const cx_t<T> *>(tw));
+    return cudaGetLastError();
+}
+
+template <typename T, bool ROW>
+cudaError_t launch_pass_impl(const PassDesc &p, const void *in, void *out, const void *tw, cudaStream_t s) {
+    switch (p.n) {
+        case 16: return launch_nf<T, 16, ROW>(p, in, out, tw, s);
+        case 24: return launch_nf<T, 24, ROW>(p, in, out, tw, s);
+        case 32: return launch_nf<T, 32, ROW>(p, in, out, tw, s);
+        case 48: return launch_nf<T, 48, ROW>(p, in, out, tw, s);
+        case 64: return launch_nf<T, 64, ROW>(p, in, out, tw, s);
+        case 96: return launch_nf<T, 96, ROW>(p, in, out, tw, s);
+        case 128: return launch_nf<T, 128, ROW>(p, in, out, tw, s);
+        case 192: return launch_nf<T, 192, ROW>(p, in, out, tw, s);
+        case 256: return launch_nf<T, 256, ROW>(p, in, out, tw, s);
+        case 384: return launch_nf<T, 384, ROW>(p, in, out, tw, s);
+        case 512: return launch_nf<T, 512, ROW>(p, in, out, tw, s);
+        case 768: return launch_nf<T, 768, ROW>(p, in, out, tw, s);
+        case 1024: return launch_nf<T, 1024, ROW>(p, in, out, tw, s);
+        case 1536: return launch_nf<T, 1536, ROW>(p, in, out, tw, s);
+        case 2048: return launch_nf<T, 2048, ROW>(p, in, out, tw, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace nlint

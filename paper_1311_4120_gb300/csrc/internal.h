@@ -54,12 +54,17 @@ struct PassDesc {
 };
 
 void make_radix(int n, PassDesc &p);
+bool fft_size_supported(int n);   // n = 2^a or 3*2^a, 16 <= n <= 2048
+int fft_next_size(int64_t m);     // smallest supported size >= m, or -1
 int64_t pass_blocks(const PassDesc &p, bool row);
 int pass_threads(const PassDesc &p);
 size_t pass_smem(const PassDesc &p, int prec);
 void config_pass(PassDesc &p, int prec, bool row);
 bool pass_fits(const PassDesc &p);
 
+template <typename T, bool ROW>
+cudaError_t launch_pass_impl(const PassDesc &p, const void *in, void *out, const void *tw,
+                             cudaStream_t s);
 template <typename T>
 cudaError_t launch_colpass(const PassDesc &p, const void *in, void *out, const void *tw,
                            cudaStream_t s);
@@ -90,7 +95,13 @@ struct NodeDesc {
     int ncrowd;          // crowded bins (FP32 plans): their tiles are summed in FP64
     double2 *crowd;      // ncrowd tiles of complex doubles
     const int32_t *crowd_bin;  // bin of each crowd slot
+    const int16_t *pair_order; // per pass and lane: stencil column (q_a << 8 | q_b) or -1
 };
+
+// Deals the w*w stencil columns (q_a, q_b) of a node to passes of 32 lanes so that, within a
+// pass, the tile offsets q_a * row + q_b fall in distinct shared-memory banks where possible
+// (`banks` = 32 for 4-byte, 16 for 8-byte elements).  Returns passes * 32 entries.
+std::vector<int16_t> build_pair_order(int w, int row, int banks);
 
 // Bin extent (stencil-origin cells) along array axis `axis`; the same rule is compiled into
 // the kernels, so a plan's bins always match the tile geometry of its kernels.  3D: 8^3 bins,
@@ -121,6 +132,7 @@ template <typename T, int D>
 cudaError_t launch_spread_d(const NodeDesc &nd, const void *c_in, void *Hext, cudaStream_t s);
 template <typename T, int D>
 cudaError_t launch_crowd_merge_d(const NodeDesc &nd, void *Hext, cudaStream_t s);
+
 template <typename T>
 cudaError_t launch_scatter_canonical(int64_t M, const void *vals, const int32_t *perm,
                                      const int32_t *mirror, double scale, void *out,

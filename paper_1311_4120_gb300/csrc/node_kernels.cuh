@@ -16,12 +16,15 @@
 // bin's tile (bin + w - 1 cells per axis) in shared memory as separate real and imaginary
 // planes.  A warp takes one node at a time; in 3D its lanes own (axis 1, axis 2) stencil
 // columns and run along axis 0 with the axis-0 kernel values in registers, in 2D they own
-// stencil cells.  Interpolation sums the lanes with a shuffle tree; spreading adds into the
+// stencil cells.  The columns are dealt to lanes by a plan-made table so that the 32 lanes of
+// a pass hit distinct shared-memory banks.  Interpolation sums the lanes with a shuffle tree; spreading adds into the
 // tile with shared atomics (the lanes of one node touch distinct cells) and then adds the
 // tile's nonzero cells to H+ with global atomics, or, for crowded bins, to an FP64 tile.
 #pragma once
 #include "common.cuh"
 #include "internal.h"
+
+#include <climits>
 
 namespace nlint {
 
@@ -68,19 +71,37 @@ __device__ __forceinline__ cx_t<T> fetch_half(const cx_t<T> *__restrict__ G, int
     return cconj(G[(int64_t)mz * n + wrapn(-l1, n)]);
 }
 
-// Kernel values of one node into ker[a*MAXW + q] = phi((q - frac_a) / (w/2)), stencil cell q
-// of axis a, computed by the lanes of the warp (D*W values, some lanes take two).
+// Per-lane node data of one node: stencil origin relative to the bin, and the fractional
+// offsets this lane needs to compute its share of the node's kernel values.
 template <typename T, int D, int W>
-__device__ __forceinline__ void warp_kernel_values(const NodeDesc &nd, int64_t j, int lane, T *ker) {
-    const T inv_half = T(2) / T(W);
-    const T beta = T(nd.beta);
+struct NodeRec {
+    static constexpr int KV = (D * W + 31) / 32;  // kernel values per lane
+    int r0, r1, r2;
+    T fr[KV];
+    __device__ __forceinline__ void load(const NodeDesc &nd, int64_t j, int lane, int4 bo) {
+        const int64_t M = nd.M;
+        r0 = nd.l0[j] - bo.x;
+        r1 = nd.l0[M + j] - bo.y;
+        r2 = (D == 3) ? nd.l0[2 * M + j] - bo.z : 0;
 #pragma unroll
-    for (int t0 = 0; t0 < D * W; t0 += 32) {
-        const int t = t0 + lane;
+        for (int v = 0; v < KV; v++) {
+            const int t = lane + 32 * v;
+            fr[v] = (t < D * W) ? reinterpret_cast<const T *>(nd.frac)[(t / W) * M + j] : T(0);
+        }
+    }
+};
+
+// Kernel values of one node into the warp's table ker[a*MAXW + q] = phi((q - frac_a)/(w/2)),
+// stencil cell q of axis a; lane t computes entry t (and t + 32 when D*W > 32).
+template <typename T, int D, int W>
+__device__ __forceinline__ void warp_kernel_values(const NodeRec<T, D, W> &nr, T beta, int lane, T *ker) {
+    const T inv_half = T(2) / T(W);
+#pragma unroll
+    for (int v = 0; v < NodeRec<T, D, W>::KV; v++) {
+        const int t = lane + 32 * v;
         if (t < D * W) {
             const int a = t / W, q = t - a * W;
-            const T fr = reinterpret_cast<const T *>(nd.frac)[a * nd.M + j];
-            ker[a * MAXW + q] = es_kernel<T>((T(q) - fr) * inv_half, beta);
+            ker[a * MAXW + q] = es_kernel<T>((T(q) - nr.fr[v]) * inv_half, beta);
         }
     }
 }
@@ -94,6 +115,41 @@ __device__ __forceinline__ void cell_coords(int cell, int &a0, int &a1, int &a2)
     a2 = rem - a1 * G_::T2;
 }
 
+// Tile offset of stencil column (qa, qb) for the origin (r0, r1, r2): axis-0 run start.
+template <typename G_, int D>
+__device__ __forceinline__ int col_index(int r0, int r1, int r2, int qa, int qb) {
+    return (D == 3) ? (r0 * G_::T1 + r1 + qa) * G_::T2 + r2 + qb : (r0 + qa) * G_::T1 + r1 + qb;
+}
+
+// Each warp owns a contiguous run of its subproblem's nodes.
+__device__ __forceinline__ void warp_chunk(int4 sb, int wid, int nw, int &ja, int &jb) {
+    ja = sb.x + (int)(((int64_t)sb.y * wid) / nw);
+    jb = sb.x + (int)(((int64_t)sb.y * (wid + 1)) / nw);
+}
+
+// Fixed-point accumulation of the spreading tile.  Shared-memory floating-point atomics are
+// several times slower than integer ones on this GPU, so each CTA adds integer multiples of
+// 1/S: S = 2^(E - ceil(log2 B)) with B >= max(sum_j |Re c_j|, sum_j |Im c_j|) over the
+// subproblem (every cell sum and every contribution is at most B, since phi <= 1), E = 29 for
+// FP32 (int32 cells) and 61 for FP64 (int64 cells), so no cell can overflow.  Each contribution is rounded to 1/S <= 2^-E B
+// (FP32: 2^-29 B, finer than FP32 rounding of the largest cells); the integer sums are exact,
+// so a tile does not depend on the order of its additions.
+template <typename T> struct FixAcc;
+template <> struct FixAcc<float> {
+    using A = int;
+    static constexpr int E = 29, MAXEXP = 126;
+    __device__ __forceinline__ static A quant(float v) { return __float2int_rn(v); }
+    __device__ __forceinline__ static void add(A *p, A v) { atomicAdd(p, v); }
+};
+template <> struct FixAcc<double> {
+    using A = long long;
+    static constexpr int E = 61, MAXEXP = 1000;
+    __device__ __forceinline__ static A quant(double v) { return __double2ll_rn(v); }
+    __device__ __forceinline__ static void add(A *p, A v) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)v);
+    }
+};
+
 template <typename T, int D, int W>
 __global__ void __launch_bounds__(SUB_THREADS) interp_sub_kernel(NodeDesc nd,
                                                                 const cx_t<T> *__restrict__ G,
@@ -101,6 +157,7 @@ __global__ void __launch_bounds__(SUB_THREADS) interp_sub_kernel(NodeDesc nd,
                                                                 int apply_W) {
     using T2 = cx_t<T>;
     using G_ = Geo<T, D, W>;
+    constexpr int PASSES = G_::PASSES, L = (D == 3) ? W : 1, PLANE = G_::T1 * G_::T2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *tr = reinterpret_cast<T *>(smem_raw);
     T *ti = tr + G_::NCELL;
@@ -109,6 +166,10 @@ __global__ void __launch_bounds__(SUB_THREADS) interp_sub_kernel(NodeDesc nd,
     const int4 sb = nd.subs[blockIdx.x];
     const int4 bo = nd.bins[sb.z];
     const int n = nd.n;
+    const T beta = T(nd.beta);
+    int pairs[PASSES];  // this lane's stencil columns, one per pass (-1: idle)
+#pragma unroll
+    for (int ps = 0; ps < PASSES; ps++) pairs[ps] = nd.pair_order[ps * 32 + lane];
 
     // stage the tile; the common case (axis-0 planes inside the stored half) needs no mirror
     const bool inside = bo.x >= 0 && bo.x + G_::T0 - 1 <= n / 2;
@@ -127,46 +188,34 @@ __global__ void __launch_bounds__(SUB_THREADS) interp_sub_kernel(NodeDesc nd,
     }
     __syncthreads();
 
-    const int64_t M = nd.M;
-    for (int i = wid; i < sb.y; i += nw) {
-        const int64_t j = (int64_t)sb.x + i;
-        warp_kernel_values<T, D, W>(nd, j, lane, ker);
-        const int r0 = nd.l0[j] - bo.x, r1 = nd.l0[M + j] - bo.y;
-        const int r2 = (D == 3) ? nd.l0[2 * M + j] - bo.z : 0;
+    int ja, jb;
+    warp_chunk(sb, wid, nw, ja, jb);
+    NodeRec<T, D, W> cur, nxt;
+    if (ja < jb) cur.load(nd, ja, lane, bo);
+    for (int j = ja; j < jb; j++) {
+        if (j + 1 < jb) nxt.load(nd, j + 1, lane, bo);  // prefetch the next node
+        const T Wj = apply_W ? reinterpret_cast<const T *>(nd.W)[j] : T(1);
+        warp_kernel_values<T, D, W>(cur, beta, lane, ker);
         __syncwarp();
         T accr = T(0), acci = T(0);
-        if constexpr (D == 3) {
-            T k0[W];
+        T k0[L];
 #pragma unroll
-            for (int q = 0; q < W; q++) k0[q] = ker[q];
+        for (int q = 0; q < L; q++) k0[q] = (D == 3) ? ker[q] : T(1);
 #pragma unroll
-            for (int ps = 0; ps < G_::PASSES; ps++) {
-                const int p = lane + 32 * ps;
-                if (p < G_::PAIRS) {
-                    const int q1 = p / W, q2 = p - q1 * W;
-                    const int idx = (r0 * G_::T1 + r1 + q1) * G_::T2 + r2 + q2;
-                    T sr = T(0), si = T(0);
+        for (int ps = 0; ps < PASSES; ps++) {
+            const int pq = pairs[ps];
+            if (pq >= 0) {
+                const int qa = pq >> 8, qb = pq & 255;
+                const T kab = (D == 3) ? ker[MAXW + qa] * ker[2 * MAXW + qb] : ker[qa] * ker[MAXW + qb];
+                const int idx = col_index<G_, D>(cur.r0, cur.r1, cur.r2, qa, qb);
+                T sr = T(0), si = T(0);
 #pragma unroll
-                    for (int q0 = 0; q0 < W; q0++) {
-                        sr += k0[q0] * tr[idx + q0 * G_::T1 * G_::T2];
-                        si += k0[q0] * ti[idx + q0 * G_::T1 * G_::T2];
-                    }
-                    const T k12 = ker[MAXW + q1] * ker[2 * MAXW + q2];
-                    accr += k12 * sr;
-                    acci += k12 * si;
+                for (int q0 = 0; q0 < L; q0++) {
+                    sr += k0[q0] * tr[idx + q0 * PLANE];
+                    si += k0[q0] * ti[idx + q0 * PLANE];
                 }
-            }
-        } else {
-#pragma unroll
-            for (int ps = 0; ps < G_::PASSES; ps++) {
-                const int p = lane + 32 * ps;
-                if (p < G_::PAIRS) {
-                    const int q0 = p / W, q1 = p - q0 * W;
-                    const int idx = (r0 + q0) * G_::T1 + r1 + q1;
-                    const T k = ker[q0] * ker[MAXW + q1];
-                    accr += k * tr[idx];
-                    acci += k * ti[idx];
-                }
+                accr += kab * sr;
+                acci += kab * si;
             }
         }
 #pragma unroll
@@ -174,11 +223,9 @@ __global__ void __launch_bounds__(SUB_THREADS) interp_sub_kernel(NodeDesc nd,
             accr += __shfl_xor_sync(0xffffffffu, accr, off);
             acci += __shfl_xor_sync(0xffffffffu, acci, off);
         }
-        if (lane == 0) {
-            const T sc = apply_W ? reinterpret_cast<const T *>(nd.W)[j] : T(1);
-            c_out[j] = cmake<T2>(accr * sc, acci * sc);
-        }
+        if (lane == 0) c_out[j] = cmake<T2>(accr * Wj, acci * Wj);
         __syncwarp();
+        cur = nxt;
     }
 }
 
@@ -196,72 +243,106 @@ __global__ void __launch_bounds__(SUB_THREADS) spread_sub_kernel(NodeDesc nd,
                                                                 cx_t<T> *__restrict__ H) {
     using T2 = cx_t<T>;
     using G_ = Geo<T, D, W>;
+    using F = FixAcc<T>;
+    using A = typename F::A;
+    constexpr int PASSES = G_::PASSES, L = (D == 3) ? W : 1, PLANE = G_::T1 * G_::T2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *tr = reinterpret_cast<T *>(smem_raw);
-    T *ti = tr + G_::NCELL;
+    A *tr = reinterpret_cast<A *>(smem_raw);
+    A *ti = tr + G_::NCELL;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    T *ker = ti + G_::NCELL + wid * 3 * MAXW;
+    T *ker = reinterpret_cast<T *>(ti + G_::NCELL) + wid * 3 * MAXW;
     const int4 sb = nd.subs[blockIdx.x];
     const int4 bo = nd.bins[sb.z];
     const int n = nd.n, pad = nd.pad;
+    const T beta = T(nd.beta);
+    int pairs[PASSES];
+#pragma unroll
+    for (int ps = 0; ps < PASSES; ps++) pairs[ps] = nd.pair_order[ps * 32 + lane];
 
+    // bound B = max(sum |Re c_j|, sum |Im c_j|) over the subproblem, while the tile is cleared
+    T bre = T(0), bim = T(0);
+    for (int i = threadIdx.x; i < sb.y; i += blockDim.x) {
+        const T2 v = c_in[sb.x + i];
+        bre += fabs(v.x);
+        bim += fabs(v.y);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        bre += __shfl_xor_sync(0xffffffffu, bre, off);
+        bim += __shfl_xor_sync(0xffffffffu, bim, off);
+    }
     for (int cell = threadIdx.x; cell < G_::NCELL; cell += blockDim.x) {
-        tr[cell] = T(0);
-        ti[cell] = T(0);
+        tr[cell] = 0;
+        ti[cell] = 0;
+    }
+    if (lane == 0) {
+        ker[0] = bre;  // the warp's kernel table is free until the node loop
+        ker[1] = bim;
     }
     __syncthreads();
+    T sre = T(0), sim = T(0);
+    for (int q = 0; q < nw; q++) {
+        const T *kq = reinterpret_cast<T *>(ti + G_::NCELL) + q * 3 * MAXW;
+        sre += kq[0];
+        sim += kq[1];
+    }
+    // B to within rounding (<= 1024 terms: a relative 1e-4 in FP32); the headroom of 2^E below
+    // the integer range (4x) absorbs it
+    const T bound = fmax(sre, sim);
+    if (!(bound > T(0))) return;  // every c_j of the subproblem is zero: nothing to add
+    int ex = F::E - ilogb(bound) - 1;  // S = 2^ex, S * bound <= 2^E
+    if (ex > F::MAXEXP) ex = F::MAXEXP;   // tiny bounds: keep S finite (cells stay < 2^E)
+    const T S = (T)ldexp(1.0, ex), inv_s = (T)ldexp(1.0, -ex);
+    __syncthreads();  // every warp has read the bound before the tables are overwritten
 
-    const int64_t M = nd.M;
-    for (int i = wid; i < sb.y; i += nw) {
-        const int64_t j = (int64_t)sb.x + i;
-        warp_kernel_values<T, D, W>(nd, j, lane, ker);
-        const int r0 = nd.l0[j] - bo.x, r1 = nd.l0[M + j] - bo.y;
-        const int r2 = (D == 3) ? nd.l0[2 * M + j] - bo.z : 0;
-        const T2 c = c_in[j];
+    int ja, jb;
+    warp_chunk(sb, wid, nw, ja, jb);
+    NodeRec<T, D, W> cur, nxt;
+    T2 c = czero<T2>(), cn = czero<T2>();
+    if (ja < jb) {
+        cur.load(nd, ja, lane, bo);
+        c = c_in[ja];
+    }
+    for (int j = ja; j < jb; j++) {
+        if (j + 1 < jb) {  // prefetch the next node
+            nxt.load(nd, j + 1, lane, bo);
+            cn = c_in[j + 1];
+        }
+        warp_kernel_values<T, D, W>(cur, beta, lane, ker);
         __syncwarp();
-        if constexpr (D == 3) {
-            T k0[W];
+        T k0[L];
 #pragma unroll
-            for (int q = 0; q < W; q++) k0[q] = ker[q];
+        for (int q = 0; q < L; q++) k0[q] = (D == 3) ? ker[q] : T(1);
+        const T csr = c.x * S, csi = c.y * S;
 #pragma unroll
-            for (int ps = 0; ps < G_::PASSES; ps++) {
-                const int p = lane + 32 * ps;
-                if (p < G_::PAIRS) {
-                    const int q1 = p / W, q2 = p - q1 * W;
-                    const T k12 = ker[MAXW + q1] * ker[2 * MAXW + q2];
-                    const T cr = c.x * k12, ci = c.y * k12;
-                    const int idx = (r0 * G_::T1 + r1 + q1) * G_::T2 + r2 + q2;
+        for (int ps = 0; ps < PASSES; ps++) {
+            const int pq = pairs[ps];
+            if (pq >= 0) {
+                const int qa = pq >> 8, qb = pq & 255;
+                const T kab = (D == 3) ? ker[MAXW + qa] * ker[2 * MAXW + qb] : ker[qa] * ker[MAXW + qb];
+                const T cr = csr * kab, ci = csi * kab;
+                const int idx = col_index<G_, D>(cur.r0, cur.r1, cur.r2, qa, qb);
 #pragma unroll
-                    for (int q0 = 0; q0 < W; q0++) {
-                        atomicAdd(tr + idx + q0 * G_::T1 * G_::T2, cr * k0[q0]);
-                        atomicAdd(ti + idx + q0 * G_::T1 * G_::T2, ci * k0[q0]);
-                    }
-                }
-            }
-        } else {
-#pragma unroll
-            for (int ps = 0; ps < G_::PASSES; ps++) {
-                const int p = lane + 32 * ps;
-                if (p < G_::PAIRS) {
-                    const int q0 = p / W, q1 = p - q0 * W;
-                    const int idx = (r0 + q0) * G_::T1 + r1 + q1;
-                    const T k = ker[q0] * ker[MAXW + q1];
-                    atomicAdd(tr + idx, c.x * k);
-                    atomicAdd(ti + idx, c.y * k);
+                for (int q0 = 0; q0 < L; q0++) {
+                    F::add(tr + idx + q0 * PLANE, F::quant(cr * k0[q0]));
+                    F::add(ti + idx + q0 * PLANE, F::quant(ci * k0[q0]));
                 }
             }
         }
         __syncwarp();
+        cur = nxt;
+        c = cn;
     }
     __syncthreads();
 
     const int slot = bo.w;
     const int nplanes = n / 2 + 1 + 2 * pad;
     for (int cell = threadIdx.x; cell < G_::NCELL; cell += blockDim.x) {
-        const T vr = tr[cell], vi = ti[cell];
-        if (vr == T(0) && vi == T(0)) continue;
-        if (slot >= 0) {
-            atomic_add_cx(nd.crowd + (int64_t)slot * G_::NCELL + cell, (double)vr, (double)vi);
+        const A qr = tr[cell], qi = ti[cell];
+        if (qr == 0 && qi == 0) continue;
+        if (slot >= 0) {  // crowded bin: FP64 sum across its subproblems (exact: q / 2^ex)
+            const double is = ldexp(1.0, -ex);
+            atomic_add_cx(nd.crowd + (int64_t)slot * G_::NCELL + cell, (double)qr * is, (double)qi * is);
             continue;
         }
         int a0, a1, a2;
@@ -271,7 +352,7 @@ __global__ void __launch_bounds__(SUB_THREADS) spread_sub_kernel(NodeDesc nd,
         const int64_t g = (D == 3)
             ? ((int64_t)pl * n + wrap1(bo.y + a1, n)) * n + wrap1(bo.z + a2, n)
             : (int64_t)pl * n + wrap1(bo.y + a1, n);
-        atomic_add_cx(H + g, vr, vi);
+        atomic_add_cx(H + g, (T)qr * inv_s, (T)qi * inv_s);
     }
 }
 

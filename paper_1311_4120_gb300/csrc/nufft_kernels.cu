@@ -13,7 +13,7 @@ int tile_cells(const NodeDesc &nd) {
 // Shared memory of the interpolation / spreading kernels: the tile (real and imaginary
 // planes) plus one table of 3 x NODE_MAXW kernel values per warp.
 size_t node_smem(const NodeDesc &nd, int prec) {
-    const size_t s = prec == NLINT_FP32 ? 4 : 8;
+    const size_t s = prec == NLINT_FP32 ? 4 : 8;  // tile cell: float/int32 or double/int64
     return 2 * (size_t)tile_cells(nd) * s + (size_t)(NODE_THREADS / 32) * 3 * NODE_MAXW * s;
 }
 
@@ -46,13 +46,12 @@ __global__ void __launch_bounds__(256) energy_partials_kernel(int64_t count, con
                                                               const T *__restrict__ rho,
                                                               double2 *__restrict__ partials) {
     __shared__ double sh[2 * 32];
-    KSum acc;
-    acc.init();
+    EAcc<T> acc;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
          i += (int64_t)gridDim.x * blockDim.x)
-        acc.add((double)u[i] * (double)rho[i]);
-    KSum tot = ksum_block(acc, sh);
-    if (threadIdx.x == 0) partials[blockIdx.x] = make_double2(tot.s, tot.c);
+        acc.add(u[i], rho[i]);
+    const double2 tot = energy_block_sum(acc, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = tot;
 }
 
 // One CTA of 1024 threads folds the partials: thread t takes partials t, t+1024, ... in

@@ -70,11 +70,34 @@ static void gauss_legendre(int m, std::vector<double> &x, std::vector<double> &w
     }
 }
 
-static bool smooth_size(int64_t n) {
-    if (n <= 0) return false;
-    while (n % 2 == 0) n /= 2;
-    while (n % 3 == 0) n /= 3;
-    return n == 1;
+
+std::vector<int16_t> build_pair_order(int w, int row, int banks) {
+    std::vector<std::pair<int, int>> rest;
+    for (int a = 0; a < w; a++)
+        for (int b = 0; b < w; b++) rest.push_back({a, b});
+    const int passes = (w * w + 31) / 32;
+    std::vector<int16_t> out((size_t)passes * 32, (int16_t)-1);
+    for (int ps = 0; ps < passes; ps++) {
+        std::vector<std::pair<int, int>> cur, later;
+        std::vector<bool> used(banks, false);
+        for (auto &q : rest) {
+            const int r = (q.first * row + q.second) % banks;
+            if ((int)cur.size() < 32 && !used[r]) {
+                used[r] = true;
+                cur.push_back(q);
+            } else {
+                later.push_back(q);
+            }
+        }
+        while ((int)cur.size() < 32 && !later.empty()) {  // a bank is shared: unavoidable
+            cur.push_back(later.front());
+            later.erase(later.begin());
+        }
+        for (size_t l = 0; l < cur.size(); l++)
+            out[(size_t)ps * 32 + l] = (int16_t)(cur[l].first << 8 | cur[l].second);
+        rest = later;
+    }
+    return out;
 }
 
 }  // namespace nlint
@@ -92,6 +115,7 @@ struct nlint_plan_s {
     void *d_frac = nullptr, *d_W = nullptr, *d_fac = nullptr, *d_tw = nullptr;
     int32_t *d_perm = nullptr, *d_mirror = nullptr;
     int4 *d_subs = nullptr, *d_bins = nullptr;
+    int16_t *d_pairs = nullptr;
     int32_t *d_crowd_bin = nullptr;
     double2 *d_crowd = nullptr;
     int B[3], T[3];
@@ -169,7 +193,7 @@ static int upload(void **dst, const std::vector<double> &v, size_t &acc) {
 
 static void plan_free(nlint_plan_s *p) {
     void *ptrs[] = {p->d_l0, p->d_frac, p->d_W, p->d_fac, p->d_tw, p->d_perm, p->d_mirror,
-                    p->d_subs, p->d_bins, p->d_crowd_bin, p->d_crowd,
+                    p->d_subs, p->d_bins, p->d_crowd_bin, p->d_crowd, p->d_pairs,
                     p->d_bufA, p->d_bufB, p->d_bufG, p->d_c, p->d_partials, p->d_E,
                     p->d_rho_io, p->d_u_io};
     for (void *q : ptrs)
@@ -212,10 +236,8 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
     p->w = w;
     p->sigma = q.sigma > 0.0 ? q.sigma : 2.0;
     if (p->sigma < 1.25) return fail(NLINT_EINVAL, "sigma must be >= 1.25");
-    int64_t nf = (int64_t)std::ceil(p->sigma * (double)p->N);
-    if (nf % 2) nf++;
-    while (!smooth_size(nf)) nf += 2;
-    if (nf > 4096) return fail(NLINT_EUNSUPPORTED, "fine grid larger than 4096 per axis");
+    const int64_t nf = fft_next_size((int64_t)std::ceil(p->sigma * (double)p->N));
+    if (nf < 0) return fail(NLINT_EUNSUPPORTED, "fine grid larger than 2048 per axis");
     p->n_fine = (int)nf;
     p->pad = w / 2 + 1;
     if (p->n_fine < 4 * p->pad + 2)
@@ -326,15 +348,24 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
     }
     int64_t nbin[3] = {1, 1, 1};
     for (int ax = 0; ax < d; ax++) nbin[ax] = (Mh ? (hi[ax] - lo[ax]) / p->B[ax] + 1 : 1);
-    std::vector<int64_t> key(Mh);
+    // sort by bin, then by stencil origin inside the bin (nodes sharing an origin become
+    // adjacent, which the kernels exploit), then canonical order
+    std::vector<int64_t> key(Mh), okey(Mh);
     for (int64_t o = 0; o < Mh; o++) {
-        int64_t kk = 0;
-        for (int ax = 0; ax < d; ax++) kk = kk * nbin[ax] + (l0[(size_t)ax * Mh + o] - lo[ax]) / p->B[ax];
+        int64_t kk = 0, oo = 0;
+        for (int ax = 0; ax < d; ax++) {
+            const int32_t rel = l0[(size_t)ax * Mh + o] - lo[ax];
+            kk = kk * nbin[ax] + rel / p->B[ax];
+            oo = oo * p->B[ax] + rel % p->B[ax];
+        }
         key[o] = kk;
+        okey[o] = oo;
     }
     std::vector<int64_t> ord(Mh);
     std::iota(ord.begin(), ord.end(), 0);
-    std::stable_sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) { return key[a] < key[b]; });
+    std::stable_sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) {
+        return key[a] != key[b] ? key[a] < key[b] : okey[a] < okey[b];
+    });
     std::vector<int32_t> l0s((size_t)d * Mh), perm(Mh), mirror(Mh);
     std::vector<double> frs((size_t)d * Mh), Ws(Mh);
     const double hd = std::pow(p->h, d);
@@ -421,6 +452,14 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
     if (!crowd_bin.empty())
         CK(cudaMemcpy(p->d_crowd_bin, crowd_bin.data(), sizeof(int32_t) * crowd_bin.size(), cudaMemcpyHostToDevice));
     acc += sizeof(int4) * (subs.size() + bins.size()) + 4 * crowd_bin.size();
+    {
+        const int row = (d == 3) ? p->T[2] : p->T[1];
+        const std::vector<int16_t> po = build_pair_order(w, row, p->prec == NLINT_FP32 ? 32 : 16);
+        CK(cudaMalloc((void **)&p->d_pairs, po.size() * sizeof(int16_t)));
+        CK(cudaMemcpy(p->d_pairs, po.data(), po.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
+        acc += po.size() * sizeof(int16_t);
+    }
+
     {
         int64_t cells = 1;
         for (int ax = 0; ax < d; ax++) cells *= p->T[ax];
@@ -579,6 +618,7 @@ static NodeDesc node_desc(nlint_plan_s *p) {
     nd.ncrowd = p->ncrowd;
     nd.crowd = p->d_crowd;
     nd.crowd_bin = p->d_crowd_bin;
+    nd.pair_order = p->d_pairs;
     return nd;
 }
 
