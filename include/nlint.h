@@ -82,6 +82,7 @@ typedef struct nlint_info {
     int64_t n_subproblems;  /* CTAs of one interpolation / spreading launch             */
     int64_t n_crowd_bins;   /* bins whose tiles are summed in FP64 (FP32 plans)         */
     int bin[3];             /* bin extent per array axis, in fine cells                 */
+    int device;             /* CUDA device ordinal the plan lives on                    */
 } nlint_info;
 
 /* Fill *p with defaults (d = 3, Coulomb, eps = 1e-6, everything else automatic). */
@@ -135,6 +136,25 @@ int nlint_plan_nodes(nlint_plan plan, double *k_host, double *W_host);
 int nlint_set_stage_timing(nlint_plan plan, int enable);
 int nlint_stage_times(nlint_plan plan, float *ms, const char **names, int max_stages,
                       int *n_stages);
+
+/* Batched evaluation of independent densities (Algorithm 1 applied to each), e.g. grids of
+ * mixed sizes, kernels and precisions.  nlint_batch_create: `count` plans (not owned: they
+ * must outlive the batch), all on one device; `branches` concurrent streams inside the batch's
+ * CUDA graph (0 = min(16, count)); plans are dealt to branches by a cost model.
+ * nlint_batch_eval: rho[i], u[i] are plan i's device arrays (its n^d reals, its precision);
+ * E_dev (may be NULL) receives count device doubles E_i = (lambda/2) h_i^d sum u_i rho_i.  The
+ * first call, and any call whose pointers or lambda differ from the previous one, captures a
+ * CUDA graph of all evaluations (one fork, one branch per stream, one join); every call then
+ * launches that graph on `stream` (no host synchronisation).  Each u_i equals what
+ * nlint_eval_energy gives for plan i alone, up to the order of the spreading's atomic
+ * additions.  One batch evaluation at a time; the plans must not be used concurrently.
+ * Errors: NLINT_EINVAL (NULL arguments, invalid plans, plans on different devices),
+ * NLINT_ECUDA. */
+int nlint_batch_create(int count, const nlint_plan *plans, int branches, nlint_batch *out);
+int nlint_batch_eval(nlint_batch batch, const void *const *rho_dev, void *const *u_dev,
+                     double lambda, double *E_dev, void *stream);
+int nlint_batch_info(nlint_batch batch, int *count, int *branches, int64_t *kernels_per_eval);
+void nlint_batch_destroy(nlint_batch batch); /* NULL is a no-op; waits for the device */
 
 /* Energy E = (lambda/2) h^d sum_i u_i rho_i (h = L/n) of caller-owned device arrays, written
  * to the device double E_dev, for callers that cannot allocate device memory when they need

@@ -28,7 +28,8 @@ EXPORTED = [
     "nlint_params_default", "nlint_plan_create", "nlint_plan_create_ex", "nlint_plan_info",
     "nlint_plan_destroy", "nlint_eval", "nlint_eval_energy", "nlint_energy", "nlint_eval_host",
     "nlint_type2", "nlint_type1", "nlint_plan_nodes", "nlint_set_stage_timing",
-    "nlint_stage_times", "nlint_launch_count", "nlint_energy_noalloc", "nlint_last_error",
+    "nlint_stage_times", "nlint_launch_count", "nlint_energy_noalloc", "nlint_batch_create",
+    "nlint_batch_eval", "nlint_batch_info", "nlint_batch_destroy", "nlint_last_error",
 ]
 
 
@@ -55,7 +56,7 @@ class nlint_info(ctypes.Structure):
                 ("sigma", ctypes.c_double), ("beta", ctypes.c_double),
                 ("workspace_bytes", ctypes.c_size_t), ("n_bins", ctypes.c_int64),
                 ("n_subproblems", ctypes.c_int64), ("n_crowd_bins", ctypes.c_int64),
-                ("bin", ctypes.c_int * 3)]
+                ("bin", ctypes.c_int * 3), ("device", ctypes.c_int)]
 
 
 _lib = None
@@ -91,10 +92,16 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                       ctypes.POINTER(ctypes.c_char_p), ci, ctypes.POINTER(ci)]
     lib.nlint_launch_count.argtypes = [vp, ctypes.POINTER(i64)]
     lib.nlint_energy_noalloc.argtypes = [ci, i64, dbl, ci, vp, vp, dbl, vp, vp]
+    lib.nlint_batch_create.argtypes = [ci, ctypes.POINTER(vp), ci, pplan]
+    lib.nlint_batch_eval.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), dbl, vp, vp]
+    lib.nlint_batch_info.argtypes = [vp, ctypes.POINTER(ci), ctypes.POINTER(ci), ctypes.POINTER(i64)]
+    lib.nlint_batch_destroy.argtypes = [vp]
+    lib.nlint_batch_destroy.restype = None
     lib.nlint_last_error.argtypes = []
     lib.nlint_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
-        if name not in ("nlint_params_default", "nlint_plan_destroy", "nlint_last_error"):
+        if name not in ("nlint_params_default", "nlint_plan_destroy", "nlint_last_error",
+                        "nlint_batch_destroy"):
             getattr(lib, name).restype = ci
     _lib = lib
     return lib
@@ -266,6 +273,62 @@ class Plan:
     def close(self):
         if getattr(self, "_h", None):
             self._lib.nlint_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Independent densities, one plan each, evaluated together by one CUDA graph.
+
+    ``plans`` must stay alive as long as the batch.  ``eval(rhos, lam)`` takes one CUDA tensor
+    per plan and returns the list of potentials and a float64 tensor of the energies.  The graph
+    is captured on the first call and re-captured only when the tensors or lam change.
+    """
+
+    def __init__(self, plans, branches: int = 0):
+        self._lib = load_library()
+        self.plans = list(plans)
+        arr = (ctypes.c_void_p * len(self.plans))(*[p._h.value for p in self.plans])
+        h = ctypes.c_void_p()
+        _check(self._lib.nlint_batch_create(len(self.plans), arr, int(branches), ctypes.byref(h)))
+        self._h = h
+        self._u = None
+        self._E = None
+
+    def info(self):
+        c, b, k = ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+        _check(self._lib.nlint_batch_info(self._h, ctypes.byref(c), ctypes.byref(b), ctypes.byref(k)))
+        return {"count": c.value, "branches": b.value, "kernels_per_eval": k.value}
+
+    def eval(self, rhos, lam: float = 1.0, outs=None, E_out=None, stream=None):
+        torch = _torch()
+        if len(rhos) != len(self.plans):
+            raise ValueError("one density per plan")
+        if outs is None:
+            if self._u is None or any(u.data_ptr() == r.data_ptr() for u, r in zip(self._u, rhos)):
+                self._u = [torch.empty(p.grid_shape, dtype=p.dtype, device=r.device)
+                           for p, r in zip(self.plans, rhos)]
+            outs = self._u
+        if E_out is None:
+            if self._E is None:
+                self._E = torch.empty(len(self.plans), dtype=torch.float64, device=rhos[0].device)
+            E_out = self._E
+        rp = (ctypes.c_void_p * len(rhos))(*[p._dev(r, p.grid_shape, p.dtype, "rho")
+                                             for p, r in zip(self.plans, rhos)])
+        up = (ctypes.c_void_p * len(outs))(*[p._dev(u, p.grid_shape, p.dtype, "u")
+                                             for p, u in zip(self.plans, outs)])
+        _check(self._lib.nlint_batch_eval(self._h, rp, up, float(lam), E_out.data_ptr(),
+                                          _stream_ptr(stream)))
+        return outs, E_out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.nlint_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

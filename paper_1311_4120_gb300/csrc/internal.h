@@ -95,13 +95,13 @@ struct NodeDesc {
     int ncrowd;          // crowded bins (FP32 plans): their tiles are summed in FP64
     double2 *crowd;      // ncrowd tiles of complex doubles
     const int32_t *crowd_bin;  // bin of each crowd slot
-    const int16_t *pair_order; // per pass and lane: stencil column (q_a << 8 | q_b) or -1
+    const int16_t *pair_order; // per pass and node lane: column (q_a << 8 | q_b) or -1
 };
 
-// Deals the w*w stencil columns (q_a, q_b) of a node to passes of 32 lanes so that, within a
-// pass, the tile offsets q_a * row + q_b fall in distinct shared-memory banks where possible
-// (`banks` = 32 for 4-byte, 16 for 8-byte elements).  Returns passes * 32 entries.
-std::vector<int16_t> build_pair_order(int w, int row, int banks);
+// Deals the w*w stencil columns (q_a, q_b) of a node to passes of `lanes` lanes so that,
+// within a pass, the tile offsets q_a * row + q_b fall in distinct shared-memory banks where
+// possible (`banks` = 32 for 4-byte, 16 for 8-byte elements).  Returns passes * lanes entries.
+std::vector<int16_t> build_pair_order(int w, int row, int banks, int lanes);
 
 // Bin extent (stencil-origin cells) along array axis `axis`; the same rule is compiled into
 // the kernels, so a plan's bins always match the tile geometry of its kernels.  3D: 8^3 bins,
@@ -112,6 +112,11 @@ __host__ __device__ constexpr int bin_extent(bool fp64, int d, int w, int axis) 
 }
 
 static constexpr int NODE_MAXW = 16;     // widest stencil
+// Lanes per node in the interpolation / spreading kernels: 16 when the w*w stencil columns
+// waste fewer lane slots in passes of 16 than in passes of 32 (w = 4, 6, 10..13, ...), else 32.
+__host__ __device__ constexpr int node_lanes(int w) {
+    return (w * w + 15) / 16 * 16 < (w * w + 31) / 32 * 32 ? 16 : 32;
+}
 static constexpr int NODE_THREADS = 256;  // threads per interpolation / spreading CTA
 
 int tile_cells(const NodeDesc &nd);

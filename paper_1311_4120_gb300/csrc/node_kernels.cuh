@@ -14,12 +14,15 @@
 //
 // Work decomposition: one CTA per subproblem (a run of nodes of one bin).  The CTA stages its
 // bin's tile (bin + w - 1 cells per axis) in shared memory as separate real and imaginary
-// planes.  A warp takes one node at a time; in 3D its lanes own (axis 1, axis 2) stencil
-// columns and run along axis 0 with the axis-0 kernel values in registers, in 2D they own
-// stencil cells.  The columns are dealt to lanes by a plan-made table so that the 32 lanes of
-// a pass hit distinct shared-memory banks.  Interpolation sums the lanes with a shuffle tree; spreading adds into the
-// tile with shared atomics (the lanes of one node touch distinct cells) and then adds the
-// tile's nonzero cells to H+ with global atomics, or, for crowded bins, to an FP64 tile.
+// planes.  Each warp owns a contiguous run of the subproblem's nodes and takes one (32 lanes
+// per node) or two (16 lanes per node, when w*w fills 16-lane passes better) at a time; in 3D
+// a node's lanes own (axis 1, axis 2) stencil columns and run along axis 0 with the axis-0
+// kernel values in registers, in 2D they own stencil cells.
+// The columns are dealt to lanes by a plan-made table so that a pass hits distinct shared-
+// memory banks.  Interpolation sums the lanes with a shuffle tree; spreading adds into the
+// tile with shared integer atomics (fixed point, see FixAcc; the lanes of one node touch
+// distinct cells) and then adds the tile's nonzero cells to H+ with global atomics, or, for
+// crowded bins, to an FP64 tile.
 #pragma once
 #include "common.cuh"
 #include "internal.h"
@@ -38,8 +41,11 @@ struct Geo {
     static constexpr int B2 = (D == 3) ? bin_extent(F64, D, W, 2) : 1;
     static constexpr int T0 = B0 + W - 1, T1 = B1 + W - 1, T2 = (D == 3) ? B2 + W - 1 : 1;
     static constexpr int NCELL = T0 * T1 * T2;
-    static constexpr int PAIRS = W * W;           // lane work items per node
-    static constexpr int PASSES = (PAIRS + 31) / 32;
+    static constexpr int PAIRS = W * W;  // stencil columns per node
+    // lanes per node: 16 (two nodes per warp) when that wastes fewer lane slots, else 32
+    static constexpr int LPN = node_lanes(W);
+    static constexpr int NPW = 32 / LPN;                 // nodes per warp iteration
+    static constexpr int PASSES = (PAIRS + LPN - 1) / LPN;
 };
 
 template <typename T>
@@ -71,37 +77,49 @@ __device__ __forceinline__ cx_t<T> fetch_half(const cx_t<T> *__restrict__ G, int
     return cconj(G[(int64_t)mz * n + wrapn(-l1, n)]);
 }
 
-// Per-lane node data of one node: stencil origin relative to the bin, and the fractional
-// offsets this lane needs to compute its share of the node's kernel values.
+// A warp works on NPW = 32 / LPN nodes at a time (one per LPN-lane group): per node its lanes
+// share the w*w stencil columns, and the nodes share the warp's per-node work (kernel values,
+// loads, shuffle reductions).  NodeGroup holds this lane's view: the stencil origin of its
+// group's node, and the fractional offsets it needs for its share of the NPW*D*w kernel values.
 template <typename T, int D, int W>
-struct NodeRec {
-    static constexpr int KV = (D * W + 31) / 32;  // kernel values per lane
+struct NodeGroup {
+    static constexpr int LPN = Geo<T, D, W>::LPN, NPW = Geo<T, D, W>::NPW;
+    static constexpr int NKV = NPW * D * W;        // kernel values of the group
+    static constexpr int KV = (NKV + 31) / 32;     // ... per lane
     int r0, r1, r2;
     T fr[KV];
-    __device__ __forceinline__ void load(const NodeDesc &nd, int64_t j, int lane, int4 bo) {
+    // nodes j .. j + NPW - 1 of the chunk ending at jb, node j + lane / LPN for this lane
+    __device__ __forceinline__ void load(const NodeDesc &nd, int j, int jb, int lane, int4 bo) {
         const int64_t M = nd.M;
-        r0 = nd.l0[j] - bo.x;
-        r1 = nd.l0[M + j] - bo.y;
-        r2 = (D == 3) ? nd.l0[2 * M + j] - bo.z : 0;
+        const int mine = (NPW == 1) ? j : j + lane / LPN;
+        if (NPW == 1 || mine < jb) {
+            r0 = nd.l0[mine] - bo.x;
+            r1 = nd.l0[M + mine] - bo.y;
+            r2 = (D == 3) ? nd.l0[2 * M + mine] - bo.z : 0;
+        } else {
+            r0 = r1 = r2 = 0;
+        }
 #pragma unroll
         for (int v = 0; v < KV; v++) {
             const int t = lane + 32 * v;
-            fr[v] = (t < D * W) ? reinterpret_cast<const T *>(nd.frac)[(t / W) * M + j] : T(0);
+            const int h = (NPW == 1) ? 0 : t / (D * W), a = (t - h * D * W) / W;
+            fr[v] = (t < NKV && (NPW == 1 || j + h < jb)) ? reinterpret_cast<const T *>(nd.frac)[a * M + j + h] : T(0);
         }
     }
 };
 
-// Kernel values of one node into the warp's table ker[a*MAXW + q] = phi((q - frac_a)/(w/2)),
-// stencil cell q of axis a; lane t computes entry t (and t + 32 when D*W > 32).
+// Kernel values of the group into the warp's table ker[h*3*MAXW + a*MAXW + q] =
+// phi((q - frac_a)/(w/2)) for node h of the group, stencil cell q of axis a.
 template <typename T, int D, int W>
-__device__ __forceinline__ void warp_kernel_values(const NodeRec<T, D, W> &nr, T beta, int lane, T *ker) {
+__device__ __forceinline__ void warp_kernel_values(const NodeGroup<T, D, W> &np, T beta, int lane, T *ker) {
     const T inv_half = T(2) / T(W);
 #pragma unroll
-    for (int v = 0; v < NodeRec<T, D, W>::KV; v++) {
+    for (int v = 0; v < NodeGroup<T, D, W>::KV; v++) {
         const int t = lane + 32 * v;
-        if (t < D * W) {
-            const int a = t / W, q = t - a * W;
-            ker[a * MAXW + q] = es_kernel<T>((T(q) - nr.fr[v]) * inv_half, beta);
+        if (t < NodeGroup<T, D, W>::NKV) {
+            const int h = (NodeGroup<T, D, W>::NPW == 1) ? 0 : t / (D * W);
+            const int rem = t - h * D * W, a = rem / W, q = rem - a * W;
+            ker[h * 3 * MAXW + a * MAXW + q] = es_kernel<T>((T(q) - np.fr[v]) * inv_half, beta);
         }
     }
 }
@@ -162,14 +180,14 @@ __global__ void __launch_bounds__(SUB_THREADS) interp_sub_kernel(NodeDesc nd,
     T *tr = reinterpret_cast<T *>(smem_raw);
     T *ti = tr + G_::NCELL;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    T *ker = ti + G_::NCELL + wid * 3 * MAXW;
+    T *ker = ti + G_::NCELL + wid * 6 * MAXW;
     const int4 sb = nd.subs[blockIdx.x];
     const int4 bo = nd.bins[sb.z];
     const int n = nd.n;
     const T beta = T(nd.beta);
     int pairs[PASSES];  // this lane's stencil columns, one per pass (-1: idle)
 #pragma unroll
-    for (int ps = 0; ps < PASSES; ps++) pairs[ps] = nd.pair_order[ps * 32 + lane];
+    for (int ps = 0; ps < PASSES; ps++) pairs[ps] = nd.pair_order[ps * G_::LPN + lane % G_::LPN];
 
     // stage the tile; the common case (axis-0 planes inside the stored half) needs no mirror
     const bool inside = bo.x >= 0 && bo.x + G_::T0 - 1 <= n / 2;
@@ -190,40 +208,46 @@ __global__ void __launch_bounds__(SUB_THREADS) interp_sub_kernel(NodeDesc nd,
 
     int ja, jb;
     warp_chunk(sb, wid, nw, ja, jb);
-    NodeRec<T, D, W> cur, nxt;
-    if (ja < jb) cur.load(nd, ja, lane, bo);
-    for (int j = ja; j < jb; j++) {
-        if (j + 1 < jb) nxt.load(nd, j + 1, lane, bo);  // prefetch the next node
-        const T Wj = apply_W ? reinterpret_cast<const T *>(nd.W)[j] : T(1);
+    const int half = lane / G_::LPN, hl = lane % G_::LPN;  // node of the group, lane in it
+    const T *kh = ker + half * 3 * MAXW;  // this lane's node's kernel values
+    NodeGroup<T, D, W> cur, nxt;
+    if (ja < jb) cur.load(nd, ja, jb, lane, bo);
+    for (int j = ja; j < jb; j += G_::NPW) {
+        if (j + G_::NPW < jb) nxt.load(nd, j + G_::NPW, jb, lane, bo);  // prefetch the next group
+        const int mine = j + half;
+        const bool act = (G_::NPW == 1) || mine < jb;
+        const T Wj = (act && apply_W) ? reinterpret_cast<const T *>(nd.W)[mine] : T(1);
         warp_kernel_values<T, D, W>(cur, beta, lane, ker);
         __syncwarp();
         T accr = T(0), acci = T(0);
-        T k0[L];
+        if (act) {
+            T k0[L];
 #pragma unroll
-        for (int q = 0; q < L; q++) k0[q] = (D == 3) ? ker[q] : T(1);
+            for (int q = 0; q < L; q++) k0[q] = (D == 3) ? kh[q] : T(1);
 #pragma unroll
-        for (int ps = 0; ps < PASSES; ps++) {
-            const int pq = pairs[ps];
-            if (pq >= 0) {
-                const int qa = pq >> 8, qb = pq & 255;
-                const T kab = (D == 3) ? ker[MAXW + qa] * ker[2 * MAXW + qb] : ker[qa] * ker[MAXW + qb];
-                const int idx = col_index<G_, D>(cur.r0, cur.r1, cur.r2, qa, qb);
-                T sr = T(0), si = T(0);
+            for (int ps = 0; ps < PASSES; ps++) {
+                const int pq = pairs[ps];
+                if (pq >= 0) {
+                    const int qa = pq >> 8, qb = pq & 255;
+                    const T kab = (D == 3) ? kh[MAXW + qa] * kh[2 * MAXW + qb] : kh[qa] * kh[MAXW + qb];
+                    const int idx = col_index<G_, D>(cur.r0, cur.r1, cur.r2, qa, qb);
+                    T sr = T(0), si = T(0);
 #pragma unroll
-                for (int q0 = 0; q0 < L; q0++) {
-                    sr += k0[q0] * tr[idx + q0 * PLANE];
-                    si += k0[q0] * ti[idx + q0 * PLANE];
+                    for (int q0 = 0; q0 < L; q0++) {
+                        sr += k0[q0] * tr[idx + q0 * PLANE];
+                        si += k0[q0] * ti[idx + q0 * PLANE];
+                    }
+                    accr += kab * sr;
+                    acci += kab * si;
                 }
-                accr += kab * sr;
-                acci += kab * si;
             }
         }
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
+        for (int off = G_::LPN / 2; off > 0; off >>= 1) {  // within each node's lanes
             accr += __shfl_xor_sync(0xffffffffu, accr, off);
             acci += __shfl_xor_sync(0xffffffffu, acci, off);
         }
-        if (lane == 0) c_out[j] = cmake<T2>(accr * Wj, acci * Wj);
+        if (hl == 0 && act) c_out[mine] = cmake<T2>(accr * Wj, acci * Wj);
         __syncwarp();
         cur = nxt;
     }
@@ -250,14 +274,14 @@ __global__ void __launch_bounds__(SUB_THREADS) spread_sub_kernel(NodeDesc nd,
     A *tr = reinterpret_cast<A *>(smem_raw);
     A *ti = tr + G_::NCELL;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    T *ker = reinterpret_cast<T *>(ti + G_::NCELL) + wid * 3 * MAXW;
+    T *ker = reinterpret_cast<T *>(ti + G_::NCELL) + wid * 6 * MAXW;
     const int4 sb = nd.subs[blockIdx.x];
     const int4 bo = nd.bins[sb.z];
     const int n = nd.n, pad = nd.pad;
     const T beta = T(nd.beta);
     int pairs[PASSES];
 #pragma unroll
-    for (int ps = 0; ps < PASSES; ps++) pairs[ps] = nd.pair_order[ps * 32 + lane];
+    for (int ps = 0; ps < PASSES; ps++) pairs[ps] = nd.pair_order[ps * G_::LPN + lane % G_::LPN];
 
     // bound B = max(sum |Re c_j|, sum |Im c_j|) over the subproblem, while the tile is cleared
     T bre = T(0), bim = T(0);
@@ -282,7 +306,7 @@ __global__ void __launch_bounds__(SUB_THREADS) spread_sub_kernel(NodeDesc nd,
     __syncthreads();
     T sre = T(0), sim = T(0);
     for (int q = 0; q < nw; q++) {
-        const T *kq = reinterpret_cast<T *>(ti + G_::NCELL) + q * 3 * MAXW;
+        const T *kq = reinterpret_cast<T *>(ti + G_::NCELL) + q * 6 * MAXW;
         sre += kq[0];
         sim += kq[1];
     }
@@ -297,35 +321,40 @@ __global__ void __launch_bounds__(SUB_THREADS) spread_sub_kernel(NodeDesc nd,
 
     int ja, jb;
     warp_chunk(sb, wid, nw, ja, jb);
-    NodeRec<T, D, W> cur, nxt;
+    const int half = lane / G_::LPN;
+    const T *kh = ker + half * 3 * MAXW;
+    NodeGroup<T, D, W> cur, nxt;
     T2 c = czero<T2>(), cn = czero<T2>();
     if (ja < jb) {
-        cur.load(nd, ja, lane, bo);
-        c = c_in[ja];
+        cur.load(nd, ja, jb, lane, bo);
+        if (ja + half < jb) c = c_in[ja + half];
     }
-    for (int j = ja; j < jb; j++) {
-        if (j + 1 < jb) {  // prefetch the next node
-            nxt.load(nd, j + 1, lane, bo);
-            cn = c_in[j + 1];
+    for (int j = ja; j < jb; j += G_::NPW) {
+        if (j + G_::NPW < jb) {  // prefetch the next group
+            nxt.load(nd, j + G_::NPW, jb, lane, bo);
+            cn = (j + G_::NPW + half < jb) ? c_in[j + G_::NPW + half] : czero<T2>();
         }
+        const bool act = (G_::NPW == 1) || j + half < jb;
         warp_kernel_values<T, D, W>(cur, beta, lane, ker);
         __syncwarp();
-        T k0[L];
+        if (act) {
+            T k0[L];
 #pragma unroll
-        for (int q = 0; q < L; q++) k0[q] = (D == 3) ? ker[q] : T(1);
-        const T csr = c.x * S, csi = c.y * S;
+            for (int q = 0; q < L; q++) k0[q] = (D == 3) ? kh[q] : T(1);
+            const T csr = c.x * S, csi = c.y * S;
 #pragma unroll
-        for (int ps = 0; ps < PASSES; ps++) {
-            const int pq = pairs[ps];
-            if (pq >= 0) {
-                const int qa = pq >> 8, qb = pq & 255;
-                const T kab = (D == 3) ? ker[MAXW + qa] * ker[2 * MAXW + qb] : ker[qa] * ker[MAXW + qb];
-                const T cr = csr * kab, ci = csi * kab;
-                const int idx = col_index<G_, D>(cur.r0, cur.r1, cur.r2, qa, qb);
+            for (int ps = 0; ps < PASSES; ps++) {
+                const int pq = pairs[ps];
+                if (pq >= 0) {
+                    const int qa = pq >> 8, qb = pq & 255;
+                    const T kab = (D == 3) ? kh[MAXW + qa] * kh[2 * MAXW + qb] : kh[qa] * kh[MAXW + qb];
+                    const T cr = csr * kab, ci = csi * kab;
+                    const int idx = col_index<G_, D>(cur.r0, cur.r1, cur.r2, qa, qb);
 #pragma unroll
-                for (int q0 = 0; q0 < L; q0++) {
-                    F::add(tr + idx + q0 * PLANE, F::quant(cr * k0[q0]));
-                    F::add(ti + idx + q0 * PLANE, F::quant(ci * k0[q0]));
+                    for (int q0 = 0; q0 < L; q0++) {
+                        F::add(tr + idx + q0 * PLANE, F::quant(cr * k0[q0]));
+                        F::add(ti + idx + q0 * PLANE, F::quant(ci * k0[q0]));
+                    }
                 }
             }
         }

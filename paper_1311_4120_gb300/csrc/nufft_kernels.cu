@@ -11,10 +11,10 @@ int tile_cells(const NodeDesc &nd) {
 }
 
 // Shared memory of the interpolation / spreading kernels: the tile (real and imaginary
-// planes) plus one table of 3 x NODE_MAXW kernel values per warp.
+// planes) plus one table of 2 x 3 x NODE_MAXW kernel values per warp (two nodes at a time).
 size_t node_smem(const NodeDesc &nd, int prec) {
     const size_t s = prec == NLINT_FP32 ? 4 : 8;  // tile cell: float/int32 or double/int64
-    return 2 * (size_t)tile_cells(nd) * s + (size_t)(NODE_THREADS / 32) * 3 * NODE_MAXW * s;
+    return 2 * (size_t)tile_cells(nd) * s + (size_t)(NODE_THREADS / 32) * 6 * NODE_MAXW * s;
 }
 
 // out[perm[j]] = scale * v_j, out[mirror[j]] = scale * conj(v_j)

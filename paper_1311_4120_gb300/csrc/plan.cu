@@ -71,30 +71,30 @@ static void gauss_legendre(int m, std::vector<double> &x, std::vector<double> &w
 }
 
 
-std::vector<int16_t> build_pair_order(int w, int row, int banks) {
+std::vector<int16_t> build_pair_order(int w, int row, int banks, int lanes) {
     std::vector<std::pair<int, int>> rest;
     for (int a = 0; a < w; a++)
         for (int b = 0; b < w; b++) rest.push_back({a, b});
-    const int passes = (w * w + 31) / 32;
-    std::vector<int16_t> out((size_t)passes * 32, (int16_t)-1);
+    const int passes = (w * w + lanes - 1) / lanes;
+    std::vector<int16_t> out((size_t)passes * lanes, (int16_t)-1);
     for (int ps = 0; ps < passes; ps++) {
         std::vector<std::pair<int, int>> cur, later;
         std::vector<bool> used(banks, false);
         for (auto &q : rest) {
             const int r = (q.first * row + q.second) % banks;
-            if ((int)cur.size() < 32 && !used[r]) {
+            if ((int)cur.size() < lanes && !used[r]) {
                 used[r] = true;
                 cur.push_back(q);
             } else {
                 later.push_back(q);
             }
         }
-        while ((int)cur.size() < 32 && !later.empty()) {  // a bank is shared: unavoidable
+        while ((int)cur.size() < lanes && !later.empty()) {  // a bank is shared: unavoidable
             cur.push_back(later.front());
             later.erase(later.begin());
         }
         for (size_t l = 0; l < cur.size(); l++)
-            out[(size_t)ps * 32 + l] = (int16_t)(cur[l].first << 8 | cur[l].second);
+            out[(size_t)ps * lanes + l] = (int16_t)(cur[l].first << 8 | cur[l].second);
         rest = later;
     }
     return out;
@@ -454,7 +454,7 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
     acc += sizeof(int4) * (subs.size() + bins.size()) + 4 * crowd_bin.size();
     {
         const int row = (d == 3) ? p->T[2] : p->T[1];
-        const std::vector<int16_t> po = build_pair_order(w, row, p->prec == NLINT_FP32 ? 32 : 16);
+        const std::vector<int16_t> po = build_pair_order(w, row, p->prec == NLINT_FP32 ? 32 : 16, node_lanes(w));
         CK(cudaMalloc((void **)&p->d_pairs, po.size() * sizeof(int16_t)));
         CK(cudaMemcpy(p->d_pairs, po.data(), po.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
         acc += po.size() * sizeof(int16_t);
@@ -766,6 +766,7 @@ int nlint_plan_info(nlint_plan p, nlint_info *info) {
     info->n_subproblems = p->nsub;
     info->n_crowd_bins = p->ncrowd;
     for (int a = 0; a < 3; a++) info->bin[a] = p->B[a];
+    info->device = p->device;
     return NLINT_OK;
 }
 

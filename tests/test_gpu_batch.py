@@ -1,0 +1,95 @@
+"""Batched evaluation (one CUDA graph over many plans) against the same plans evaluated one at
+a time, and against the oracle for a few members of the mixed-size workload."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import pipeline
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1311_4120_gb300 as p
+    p.load_library()
+    return p
+
+
+def _members(precision, count=10):
+    # a reduced mixed-size batch with the recipe of the 64-density workload (sizes <= 64 so that
+    # the oracle stays fast)
+    rng = np.random.default_rng(synth.SEED_MIX + 7)
+    arng = np.random.default_rng(synth.SEED_AXIS + 7)
+    out = []
+    for i in range(count):
+        n = int(rng.choice([24, 32, 48, 64]))
+        kern = "coulomb" if i % 2 == 0 else "dipole"
+        axis = synth.random_unit(arng, 3) if kern == "dipole" else None
+        c, s, w = synth.mixture_params(rng, 6, 3, 3.0, 0.6, 1.4, 0.5, 1.0)
+        rho = synth.mixture(3, n, 16.0, c, s, w)
+        nodes = synth.default_nodes(3, n)
+        out.append((n, kern, axis, nodes, rho))
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_batch_equals_single_plans_and_replays(pkg, precision):
+    members = _members(precision)
+    eps = 1e-6 if precision == "fp32" else 1e-12
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    plans = [pkg.Plan(3, n, 16.0, k, axis=a, nodes=nd, precision=precision, eps=eps, device=0)
+             for n, k, a, nd, _ in members]
+    rhos = [torch.from_numpy(r).to("cuda:0", dt) for *_, r in members]
+    singles = []
+    for p, r in zip(plans, rhos):
+        u, E = p.eval_energy(r, lam=0.9)
+        singles.append((u.double().cpu().numpy(), float(E.item())))
+    batch = pkg.Batch(plans, branches=4)
+    for rep in range(2):  # second call replays the captured graph
+        us, Es = batch.eval(rhos, lam=0.9)
+        torch.cuda.synchronize()
+        Es = Es.cpu().numpy()
+        for i, (u, E) in enumerate(singles):
+            ub = us[i].double().cpu().numpy()
+            tol = 1e-5 if precision == "fp32" else 1e-12
+            assert np.max(np.abs(ub - u)) <= tol * np.max(np.abs(u)), (rep, i)
+            assert abs(Es[i] - E) <= tol * abs(E) + 1e-14, (rep, i)
+    info = batch.info()
+    assert info["count"] == len(plans) and info["kernels_per_eval"] >= 9 * len(plans)
+    # new contents in the same tensors: the replayed graph reads them
+    for r in rhos:
+        r.mul_(2.0)
+    us, Es = batch.eval(rhos, lam=0.9)
+    torch.cuda.synchronize()
+    for i, (u, E) in enumerate(singles):
+        ub = us[i].double().cpu().numpy()
+        tol = 1e-5 if precision == "fp32" else 1e-12
+        assert np.max(np.abs(ub - 2 * u)) <= tol * 2 * np.max(np.abs(u))
+        assert abs(float(Es[i]) - 4 * E) <= tol * 4 * abs(E) + 1e-14
+    batch.close()
+
+
+def test_batch_members_match_oracle(pkg):
+    members = _members("fp32", count=4)
+    plans = [pkg.Plan(3, n, 16.0, k, axis=a, nodes=nd, precision="fp32", eps=1e-6, device=0)
+             for n, k, a, nd, _ in members]
+    rhos = [torch.from_numpy(r).to("cuda:0", torch.float32) for *_, r in members]
+    batch = pkg.Batch(plans)
+    us, Es = batch.eval(rhos, lam=1.0)
+    torch.cuda.synchronize()
+    for i, (n, k, a, nd, rho) in enumerate(members):
+        ref = pipeline.oracle_eval(rho, 16.0, nd, k, axis=a, setting="fp32ref")
+        err = np.max(np.abs(us[i].double().cpu().numpy() - ref["u"])) / np.max(np.abs(ref["u"]))
+        assert err <= 1e-5, (i, err)
+        assert abs(float(Es[i]) - ref["E"]) <= 1e-5 * ref["E_scale"]
+    batch.close()
+
+
+def test_batch_rejects_bad_arguments(pkg):
+    with pytest.raises(pkg.NlintError):
+        pkg.Batch([])
