@@ -41,11 +41,22 @@ L2_FLUSH_BYTES = 256 << 20          # > 129 MB L2: written between timed steps
 # DRAM bytes per launch from an ncu capture of the kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum), keyed by stage name, with the hash of the kernel source the capture
 # was taken on: a changed source reports traffic null until it is captured again.
-TRAFFIC = {}
+# Measured on the 256^3 FP32 workload (profiles/spread_interp_c4_fp32.md,
+# profiles/fft_passes_c4_fp32.md).
+TRAFFIC = {
+    "interp": {"bytes": 471.3e6, "src": "da2c9d1b1cfcb447"},
+    "spread": {"bytes": 684.8e6, "src": "da2c9d1b1cfcb447"},
+    "fwd_fft_z": {"bytes": 148.0e6, "src": "00cab7524e8772fd"},
+    "fwd_fft_y": {"bytes": 345.4e6, "src": "00cab7524e8772fd"},
+    "fwd_fft_x": {"bytes": 749.6e6, "src": "00cab7524e8772fd"},
+    "inv_fft_x": {"bytes": 797.9e6, "src": "00cab7524e8772fd"},
+    "inv_fft_y": {"bytes": 373.5e6, "src": "00cab7524e8772fd"},
+    "inv_fft_z": {"bytes": 250.5e6, "src": "00cab7524e8772fd"},
+}
 
 
 def _src_hash(stage: str) -> str:
-    fname = "nufft_kernels.cu" if stage in ("interp", "spread") else "fft_passes.cu"
+    fname = "node_kernels.cuh" if stage in ("interp", "spread") else "fft_kernels.cuh"
     with open(os.path.join(ROOT, "paper_1311_4120_gb300", "csrc", fname), "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
@@ -214,6 +225,56 @@ def run_reference(args, rank, world):
     return 0
 
 
+# ----------------------------------------------------------------------------- batched form
+def run_batched(pkg, torch, dev, precision, reps, flush, stream, loop_too=False):
+    """64 seeded densities on uneven grids {32,48,64,96,128}^3 (box [-12,12]^3, 16-Gaussian
+    mixtures, half Coulomb and half dipolar with seeded axes), one plan each, evaluated by one
+    captured CUDA graph.  Returns throughput (total grid points per second) and, optionally, the
+    same plans evaluated one after another on one stream."""
+    members = synth.config5(precision)
+    eps = 1e-6 if precision == "fp32" else 1e-12
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    plans = [pkg.Plan(3, m.n, m.L, m.kernel, axis=m.axis, nodes=m.nodes, precision=precision,
+                      eps=eps, device=dev.index) for m in members]
+    rhos = [torch.from_numpy(m.rho()).to(dev, dt) for m in members]
+    points = sum(m.n_points for m in members)
+    batch = pkg.Batch(plans)
+    for _ in range(3):
+        batch.eval(rhos)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * reps)]
+    for k in range(reps):
+        flush.fill_(float(k))
+        ev[2 * k].record(stream)
+        batch.eval(rhos)
+        ev[2 * k + 1].record(stream)
+    torch.cuda.synchronize()
+    ms = statistics.median(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(reps))
+    info = batch.info()
+    out = {"value": points / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "densities": len(members),
+           "grid_points": points, "kernels_per_eval": info["kernels_per_eval"],
+           "branches": info["branches"], "sizes": sorted({m.n for m in members})}
+    if loop_too:
+        us = [torch.empty_like(r) for r in rhos]
+        Es = torch.empty(len(rhos), dtype=torch.float64, device=dev)
+        for k in range(reps + 1):
+            flush.fill_(float(k))
+            ev[0].record(stream)
+            for i, (p, r) in enumerate(zip(plans, rhos)):
+                p.eval_energy(r, out=us[i], E_out=Es[i])
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            if k == 0:
+                continue
+            ms_loop = ev[0].elapsed_time(ev[1])
+        out["one_by_one_ms"] = ms_loop
+        out["speedup_vs_one_by_one"] = ms_loop / ms
+    batch.close()
+    for p in plans:
+        p.close()
+    return out
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -300,27 +361,30 @@ def run_ours(args, rank, world, local_rank):
            "d2h_bytes_per_step": rho_np.nbytes + 8}
 
     # ---- the same workload on the FP64 GPU path: speedup and the FP32 result's error
-    plan64 = pkg.Plan(wl.d, wl.n, wl.L, wl.kernel, nodes=wl.nodes, eps=1e-12, precision="fp64",
-                      device=local_rank)
-    rho64 = torch.from_numpy(wl.rho()).to(dev)
-    u64 = torch.empty_like(rho64)
-    E64 = torch.empty((), dtype=torch.float64, device=dev)
-    for _ in range(2):
-        plan64.eval_energy(rho64, lam=wl.lam, out=u64, E_out=E64)
-    k64 = max(2, min(args.steps, 5))
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * k64)]
-    ms64 = []
-    for k in range(k64):
-        flush.fill_(float(k))
-        ev[2 * k].record(stream)
-        plan64.eval_energy(rho64, lam=wl.lam, out=u64, E_out=E64)
-        ev[2 * k + 1].record(stream)
-    torch.cuda.synchronize()
-    ms64 = [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(k64)]
-    rel = float((u32.double() - u64).abs().max() / u64.abs().max())
-    E64v = float(E64.item())
-    w64 = plan64.info["w"]
-    plan64.close()
+    fp64 = None
+    if not args.no_fp64:
+        plan64 = pkg.Plan(wl.d, wl.n, wl.L, wl.kernel, nodes=wl.nodes, eps=1e-12, precision="fp64",
+                          device=local_rank)
+        rho64 = torch.from_numpy(wl.rho()).to(dev)
+        u64 = torch.empty_like(rho64)
+        E64 = torch.empty((), dtype=torch.float64, device=dev)
+        for _ in range(2):
+            plan64.eval_energy(rho64, lam=wl.lam, out=u64, E_out=E64)
+        k64 = max(2, min(args.steps, 5))
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * k64)]
+        for k in range(k64):
+            flush.fill_(float(k))
+            ev[2 * k].record(stream)
+            plan64.eval_energy(rho64, lam=wl.lam, out=u64, E_out=E64)
+            ev[2 * k + 1].record(stream)
+        torch.cuda.synchronize()
+        ms64 = statistics.median(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(k64))
+        fp64 = {"value": wl.n_points / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
+                "w": plan64.info["w"], "energy": float(E64.item()),
+                "rel_linf_fp32_vs_fp64": float((u32.double() - u64).abs().max() / u64.abs().max()),
+                "rel_energy_fp32_vs_fp64": abs(E32 - float(E64.item())) / abs(float(E64.item()))}
+        plan64.close()
+        del rho64, u64
 
     if rank != 0:
         return 0
@@ -340,6 +404,14 @@ def run_ours(args, rank, world, local_rank):
     ms_step = 1e3 * t_max / args.steps
     path_gbs = path_bytes(info) / (ms_step / 1e3) / 1e9
 
+    batched = None
+    if not args.no_batch:
+        b32 = run_batched(pkg, torch, dev, "fp32", 5, flush, stream, loop_too=True)
+        b64 = run_batched(pkg, torch, dev, "fp64", 3, flush, stream)
+        batched = {"workload": "64 seeded densities on {32,48,64,96,128}^3 grids over [-12,12]^3, "
+                               "half Coulomb, half dipole, one CUDA graph",
+                   "fp32": b32, "fp64": b64,
+                   "speedup_fp32_vs_fp64_gpu": b64["ms_per_step"] / b32["ms_per_step"]}
     cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline_obj()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -351,11 +423,10 @@ def run_ours(args, rank, world, local_rank):
                    "w": info["w"], "sigma": info["sigma"], "n_fine": info["n_fine"],
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
-        "rel_linf_vs_fp64_gpu": rel,
-        "energy": {"fp32": E32, "fp64_gpu": E64v},
-        "fp64_gpu": {"value": wl.n_points / (statistics.median(ms64) / 1e3), "unit": UNIT,
-                     "ms_per_step": statistics.median(ms64), "w": w64},
-        "speedup_fp32_vs_fp64_gpu": statistics.median(ms64) / ms_step,
+        "energy": E32,
+        "fp64_gpu": fp64,
+        "speedup_fp32_vs_fp64_gpu": (fp64["ms_per_step"] / ms_step) if fp64 else None,
+        "batched": batched,
         "stages_ms": {k: round(v, 4) for k, v in mean_stage.items()},
         "path_bytes_per_step": path_bytes(info),
         "path_frac_of_hbm": path_gbs / peak,
@@ -373,10 +444,12 @@ def run_ours(args, rank, world, local_rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-density batched form")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
