@@ -6,6 +6,14 @@ Sources:
   * 2.5D Coulomb of a Gaussian, eq. (4.2) (Example 1).
   * Example 4 (eqs. 4.10-4.11): rho = [-2 beta + 4 sum x_i^2/a_i^2] e^{-g}  ->  u = -e^{-g}.
   * Example 5: 3D dipole, u = -rho + 6 [2 g_n^2 - sum n_i^2/a_i] e^{-g}.
+  * Example 6: 3D dipole with two orientations n, m (eq. dipkerneldF), same density:
+    u = -(m.n) rho + 6 [2 g_n g_m - sum n_i m_i / a_i] e^{-g}.  The paper prints -rho for the
+    first term; the kernel's delta term is -(m.n) delta, so -(m.n) rho is what U * rho is
+    (the two agree only when m = n).
+  * Examples 2-3: 2.5D dipole (alpha = 0, n_3 = m_3 = 0) of exp(-|x|^2/a).  For the kernel of
+    eq. dipkernelF2dd, U * rho = -(3/2) d_n d_m u_C with u_C the 2.5D Coulomb potential of
+    eq. (4.2); the expressions printed in Examples 2 and 3 are its negative, so ex23_u returns
+    the negated printed expression (the sign follows the kernel, as for the 3D dipole).
   * Example 7: dipole energy of a cylindrical Gaussian, closed form in kappa = sqrt(gz/gx).
   * The 1D t-integral for anisotropic Gaussians, from 1/|x| = (2/sqrt(pi)) int_0^inf
     e^{-|x|^2 t^2} dt: for rho = prod_i exp(-x_i^2/a_i),
@@ -146,6 +154,38 @@ def ex5_u(x, y, z, n, a=(1.3, 1.5, 1.8)):
     gn = x * n[0] / a[0] + y * n[1] / a[1] + z * n[2] / a[2]
     s = n[0] ** 2 / a[0] + n[1] ** 2 / a[1] + n[2] ** 2 / a[2]
     return -ex4_rho(x, y, z, a) + 6.0 * (2.0 * gn * gn - s) * np.exp(-g)
+
+
+def ex6_u(x, y, z, n, m, a=(1.2, 1.45, 1.73)):
+    n = np.asarray(n, dtype=np.float64)
+    m = np.asarray(m, dtype=np.float64)
+    n = n / np.linalg.norm(n)
+    m = m / np.linalg.norm(m)
+    g = x * x / a[0] + y * y / a[1] + z * z / a[2]
+    gn = x * n[0] / a[0] + y * n[1] / a[1] + z * n[2] / a[2]
+    gm = x * m[0] / a[0] + y * m[1] / a[1] + z * m[2] / a[2]
+    s = n[0] * m[0] / a[0] + n[1] * m[1] / a[1] + n[2] * m[2] / a[2]
+    return -float(n @ m) * ex4_rho(x, y, z, a) + 6.0 * (2.0 * gn * gm - s) * np.exp(-g)
+
+
+# ----------------------------------------------------------------- Examples 2-3 (2.5D dipole)
+def ex23_u(x, y, a: float, n, m=None):
+    """2.5D dipole potential of exp(-(x^2+y^2)/a) for in-plane unit axes n, m (m = n:
+    Example 2), alpha = 0: (3 sqrt(pi) / (4 sqrt(a))) e^{-r} [(n.m)(I_0(r) - I_1(r))
+    - ((x.n)(x.m)/a)(2 I_0(r) - (1 + 2r) I_1(r)/r)], r = |x|^2 / (2a)."""
+    n = np.asarray(n, dtype=np.float64)[:2]
+    m = n if m is None else np.asarray(m, dtype=np.float64)[:2]
+    n = n / np.linalg.norm(n)
+    m = m / np.linalg.norm(m)
+    r = (x * x + y * y) / (2.0 * a)
+    i0 = special.ive(0, r)
+    i1 = special.ive(1, r)
+    safe = np.where(r > 1e-12, r, 1.0)
+    t = np.where(r > 1e-12, (1.0 + 2.0 * safe) * i1 / safe, 0.5)  # (1+2r) I_1(r)/r -> 1/2
+    xn = x * n[0] + y * n[1]
+    xm = x * m[0] + y * m[1]
+    pref = 3.0 * math.sqrt(math.pi) / (4.0 * math.sqrt(a))
+    return pref * (float(n @ m) * (i0 - i1) - xn * xm / a * (2.0 * i0 - t))
 
 
 # ----------------------------------------------------------------- Example 7

@@ -55,6 +55,7 @@ def mix_err(method="nufft", n=20):
 
 def test_unmutated_baseline_passes():
     assert ex4_err() < 1e-4 and ex5_err() < 1e-4 and mix_err() < 1e-4
+    assert ex2_err() < 1e-4 and ex6_err() < 1e-4
 
 
 def _drop_sin(d, n, L, nodes, kernel="coulomb", axis=None, axis2=None, alpha=0.0, P=None):
@@ -75,12 +76,43 @@ def _transpose_nodes(d, n, L, nodes, kernel="coulomb", axis=None, axis2=None, al
     return k[:, ::-1].copy(), W
 
 
+def _planar_dipole_no_half(k, d, kernel, axis=None, axis2=None, alpha=0.0):
+    # drops the 1/2 of the 2.5D dipole symbol (eqs. dipkernelF2d / dipkernelF2dd)
+    v = ORIG_UHAT(k, d, kernel, axis, axis2, alpha)
+    return 2.0 * v if (kernel == "dipole" and d == 2) else v
+
+
+def _two_axis_uses_n_twice(k, d, kernel, axis=None, axis2=None, alpha=0.0):
+    # ignores the second orientation m of eq. dipkerneldF
+    return ORIG_UHAT(k, d, kernel, axis, None, alpha)
+
+
+def ex2_err():
+    a, n = 1.3, np.array([0.52460, -0.85135, 0.0])
+    y, x = synth.grid_coords(2, 64, 24.0)
+    rho = np.exp(-(x * x + y * y) / a)
+    o = pipeline.oracle_eval(rho, 24.0, (48, 96), "dipole", axis=n)
+    ref = cf.ex23_u(x, y, a, n)
+    m = np.sqrt(x * x + y * y) < 4
+    return np.max(np.abs(o["u"][m] - ref[m])) / np.max(np.abs(ref[m]))
+
+
+def ex6_err():
+    a = (1.2, 1.45, 1.73)
+    n, mm = np.array([0.82778, 0.41505, -0.37751]), np.array([0.31180, 0.93780, -0.15214])
+    z, y, x = synth.grid_coords(3, 20, 10.0)
+    o = pipeline.oracle_eval(cf.ex4_rho(x, y, z, a), 10.0, (20, 20, 40), "dipole", axis=n, axis2=mm)
+    ref = cf.ex6_u(x, y, z, n, mm, a)
+    m = np.sqrt(x * x + y * y + z * z) < 3
+    return np.max(np.abs(o["u"][m] - ref[m])) / np.max(np.abs(ref[m]))
+
+
 def _conj_type2(rho, L, k, method="nufft", setting="parity"):
     return np.conj(ORIG_T2(rho, L, k, method, setting))
 
 
 @pytest.mark.parametrize("mutation", ["drop_sin", "flip_dipole", "transpose", "conj_type2",
-                                      "grid_offset"])
+                                      "grid_offset", "planar_half", "two_axis"])
 def test_pins_catch_mutation(monkeypatch, mutation):
     if mutation == "drop_sin":
         monkeypatch.setattr(quadrature, "nodes_weights", _drop_sin)
@@ -91,6 +123,12 @@ def test_pins_catch_mutation(monkeypatch, mutation):
     elif mutation == "transpose":
         monkeypatch.setattr(quadrature, "nodes_weights", _transpose_nodes)
         err = max(ex4_err(), ex5_err())
+    elif mutation == "planar_half":
+        monkeypatch.setattr(quadrature, "u_hat", _planar_dipole_no_half)
+        err = ex2_err()
+    elif mutation == "two_axis":
+        monkeypatch.setattr(quadrature, "u_hat", _two_axis_uses_n_twice)
+        err = ex6_err()
     elif mutation == "conj_type2":
         monkeypatch.setattr(pipeline, "type2", _conj_type2)
         err = mix_err()

@@ -271,3 +271,45 @@ def test_invariant_dipole_trace():
     rho = np.random.default_rng(9).standard_normal((n,) * 3)
     us = [_op(rho, L, nodes, "dipole", axis=e)["u"] for e in np.eye(3)]
     assert np.max(np.abs(us[0] + us[1] + us[2])) < 1e-13 * np.max(np.abs(us[0]))
+
+
+# --------------------------------------------------------------------------- other dipole kernels
+def test_pipeline_example6_two_axis_dipole():
+    a = (1.2, 1.45, 1.73)
+    n = np.array([0.82778, 0.41505, -0.37751])
+    m = np.array([0.31180, 0.93780, -0.15214])
+    N, L = 40, 12.0
+    z, y, x = synth.grid_coords(3, N, L)
+    rho = cf.ex4_rho(x, y, z, a)
+    o = pipeline.oracle_eval(rho, L, (40, 40, 80), "dipole", axis=n, axis2=m, setting="fine")
+    ref = cf.ex6_u(x, y, z, n, m, a)
+    mask = np.sqrt(x * x + y * y + z * z) < 3
+    assert rel_inf(o["u"], ref, mask) < 1e-8
+
+
+@pytest.mark.parametrize("ex", [2, 3])
+def test_pipeline_examples_2_3_planar_dipole(ex):
+    if ex == 2:
+        a, n, m = 1.3, np.array([0.52460, -0.85135, 0.0]), None
+    else:
+        a, n, m = 1.8, np.array([-0.44404, -0.89600, 0.0]), np.array([0.85125, -0.52476, 0.0])
+    N, L = 96, 24.0
+    y, x = synth.grid_coords(2, N, L)
+    rho = np.exp(-(x * x + y * y) / a)
+    o = pipeline.oracle_eval(rho, L, (72, 144), "dipole", axis=n, axis2=m, setting="fine")
+    ref = cf.ex23_u(x, y, a, n, m)
+    assert rel_inf(o["u"], ref) < 1e-9
+
+
+def test_planar_dipole_alpha_term_is_minus_alpha_rho():
+    # the constant -alpha of the 2.5D symbol acts as -alpha times the (band-limited) density
+    # (inside |x| < 6: at the box corners the phi rule with 144 nodes no longer resolves
+    # exp(i k.x) for |k||x| up to ~ 140)
+    N, L = 96, 24.0
+    y, x = synth.grid_coords(2, N, L)
+    rho = np.exp(-(x * x + y * y) / 1.3)
+    n = np.array([0.3, -0.5, 0.8])
+    o1 = pipeline.oracle_eval(rho, L, (72, 144), "dipole", axis=n, alpha=0.7, setting="fine")
+    o0 = pipeline.oracle_eval(rho, L, (72, 144), "dipole", axis=n, alpha=0.0, setting="fine")
+    mask = np.sqrt(x * x + y * y) < 6
+    assert np.max(np.abs((o1["u"] - o0["u"]) + 0.7 * rho)[mask]) < 1e-10
