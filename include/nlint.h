@@ -9,8 +9,10 @@
  *   nodes     k_j = r (sin t cos p, sin t sin p, cos t) in 3D, r (cos p, sin p) in 2D, with
  *             r Gauss-Legendre on [0, P], t Gauss-Legendre on [0, pi], p = 2 pi l / N_phi;
  *   weights   W_j = (2 pi)^{-d} w_r w_t sin(t) w_p |k_j|^{d-1} U_hat(k_j)     (eq. 3.7)
- *             U_hat = 1/|k|^2 (3D Coulomb), -1 + 3 (n.k)^2/|k|^2 (3D dipole),
- *             1/|k| (2.5D Coulomb)                                        (eq. int3dd)
+ *             U_hat = 1/|k|^2 (3D Coulomb), 1/|k| (2.5D Coulomb),
+ *             -(m.n) + 3 (n.k)(m.k)/|k|^2 (3D dipole, eq. dipkerneldF; m = n: dipkernelF),
+ *             -alpha + 3 [(n_p.k)(m_p.k) - n_3 m_3 |k|^2] / (2|k|) (2.5D dipole,
+ *             eq. dipkernelF2dd; n_p = (n_1, n_2); m = n: dipkernelF2d)   (table int3dd)
  *   type 2    rho_hat_j = h^d sum_i rho_i exp(-i k_j . x_i)                  (eq. 3.2)
  *   type 1    u_i = Re sum_j W_j rho_hat_j exp(+i k_j . x_i)                 (eq. 3.7)
  *   energy    E = (lambda / 2) h^d sum_i u_i rho_i                    (Remark 3.3)
@@ -69,6 +71,11 @@ typedef struct nlint_params {
     int w;               /* spreading width in fine cells; 0 = from eps                  */
     double sigma;        /* oversampling factor of the fine grid; 0 = 2                  */
     int device;          /* CUDA device ordinal; -1 = current device                     */
+    double axis2[3];     /* second dipole orientation m (eq. dipkerneldF, dipkernelF2dd);
+                            zero = same as axis (one orientation)                        */
+    double alpha;        /* 2.5D dipole constant alpha (eq. dipkernelF2d); 0 in 3D         */
+    int max_sub;         /* nodes per interpolation/spreading CTA; 0 = 1024 (FP32), 512 (FP64) */
+    int crowd_min;       /* bins above this many nodes sum their tiles in FP64; 0 = 4096    */
 } nlint_params;
 
 /* Read-only description of a plan. */
@@ -90,9 +97,11 @@ void nlint_params_default(nlint_params *p);
 
 /* Build a plan: nodes and weights in FP64 on the host, sorted into fine-grid tiles, uploaded
  * once; device workspaces allocated.  Algorithm 1 steps 1-3 (Section 3.2).
- * dipole_axis: 3 doubles for NLINT_DIPOLE (must be non-zero), NULL for Coulomb.
- * Errors: NLINT_EINVAL (d not 2/3, n odd or < 8, L <= 0, bad axis, 2D dipole),
- *         NLINT_ENOMEM, NLINT_ECUDA. */
+ * dipole_axis: 3 doubles for NLINT_DIPOLE (must be non-zero; normalised), NULL for Coulomb;
+ * one orientation, alpha = 0.  nlint_plan_create_ex also takes a second orientation (axis2)
+ * and the 2.5D constant alpha.
+ * Errors: NLINT_EINVAL (d not 2/3, n odd or < 8, L <= 0, zero axis), NLINT_EUNSUPPORTED
+ *         (fine grid above 2048 per axis), NLINT_ENOMEM, NLINT_ECUDA. */
 int nlint_plan_create(int d, int64_t n, double L, int kernel, const double *dipole_axis,
                       double eps, nlint_plan *out);
 int nlint_plan_create_ex(const nlint_params *p, nlint_plan *out);
@@ -136,6 +145,24 @@ int nlint_plan_nodes(nlint_plan plan, double *k_host, double *W_host);
 int nlint_set_stage_timing(nlint_plan plan, int enable);
 int nlint_stage_times(nlint_plan plan, float *ms, const char **names, int max_stages,
                       int *n_stages);
+
+/* Autotuner.  For the plan described by *in and a target relative L-inf error `tol` of u,
+ * picks (1) the smallest spreading width w whose error, measured on the device against an FP64
+ * plan with the widest stencil (same grid, nodes, cutoff and kernel) on a seeded probe
+ * density with content up to the grid's Nyquist radius, is at most tol/2, and (2) the fastest
+ * subproblem size (max_sub) among 256..2048 at that width.  *out = *in with w, max_sub and
+ * the precision (from tol when in->precision is -1) filled in; rep (may be NULL) reports the
+ * choice, its measured error and time.  The choice is cached as one JSON object per line in
+ * cache_path (NULL: $NLINT_TUNE_CACHE; neither: no cache); a cached key skips measurement.
+ * Synchronous; creates and destroys several plans (NLINT_ENOMEM etc. pass through). */
+typedef struct nlint_tune_report {
+    int w, max_sub;
+    double err;      /* measured relative L-inf error of the chosen width on the probe */
+    double ms;       /* median evaluation time of the choice                           */
+    int from_cache;  /* 1: read from the cache, nothing measured                      */
+} nlint_tune_report;
+int nlint_autotune(const nlint_params *in, double tol, const char *cache_path, nlint_params *out,
+                   nlint_tune_report *rep);
 
 /* Batched evaluation of independent densities (Algorithm 1 applied to each), e.g. grids of
  * mixed sizes, kernels and precisions.  nlint_batch_create: `count` plans (not owned: they

@@ -29,7 +29,8 @@ EXPORTED = [
     "nlint_plan_destroy", "nlint_eval", "nlint_eval_energy", "nlint_energy", "nlint_eval_host",
     "nlint_type2", "nlint_type1", "nlint_plan_nodes", "nlint_set_stage_timing",
     "nlint_stage_times", "nlint_launch_count", "nlint_energy_noalloc", "nlint_batch_create",
-    "nlint_batch_eval", "nlint_batch_info", "nlint_batch_destroy", "nlint_last_error",
+    "nlint_batch_eval", "nlint_batch_info", "nlint_batch_destroy", "nlint_autotune",
+    "nlint_last_error",
 ]
 
 
@@ -44,7 +45,14 @@ class nlint_params(ctypes.Structure):
                 ("kernel", ctypes.c_int), ("axis", ctypes.c_double * 3),
                 ("n_r", ctypes.c_int64), ("n_theta", ctypes.c_int64), ("n_phi", ctypes.c_int64),
                 ("P", ctypes.c_double), ("eps", ctypes.c_double), ("precision", ctypes.c_int),
-                ("w", ctypes.c_int), ("sigma", ctypes.c_double), ("device", ctypes.c_int)]
+                ("w", ctypes.c_int), ("sigma", ctypes.c_double), ("device", ctypes.c_int),
+                ("axis2", ctypes.c_double * 3), ("alpha", ctypes.c_double),
+                ("max_sub", ctypes.c_int), ("crowd_min", ctypes.c_int)]
+
+
+class nlint_tune_report(ctypes.Structure):
+    _fields_ = [("w", ctypes.c_int), ("max_sub", ctypes.c_int), ("err", ctypes.c_double),
+                ("ms", ctypes.c_double), ("from_cache", ctypes.c_int)]
 
 
 class nlint_info(ctypes.Structure):
@@ -97,6 +105,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.nlint_batch_info.argtypes = [vp, ctypes.POINTER(ci), ctypes.POINTER(ci), ctypes.POINTER(i64)]
     lib.nlint_batch_destroy.argtypes = [vp]
     lib.nlint_batch_destroy.restype = None
+    lib.nlint_autotune.argtypes = [ctypes.POINTER(nlint_params), dbl, ctypes.c_char_p,
+                                   ctypes.POINTER(nlint_params), ctypes.POINTER(nlint_tune_report)]
     lib.nlint_last_error.argtypes = []
     lib.nlint_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
@@ -125,10 +135,48 @@ def _stream_ptr(stream) -> int:
     return int(stream.cuda_stream)
 
 
+def make_params(d: int, n: int, L: float, kernel: str = "coulomb", axis=None, axis2=None,
+                alpha: float = 0.0, eps: float = 1e-6, precision: Optional[str] = None, nodes=None,
+                w: int = 0, sigma: float = 0.0, P: float = 0.0, device: int = -1,
+                max_sub: int = 0, crowd_min: int = 0) -> nlint_params:
+    """A filled nlint_params (the C-ABI's complete parameter set)."""
+    lib = load_library()
+    prm = nlint_params()
+    lib.nlint_params_default(ctypes.byref(prm))
+    prm.d, prm.n, prm.L = int(d), int(n), float(L)
+    prm.kernel = {"coulomb": NLINT_COULOMB, "dipole": NLINT_DIPOLE}[kernel]
+    for a in range(3):
+        prm.axis[a] = float(axis[a]) if axis is not None else 0.0
+        prm.axis2[a] = float(axis2[a]) if axis2 is not None else 0.0
+    prm.alpha = float(alpha)
+    if nodes is not None:
+        if d == 3:
+            prm.n_r, prm.n_theta, prm.n_phi = (int(v) for v in nodes)
+        else:
+            prm.n_r, prm.n_phi = (int(v) for v in nodes)
+    prm.eps = float(eps)
+    prm.precision = {None: -1, "fp32": NLINT_FP32, "fp64": NLINT_FP64}[precision]
+    prm.w, prm.sigma, prm.P, prm.device = int(w), float(sigma), float(P), int(device)
+    prm.max_sub, prm.crowd_min = int(max_sub), int(crowd_min)
+    return prm
+
+
+def autotune(params: nlint_params, tol: float, cache_path: Optional[str] = None):
+    """Tuned copy of ``params`` for relative L-inf tolerance ``tol`` and the tuner's report."""
+    lib = load_library()
+    out = nlint_params()
+    rep = nlint_tune_report()
+    _check(lib.nlint_autotune(ctypes.byref(params), float(tol),
+                              cache_path.encode() if cache_path else None, ctypes.byref(out),
+                              ctypes.byref(rep)))
+    return out, {f: getattr(rep, f) for f, _ in nlint_tune_report._fields_}
+
+
 class Plan:
     """A plan for u = U * rho and E = (lambda/2) <u, rho> on an n^d grid over [-L/2, L/2)^d.
 
-    kernel: "coulomb" (3D: 1/(4 pi |x|); 2D: 1/(2 pi |x|)) or "dipole" (3D, needs ``axis``).
+    kernel: "coulomb" (3D: 1/(4 pi |x|); 2D: 1/(2 pi |x|)) or "dipole" (needs ``axis``, a 3-vector;
+    ``axis2`` a second orientation, default the same; ``alpha`` the 2.5D constant).
     eps picks the precision (>= 1e-7: FP32, else FP64) and the spreading width unless given.
     nodes: (n_r, n_theta, n_phi) in 3D or (n_r, n_phi) in 2D; default from n.
     """
@@ -136,7 +184,9 @@ class Plan:
     def __init__(self, d: int, n: int, L: float, kernel: str = "coulomb",
                  axis: Optional[Sequence[float]] = None, eps: float = 1e-6,
                  precision: Optional[str] = None, nodes: Optional[Sequence[int]] = None,
-                 w: int = 0, sigma: float = 0.0, P: float = 0.0, device: Optional[int] = None):
+                 w: int = 0, sigma: float = 0.0, P: float = 0.0, device: Optional[int] = None,
+                 axis2: Optional[Sequence[float]] = None, alpha: float = 0.0,
+                 max_sub: int = 0, crowd_min: int = 0, params: Optional["nlint_params"] = None):
         lib = load_library()
         prm = nlint_params()
         lib.nlint_params_default(ctypes.byref(prm))
@@ -145,6 +195,10 @@ class Plan:
         if axis is not None:
             for a in range(3):
                 prm.axis[a] = float(axis[a])
+        if axis2 is not None:
+            for a in range(3):
+                prm.axis2[a] = float(axis2[a])
+        prm.alpha = float(alpha)
         if nodes is not None:
             if d == 3:
                 prm.n_r, prm.n_theta, prm.n_phi = (int(v) for v in nodes)
@@ -157,6 +211,10 @@ class Plan:
             torch = _torch()
             device = torch.cuda.current_device() if torch.cuda.is_available() else -1
         prm.device = int(device)
+        prm.max_sub, prm.crowd_min = int(max_sub), int(crowd_min)
+        if params is not None:  # a complete parameter set, e.g. from autotune()
+            prm = params
+            prm.device = int(device)
         h = ctypes.c_void_p()
         _check(lib.nlint_plan_create_ex(ctypes.byref(prm), ctypes.byref(h)))
         self._h = h
@@ -165,7 +223,7 @@ class Plan:
         _check(lib.nlint_plan_info(h, ctypes.byref(info)))
         self.info = {f: getattr(info, f) for f, _ in nlint_info._fields_}
         self.info["bin"] = tuple(info.bin)
-        self.d, self.n, self.L = d, n, L
+        self.d, self.n, self.L = int(info.d), int(info.n), float(info.L)
         self.device = int(device)
         self.precision = "fp32" if info.precision == NLINT_FP32 else "fp64"
 

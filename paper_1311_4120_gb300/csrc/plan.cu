@@ -108,7 +108,7 @@ struct nlint_plan_s {
     int d, prec, w, pad, n_fine;
     int64_t N, nr, nt, nphi, Nf, Mh;
     double L, h, P, sigma, beta;
-    double axis[3];
+    double axis[3], axis2[3], alpha;
     int device;
     // device memory
     int32_t *d_l0 = nullptr;
@@ -153,11 +153,20 @@ static int64_t default_nr(int d, int64_t n) {
     return std::max<int64_t>(8, r);
 }
 
+// Kernel symbols of table int3dd: eqs. Cou3D, Cou2D, dipkerneldF (dipkernelF when m = n) and
+// dipkernelF2dd (dipkernelF2d when m = n); n = axis, m = axis2, both unit vectors.
 static double u_hat(const nlint_plan_s *p, const double k[3]) {
     const double k2 = k[0] * k[0] + k[1] * k[1] + (p->d == 3 ? k[2] * k[2] : 0.0);
     if (p->prm.kernel == NLINT_COULOMB) return p->d == 3 ? 1.0 / k2 : 1.0 / std::sqrt(k2);
-    const double kn = k[0] * p->axis[0] + k[1] * p->axis[1] + k[2] * p->axis[2];
-    return -1.0 + 3.0 * kn * kn / k2;
+    const double *n = p->axis, *m = p->axis2;
+    if (p->d == 3) {
+        const double kn = k[0] * n[0] + k[1] * n[1] + k[2] * n[2];
+        const double km = k[0] * m[0] + k[1] * m[1] + k[2] * m[2];
+        const double mn = m[0] * n[0] + m[1] * n[1] + m[2] * n[2];
+        return -mn + 3.0 * kn * km / k2;
+    }
+    const double kn = k[0] * n[0] + k[1] * n[1], km = k[0] * m[0] + k[1] * m[1];
+    return -p->alpha + 3.0 * (kn * km - n[2] * m[2] * k2) / (2.0 * std::sqrt(k2));
 }
 
 // Fourier transform of the ES kernel, Phi(xi) = int_{-1}^{1} phi(z) cos(xi z) dz, by a
@@ -209,18 +218,24 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
     if (!(q.L > 0.0) || !std::isfinite(q.L)) return fail(NLINT_EINVAL, "L must be positive");
     if (q.kernel != NLINT_COULOMB && q.kernel != NLINT_DIPOLE)
         return fail(NLINT_EINVAL, "kernel must be NLINT_COULOMB or NLINT_DIPOLE");
-    if (q.kernel == NLINT_DIPOLE && q.d == 2)
-        return fail(NLINT_EUNSUPPORTED, "the 2.5D dipole kernel is not implemented");
+    if (q.max_sub < 0 || q.max_sub > (1 << 20)) return fail(NLINT_EINVAL, "max_sub must be in [0, 2^20]");
+    if (q.crowd_min < 0) return fail(NLINT_EINVAL, "crowd_min must be >= 0");
     p->d = q.d;
     p->N = q.n;
     p->L = q.L;
     p->h = q.L / (double)q.n;
+    p->alpha = 0.0;
     if (q.kernel == NLINT_DIPOLE) {
         const double nn = std::sqrt(q.axis[0] * q.axis[0] + q.axis[1] * q.axis[1] + q.axis[2] * q.axis[2]);
         if (!(nn > 0.0) || !std::isfinite(nn)) return fail(NLINT_EINVAL, "dipole axis must be non-zero");
         for (int a = 0; a < 3; a++) p->axis[a] = q.axis[a] / nn;
+        const double mm = std::sqrt(q.axis2[0] * q.axis2[0] + q.axis2[1] * q.axis2[1] + q.axis2[2] * q.axis2[2]);
+        if (!std::isfinite(mm)) return fail(NLINT_EINVAL, "second dipole axis must be finite");
+        for (int a = 0; a < 3; a++) p->axis2[a] = mm > 0.0 ? q.axis2[a] / mm : p->axis[a];
+        if (!std::isfinite(q.alpha)) return fail(NLINT_EINVAL, "alpha must be finite");
+        if (q.d == 2) p->alpha = q.alpha;
     } else {
-        p->axis[0] = p->axis[1] = p->axis[2] = 0.0;
+        for (int a = 0; a < 3; a++) p->axis[a] = p->axis2[a] = 0.0;
     }
     const double pmax = M_PI / p->h;
     p->P = (q.P > 0.0) ? q.P : pmax;
@@ -380,9 +395,9 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
         Ws[o] = hd * p->W_canon[half[s]];
     }
     // non-empty bins and their subproblems; crowded bins (FP32 plans) are summed in FP64
-    const int max_sub = (p->prec == NLINT_FP32) ? 1024 : 512;
-    const int max_sub_crowd = 512;
-    const int64_t crowd_min = 4096;
+    const int max_sub = q.max_sub > 0 ? q.max_sub : ((p->prec == NLINT_FP32) ? 1024 : 512);
+    const int max_sub_crowd = std::min(max_sub, 512);
+    const int64_t crowd_min = q.crowd_min > 0 ? q.crowd_min : 4096;
     std::vector<int4> bins, subs;
     std::vector<int32_t> crowd_bin;
     for (int64_t o = 0; o < Mh;) {

@@ -64,7 +64,8 @@ def _create(lib, **kw):
     (dict(L=-2.0), -1, "L must"),
     (dict(kernel=7), -1, "kernel"),
     (dict(kernel=1, axis=(0.0, 0.0, 0.0)), -1, "axis"),
-    (dict(d=2, kernel=1, axis=(1.0, 0.0, 0.0)), -5, "2.5D dipole"),
+    (dict(n=2048), -5, "2048"),
+    (dict(d=2, kernel=1, axis=(1.0, 0.0, 0.0), alpha=float("inf")), -1, "alpha"),
     (dict(P=100.0), -1, "P must"),
     (dict(w=40), -1, "width"),
     (dict(n_phi=63), -1, "n_phi"),

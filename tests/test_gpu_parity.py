@@ -208,3 +208,36 @@ def test_bad_tensor_arguments_raise(pkg):
         plan.eval(torch.zeros((32, 32, 32)))
     with pytest.raises(pkg.NlintError):
         pkg.Plan(3, 12, 6.0, eps=1e-12, device=0)   # fine grid too small for w = 13
+
+
+# --------------------------------------------------------------------------- other dipole kernels
+OTHER = [
+    # d, n, L, nodes, precision, axis, axis2, alpha
+    (3, 32, 12.0, (24, 24, 48), "fp64", (0.82778, 0.41505, -0.37751), (0.31180, 0.93780, -0.15214), 0.0),
+    (3, 48, 12.0, (32, 32, 64), "fp32", (0.3, -0.5, 0.8), (-0.7, 0.1, 0.2), 0.0),
+    (2, 64, 16.0, (40, 80), "fp64", (0.52460, -0.85135, 0.0), None, 0.0),
+    (2, 96, 16.0, (48, 96), "fp64", (0.3, -0.5, 0.8), (0.85125, -0.52476, 0.1), 0.7),
+    (2, 128, 20.0, (64, 128), "fp32", (-0.44404, -0.89600, 0.0), (0.85125, -0.52476, 0.0), -0.3),
+]
+
+
+@pytest.mark.parametrize("case", OTHER)
+def test_parity_two_axis_and_planar_dipoles(pkg, case):
+    d, n, L, nodes, prec, axis, axis2, alpha = case
+    rng = np.random.default_rng(n + 3 * d)
+    cen, wid, wts = synth.mixture_params(rng, 4, d, L / 8, 0.7, 1.3, 0.5, 1.0)
+    rho = synth.mixture(d, n, L, cen, wid, wts)
+    tol = 1e-5 if prec == "fp32" else 1e-10
+    plan = pkg.Plan(d, n, L, "dipole", axis=axis, axis2=axis2, alpha=alpha, nodes=nodes,
+                    precision=prec, eps=1e-6 if prec == "fp32" else 1e-12, device=0)
+    k, W = plan.nodes()
+    kr, Wr = quadrature.nodes_weights(d, n, L, nodes, "dipole", axis=axis, axis2=axis2, alpha=alpha)
+    assert np.max(np.abs(W - Wr)) <= 1e-13 * np.max(np.abs(Wr))
+    dt = torch.float32 if prec == "fp32" else torch.float64
+    u, E = plan.eval_energy(torch.from_numpy(rho).to("cuda:0", dt), lam=1.3)
+    torch.cuda.synchronize()
+    ref = pipeline.oracle_eval(rho, L, nodes, "dipole", axis=axis, axis2=axis2, alpha=alpha,
+                               lam=1.3, setting="parity")
+    err = rel_inf(u.double().cpu().numpy(), ref["u"])
+    assert err <= tol, f"rel L-inf {err:.3e}"
+    assert abs(float(E.item()) - ref["E"]) <= tol * ref["E_scale"]
