@@ -123,6 +123,15 @@ int nlint_eval_energy(nlint_plan plan, const void *rho_dev, void *u_dev, double 
 int nlint_energy(nlint_plan plan, const void *rho_dev, const void *u_dev, double lambda,
                  double *E_dev, double *E_host, void *stream);
 
+/* Energy without the potential: E = (lambda/2) sum_j W_j |rho_hat_j|^2 (eq. 3.7 substituted
+ * into the trapezoidal energy of Remark 3.3; for the discrete operator this equals
+ * (lambda/2) h^d sum_i u_i rho_i up to the NUFFT tolerance).  Runs the type-2 half of the path
+ * only (forward FFT passes and interpolation), about half the work of nlint_eval_energy.
+ * E_dev (device double) and/or E_host may be NULL; a non-NULL E_host synchronises `stream`.
+ * The sum is compensated and taken in a fixed order. */
+int nlint_energy_only(nlint_plan plan, const void *rho_dev, double lambda, double *E_dev,
+                      double *E_host, void *stream);
+
 /* End-to-end form with HOST buffers: copies rho_host to the device, evaluates u and E,
  * copies u back to u_host and E to *E_host (E_host may be NULL), and synchronises
  * `stream`.  Pinned host memory gives the fastest copies. */

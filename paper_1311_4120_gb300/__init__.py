@@ -30,7 +30,7 @@ EXPORTED = [
     "nlint_type2", "nlint_type1", "nlint_plan_nodes", "nlint_set_stage_timing",
     "nlint_stage_times", "nlint_launch_count", "nlint_energy_noalloc", "nlint_batch_create",
     "nlint_batch_eval", "nlint_batch_info", "nlint_batch_destroy", "nlint_autotune",
-    "nlint_last_error",
+    "nlint_energy_only", "nlint_last_error",
 ]
 
 
@@ -107,6 +107,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.nlint_batch_destroy.restype = None
     lib.nlint_autotune.argtypes = [ctypes.POINTER(nlint_params), dbl, ctypes.c_char_p,
                                    ctypes.POINTER(nlint_params), ctypes.POINTER(nlint_tune_report)]
+    lib.nlint_energy_only.argtypes = [vp, vp, dbl, vp, ctypes.POINTER(dbl), vp]
     lib.nlint_last_error.argtypes = []
     lib.nlint_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
@@ -275,6 +276,15 @@ class Plan:
                                       self._dev(u, self.grid_shape, self.dtype, "u"), float(lam),
                                       None, ctypes.byref(Eh), _stream_ptr(stream)))
         return Eh.value
+
+    def energy_only(self, rho, lam: float = 1.0, E_out=None, stream=None):
+        """E = (lam/2) sum_j W_j |rho_hat_j|^2 from the type-2 half of the path (no potential).
+        Returns a device float64 scalar tensor (no synchronisation)."""
+        torch = _torch()
+        E = E_out if E_out is not None else torch.empty((), dtype=torch.float64, device=rho.device)
+        _check(self._lib.nlint_energy_only(self._h, self._dev(rho, self.grid_shape, self.dtype, "rho"),
+                                           float(lam), E.data_ptr(), None, _stream_ptr(stream)))
+        return E
 
     def eval_host(self, rho_host, lam: float = 1.0, u_host=None, stream=None):
         """End-to-end call with host buffers (numpy arrays or CPU tensors, pinned is best)."""

@@ -122,9 +122,11 @@ static constexpr int NODE_THREADS = 256;  // threads per interpolation / spreadi
 int tile_cells(const NodeDesc &nd);
 size_t node_smem(const NodeDesc &nd, int prec);
 
+// c_out[j] = (apply_W ? W_j : 1) rho_hat_j / h^d; with epart != NULL nothing is written to
+// c_out and each CTA writes sum_j W_j |rho_hat_j / h^d|^2 over its nodes to epart[cta]
 template <typename T>
 cudaError_t launch_interp(const NodeDesc &nd, const void *G, void *c_out, int apply_W,
-                          cudaStream_t s);
+                          cudaStream_t s, double2 *epart = nullptr);
 template <typename T>
 cudaError_t launch_spread(const NodeDesc &nd, const void *c_in, void *Hext, cudaStream_t s);
 template <typename T>
@@ -132,7 +134,7 @@ cudaError_t launch_crowd_merge(const NodeDesc &nd, void *Hext, cudaStream_t s);
 // per (precision, dimension) launchers, one translation unit each (width dispatch inside)
 template <typename T, int D>
 cudaError_t launch_interp_d(const NodeDesc &nd, const void *G, void *c_out, int apply_W,
-                            cudaStream_t s);
+                            double2 *epart, cudaStream_t s);
 template <typename T, int D>
 cudaError_t launch_spread_d(const NodeDesc &nd, const void *c_in, void *Hext, cudaStream_t s);
 template <typename T, int D>

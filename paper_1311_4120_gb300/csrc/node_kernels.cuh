@@ -168,11 +168,12 @@ template <> struct FixAcc<double> {
     }
 };
 
-template <typename T, int D, int W>
+template <typename T, int D, int W, bool EN>
 __global__ void __launch_bounds__(SUB_THREADS) interp_sub_kernel(NodeDesc nd,
                                                                 const cx_t<T> *__restrict__ G,
                                                                 cx_t<T> *__restrict__ c_out,
-                                                                int apply_W) {
+                                                                int apply_W,
+                                                                double2 *__restrict__ epart) {
     using T2 = cx_t<T>;
     using G_ = Geo<T, D, W>;
     constexpr int PASSES = G_::PASSES, L = (D == 3) ? W : 1, PLANE = G_::T1 * G_::T2;
@@ -211,6 +212,7 @@ __global__ void __launch_bounds__(SUB_THREADS) interp_sub_kernel(NodeDesc nd,
     const int half = lane / G_::LPN, hl = lane % G_::LPN;  // node of the group, lane in it
     const T *kh = ker + half * 3 * MAXW;  // this lane's node's kernel values
     NodeGroup<T, D, W> cur, nxt;
+    EAcc<T> eacc;  // energy-only mode: sum of W_j |rho_hat_j|^2 over this lane's nodes
     if (ja < jb) cur.load(nd, ja, jb, lane, bo);
     for (int j = ja; j < jb; j += G_::NPW) {
         if (j + G_::NPW < jb) nxt.load(nd, j + G_::NPW, jb, lane, bo);  // prefetch the next group
@@ -247,9 +249,17 @@ __global__ void __launch_bounds__(SUB_THREADS) interp_sub_kernel(NodeDesc nd,
             accr += __shfl_xor_sync(0xffffffffu, accr, off);
             acci += __shfl_xor_sync(0xffffffffu, acci, off);
         }
-        if (hl == 0 && act) c_out[mine] = cmake<T2>(accr * Wj, acci * Wj);
+        if (hl == 0 && act) {
+            if constexpr (EN) eacc.add(Wj * (accr * accr + acci * acci), T(1));  // W_j |rho_hat_j|^2
+            else c_out[mine] = cmake<T2>(accr * Wj, acci * Wj);
+        }
         __syncwarp();
         cur = nxt;
+    }
+    if constexpr (EN) {  // energy-only mode: one compensated partial per CTA
+        __syncthreads();
+        const double2 tot = energy_block_sum(eacc, reinterpret_cast<double *>(smem_raw));
+        if (threadIdx.x == 0) epart[blockIdx.x] = tot;
     }
 }
 
@@ -387,12 +397,20 @@ __global__ void __launch_bounds__(SUB_THREADS) spread_sub_kernel(NodeDesc nd,
 
 template <typename T, int D, int W>
 static cudaError_t launch_interp_w(const NodeDesc &nd, const void *G, void *c_out, int apply_W,
-                                   size_t smem, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(interp_sub_kernel<T, D, W>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    interp_sub_kernel<T, D, W><<<(unsigned)nd.nsub, SUB_THREADS, smem, s>>>(
-        nd, (const cx_t<T> *)G, (cx_t<T> *)c_out, apply_W);
+                                   double2 *epart, size_t smem, cudaStream_t s) {
+    if (epart) {
+        cudaError_t e = cudaFuncSetAttribute(interp_sub_kernel<T, D, W, true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        interp_sub_kernel<T, D, W, true><<<(unsigned)nd.nsub, SUB_THREADS, smem, s>>>(
+            nd, (const cx_t<T> *)G, (cx_t<T> *)c_out, apply_W, epart);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(interp_sub_kernel<T, D, W, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        interp_sub_kernel<T, D, W, false><<<(unsigned)nd.nsub, SUB_THREADS, smem, s>>>(
+            nd, (const cx_t<T> *)G, (cx_t<T> *)c_out, apply_W, nullptr);
+    }
     return cudaGetLastError();
 }
 
@@ -453,10 +471,10 @@ cudaError_t launch_crowd_merge_d(const NodeDesc &nd, void *H, cudaStream_t s) {
 
 template <typename T, int D>
 cudaError_t launch_interp_d(const NodeDesc &nd, const void *G, void *c_out, int apply_W,
-                            cudaStream_t s) {
+                            double2 *epart, cudaStream_t s) {
     if (nd.nsub == 0) return cudaSuccess;
     const size_t sm = node_smem(nd, sizeof(T) == 4 ? NLINT_FP32 : NLINT_FP64);
-#define NLINT_CALL_I(WW) launch_interp_w<T, D, WW>(nd, G, c_out, apply_W, sm, s)
+#define NLINT_CALL_I(WW) launch_interp_w<T, D, WW>(nd, G, c_out, apply_W, epart, sm, s)
     NLINT_W_SWITCH(NLINT_CALL_I)
 #undef NLINT_CALL_I
 }
@@ -472,7 +490,7 @@ cudaError_t launch_spread_d(const NodeDesc &nd, const void *c_in, void *H, cudaS
 
 #define NLINT_NODE_KERNELS_INSTANTIATE(T, D)                                                    \
     template cudaError_t launch_interp_d<T, D>(const NodeDesc &, const void *, void *, int,      \
-                                               cudaStream_t);                                  \
+                                               double2 *, cudaStream_t);                       \
     template cudaError_t launch_spread_d<T, D>(const NodeDesc &, const void *, void *,           \
                                                cudaStream_t);                                  \
     template cudaError_t launch_crowd_merge_d<T, D>(const NodeDesc &, void *, cudaStream_t);

@@ -73,9 +73,9 @@ static inline unsigned nblk(int64_t M, int t) { return (unsigned)((M + t - 1) / 
 
 template <typename T>
 cudaError_t launch_interp(const NodeDesc &nd, const void *G, void *c_out, int apply_W,
-                          cudaStream_t s) {
-    return nd.d == 3 ? launch_interp_d<T, 3>(nd, G, c_out, apply_W, s)
-                     : launch_interp_d<T, 2>(nd, G, c_out, apply_W, s);
+                          cudaStream_t s, double2 *epart) {
+    return nd.d == 3 ? launch_interp_d<T, 3>(nd, G, c_out, apply_W, epart, s)
+                     : launch_interp_d<T, 2>(nd, G, c_out, apply_W, epart, s);
 }
 
 template <typename T>
@@ -121,7 +121,8 @@ cudaError_t launch_energy_final(const double2 *partials, int nparts, double scal
 }
 
 #define NLINT_INST(T)                                                                              \
-    template cudaError_t launch_interp<T>(const NodeDesc &, const void *, void *, int, cudaStream_t); \
+    template cudaError_t launch_interp<T>(const NodeDesc &, const void *, void *, int, cudaStream_t, \
+                                          double2 *);                                             \
     template cudaError_t launch_spread<T>(const NodeDesc &, const void *, void *, cudaStream_t);      \
     template cudaError_t launch_crowd_merge<T>(const NodeDesc &, void *, cudaStream_t);              \
     template cudaError_t launch_scatter_canonical<T>(int64_t, const void *, const int32_t *,         \

@@ -116,6 +116,7 @@ struct nlint_plan_s {
     int32_t *d_perm = nullptr, *d_mirror = nullptr;
     int4 *d_subs = nullptr, *d_bins = nullptr;
     int16_t *d_pairs = nullptr;
+    double2 *d_epart = nullptr;  // energy-only path: one partial per subproblem
     int32_t *d_crowd_bin = nullptr;
     double2 *d_crowd = nullptr;
     int B[3], T[3];
@@ -202,7 +203,7 @@ static int upload(void **dst, const std::vector<double> &v, size_t &acc) {
 
 static void plan_free(nlint_plan_s *p) {
     void *ptrs[] = {p->d_l0, p->d_frac, p->d_W, p->d_fac, p->d_tw, p->d_perm, p->d_mirror,
-                    p->d_subs, p->d_bins, p->d_crowd_bin, p->d_crowd, p->d_pairs,
+                    p->d_subs, p->d_bins, p->d_crowd_bin, p->d_crowd, p->d_pairs, p->d_epart,
                     p->d_bufA, p->d_bufB, p->d_bufG, p->d_c, p->d_partials, p->d_E,
                     p->d_rho_io, p->d_u_io};
     for (void *q : ptrs)
@@ -573,6 +574,8 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
     CK(cudaMalloc(&p->d_bufG, std::max(p->bytes_G, p->bytes_Hext)));
     CK(cudaMalloc(&p->d_c, p->bytes_c + cs));
     CK(cudaMalloc((void **)&p->d_partials, sizeof(double2) * (size_t)std::max(p->n_partials, 1024)));
+    CK(cudaMalloc((void **)&p->d_epart, sizeof(double2) * (size_t)std::max<int64_t>(p->nsub, 1)));
+    acc += sizeof(double2) * (size_t)p->nsub;
     CK(cudaMalloc((void **)&p->d_E, sizeof(double)));
     acc += p->bytes_A + p->bytes_B + std::max(p->bytes_G, p->bytes_Hext) + p->bytes_c +
            sizeof(double2) * (size_t)std::max(p->n_partials, 1024);
@@ -825,6 +828,33 @@ int nlint_energy(nlint_plan p, const void *rho, const void *u, double lambda, do
     else CK(launch_energy_partials<double>(count, u, rho, p->d_partials, nb, s));
     double *E = E_dev ? E_dev : p->d_E;
     CK(launch_energy_final(p->d_partials, nb, 0.5 * lambda * std::pow(p->h, p->d), E, s));
+    p->launches += 2;
+    if (E_host) {
+        CK(cudaMemcpyAsync(E_host, E, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
+    return NLINT_OK;
+}
+
+int nlint_energy_only(nlint_plan p, const void *rho, double lambda, double *E_dev, double *E_host,
+                      void *stream) {
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!rho) return fail(NLINT_EINVAL, "NULL rho");
+    cudaStream_t s = (cudaStream_t)stream;
+    p->ev_used = 0;
+    // E = (lambda/2) sum_j W_j |rho_hat_j|^2 over the full node set = lambda sum over the half
+    // set (W and |rho_hat| are even under k -> -k); the kernel sums (h^d W_j) |rho_hat_j/h^d|^2
+    const double scale = lambda * std::pow(p->h, p->d);
+    if (p->prec == NLINT_FP32) {
+        if ((rc = run_type2<float>(p, rho, s))) return rc;
+        CK(launch_interp<float>(node_desc(p), p->d_bufG, nullptr, 1, s, p->d_epart));
+    } else {
+        if ((rc = run_type2<double>(p, rho, s))) return rc;
+        CK(launch_interp<double>(node_desc(p), p->d_bufG, nullptr, 1, s, p->d_epart));
+    }
+    double *E = E_dev ? E_dev : p->d_E;
+    CK(launch_energy_final(p->d_epart, (int)p->nsub, scale, E, s));
     p->launches += 2;
     if (E_host) {
         CK(cudaMemcpyAsync(E_host, E, sizeof(double), cudaMemcpyDeviceToHost, s));

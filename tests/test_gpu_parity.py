@@ -241,3 +241,22 @@ def test_parity_two_axis_and_planar_dipoles(pkg, case):
     err = rel_inf(u.double().cpu().numpy(), ref["u"])
     assert err <= tol, f"rel L-inf {err:.3e}"
     assert abs(float(E.item()) - ref["E"]) <= tol * ref["E_scale"]
+
+
+# --------------------------------------------------------------------------- energy-only path
+@pytest.mark.parametrize("name", ["c1", "c2", "c3"])
+def test_energy_only_matches_oracle_dual_energy(pkg, name):
+    wl = synth.CONFIGS[name]()
+    rho = wl.rho()
+    setting = "fp32ref" if wl.precision == "fp32" else "parity"
+    ref = pipeline.oracle_eval(rho, wl.L, wl.nodes, wl.kernel, axis=wl.axis, setting=setting, lam=1.7)
+    plan = pkg.Plan(wl.d, wl.n, wl.L, wl.kernel, axis=wl.axis, nodes=wl.nodes, precision=wl.precision,
+                    eps=1e-6 if wl.precision == "fp32" else 1e-12, device=0)
+    dt = torch.float32 if wl.precision == "fp32" else torch.float64
+    r = torch.from_numpy(rho).to("cuda:0", dt)
+    E = float(plan.energy_only(r, lam=1.7).item())
+    _, E2 = plan.eval_energy(r, lam=1.7)
+    torch.cuda.synchronize()
+    tol = wl.tol
+    assert abs(E - ref["E_dual"]) <= tol * ref["E_scale"], (E, ref["E_dual"])
+    assert abs(E - float(E2.item())) <= tol * ref["E_scale"]
