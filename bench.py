@@ -360,6 +360,30 @@ def run_ours(args, rank, world, local_rank):
     e2e = {"value": points / t_e2e, "unit": UNIT, "h2d_bytes_per_step": rho_np.nbytes,
            "d2h_bytes_per_step": rho_np.nbytes + 8}
 
+    # ---- the same operator in its precomputed Toeplitz form (FFT passes only per evaluation)
+    toep = None
+    if not args.no_toeplitz:
+        t0 = time.perf_counter()
+        plan.toeplitz()
+        t_pre = time.perf_counter() - t0
+        ut = torch.empty_like(u)
+        Et = torch.empty((), dtype=torch.float64, device=dev)
+        for _ in range(args.warmup):
+            plan.eval_toeplitz(rho, lam=wl.lam, out=ut, E_out=Et)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            ev[2 * k].record(stream)
+            plan.eval_toeplitz(rho, lam=wl.lam, out=ut, E_out=Et)
+            ev[2 * k + 1].record(stream)
+        torch.cuda.synchronize()
+        ms_t = sum(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(args.steps)) / args.steps
+        toep = {"value": wl.n_points / (ms_t / 1e3), "unit": UNIT, "ms_per_step": ms_t,
+                "precompute_s": t_pre,
+                "rel_linf_vs_nufft_path": float((ut.double() - u32.double()).abs().max()
+                                                / u32.double().abs().max()),
+                "energy": float(Et.item())}
+
     # ---- the same workload on the FP64 GPU path: speedup and the FP32 result's error
     fp64 = None
     if not args.no_fp64:
@@ -427,6 +451,7 @@ def run_ours(args, rank, world, local_rank):
         "fp64_gpu": fp64,
         "speedup_fp32_vs_fp64_gpu": (fp64["ms_per_step"] / ms_step) if fp64 else None,
         "batched": batched,
+        "toeplitz_form": toep,
         "stages_ms": {k: round(v, 4) for k, v in mean_stage.items()},
         "path_bytes_per_step": path_bytes(info),
         "path_frac_of_hbm": path_gbs / peak,
@@ -450,6 +475,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-density batched form")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
+    ap.add_argument("--no-toeplitz", action="store_true", help="skip the precomputed-kernel form")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

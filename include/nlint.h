@@ -132,6 +132,20 @@ int nlint_energy(nlint_plan plan, const void *rho_dev, const void *u_dev, double
 int nlint_energy_only(nlint_plan plan, const void *rho_dev, double lambda, double *E_dev,
                       double *E_host, void *stream);
 
+/* Precomputed Toeplitz form of the same discrete operator.  u = K rho with the translation-
+ * invariant kernel K(dx) = h^d Re sum_j W_j exp(i k_j . dx) (eq. 3.2 substituted into eq. 3.7).
+ * nlint_plan_toeplitz computes K on dx in [-N, N)^d cells with 2^d type-1 NUFFTs of the plan
+ * itself, and its DFT K_hat on the plan's oversampled grid (n_fine >= 2N, so the circular
+ * convolution equals the linear one on the grid); it allocates K_hat (real, Hermitian half) and
+ * synchronises `stream`.  nlint_eval_toeplitz then computes u (and E if E_dev != NULL) with the
+ * FFT passes only: zero-padded forward FFT of rho, multiply by K_hat (fused into the first
+ * inverse pass), inverse FFT, crop.  The result equals nlint_eval_energy's to the NUFFT
+ * tolerance; no interpolation or spreading runs per evaluation.  This form is not in the paper:
+ * it follows from the operator's Toeplitz structure. */
+int nlint_plan_toeplitz(nlint_plan plan, void *stream);
+int nlint_eval_toeplitz(nlint_plan plan, const void *rho_dev, void *u_dev, double lambda,
+                        double *E_dev, void *stream);
+
 /* End-to-end form with HOST buffers: copies rho_host to the device, evaluates u and E,
  * copies u back to u_host and E to *E_host (E_host may be NULL), and synchronises
  * `stream`.  Pinned host memory gives the fastest copies. */

@@ -30,7 +30,7 @@ EXPORTED = [
     "nlint_type2", "nlint_type1", "nlint_plan_nodes", "nlint_set_stage_timing",
     "nlint_stage_times", "nlint_launch_count", "nlint_energy_noalloc", "nlint_batch_create",
     "nlint_batch_eval", "nlint_batch_info", "nlint_batch_destroy", "nlint_autotune",
-    "nlint_energy_only", "nlint_last_error",
+    "nlint_energy_only", "nlint_plan_toeplitz", "nlint_eval_toeplitz", "nlint_last_error",
 ]
 
 
@@ -108,6 +108,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.nlint_autotune.argtypes = [ctypes.POINTER(nlint_params), dbl, ctypes.c_char_p,
                                    ctypes.POINTER(nlint_params), ctypes.POINTER(nlint_tune_report)]
     lib.nlint_energy_only.argtypes = [vp, vp, dbl, vp, ctypes.POINTER(dbl), vp]
+    lib.nlint_plan_toeplitz.argtypes = [vp, vp]
+    lib.nlint_eval_toeplitz.argtypes = [vp, vp, vp, dbl, vp, vp]
     lib.nlint_last_error.argtypes = []
     lib.nlint_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
@@ -276,6 +278,20 @@ class Plan:
                                       self._dev(u, self.grid_shape, self.dtype, "u"), float(lam),
                                       None, ctypes.byref(Eh), _stream_ptr(stream)))
         return Eh.value
+
+    def toeplitz(self, stream=None):
+        """Precompute the Toeplitz kernel's DFT (synchronous); enables eval_toeplitz."""
+        _check(self._lib.nlint_plan_toeplitz(self._h, _stream_ptr(stream)))
+
+    def eval_toeplitz(self, rho, lam: float = 1.0, out=None, E_out=None, stream=None):
+        """u (and E) by the precomputed-kernel FFT convolution (same operator as eval)."""
+        torch = _torch()
+        u = out if out is not None else torch.empty(self.grid_shape, dtype=self.dtype, device=rho.device)
+        E = E_out if E_out is not None else torch.empty((), dtype=torch.float64, device=rho.device)
+        _check(self._lib.nlint_eval_toeplitz(self._h, self._dev(rho, self.grid_shape, self.dtype, "rho"),
+                                             self._dev(u, self.grid_shape, self.dtype, "u"), float(lam),
+                                             E.data_ptr(), _stream_ptr(stream)))
+        return u, E
 
     def energy_only(self, rho, lam: float = 1.0, E_out=None, stream=None):
         """E = (lam/2) sum_j W_j |rho_hat_j|^2 from the type-2 half of the path (no potential).

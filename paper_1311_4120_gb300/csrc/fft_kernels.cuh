@@ -129,6 +129,7 @@ struct LineIO {
     int64_t in_st, out_st;      // element stride along the line
     T bfac;                     // deconvolution product over the other axes
     int64_t mirror_base;        // fold: the mirrored line of H+, or -1
+    const T *mult;              // IN_CPLX_MULT: multiplier row (same layout as the input)
 
     // FFT-index entry e of the input line (zero outside the stored modes)
     __device__ __forceinline__ T2 load(int e, const void *vin) const {
@@ -154,6 +155,9 @@ struct LineIO {
             case IN_CPLX_HERM:
                 v = (e <= n / 2) ? reinterpret_cast<const T2 *>(vin)[in_base + e * in_st]
                                  : cconj(reinterpret_cast<const T2 *>(vin)[in_base + (n - e) * in_st]);
+                break;
+            case IN_CPLX_MULT:
+                v = cscale(reinterpret_cast<const T2 *>(vin)[in_base + e], mult[in_base + e]);
                 break;
             default: {  // IN_CPLX_FOLD: H[l] = H+[l] + conj(H+[-l])
                 const T2 *in = reinterpret_cast<const T2 *>(vin);
@@ -190,6 +194,7 @@ __global__ void __launch_bounds__(FftCfg<T, NF>::threads(ROW)) fft_pass_kernel(
     io.kind = P.in_kind;
     io.fac = reinterpret_cast<const T *>(P.fac);
     io.mirror_base = -1;
+    io.mult = reinterpret_cast<const T *>(P.mult);
     io.bfac = T(1);
     if (!ROW) {
         const int64_t tiles = (P.I + B - 1) / B;

@@ -22,7 +22,8 @@ enum InKind {
     IN_CPLX_MODES = 1,   // N complex at centred mode positions
     IN_CPLX_FULL = 2,    // n complex
     IN_CPLX_HERM = 3,    // n/2+1 complex of a Hermitian line (rest by conjugate symmetry)
-    IN_CPLX_FOLD = 4     // row pass only: n complex plus the conjugated mirror row (fold)
+    IN_CPLX_FOLD = 4,    // row pass only: n complex plus the conjugated mirror row (fold)
+    IN_CPLX_MULT = 5     // row pass only: n complex times a real n-entry row of `mult`
 };
 enum OutKind {
     OUT_CPLX_FULL = 0,   // n complex
@@ -49,6 +50,7 @@ struct PassDesc {
     int64_t fold_plane;  // elements per plane of the slowest axis (rows per plane * n)
     int64_t fold_rows_per_plane;
     const void *fac;     // deconvolution factors, length N (plan precision)
+    const void *mult;    // IN_CPLX_MULT: real multiplier, same row layout as the input
     const void *rho;     // energy: density (OUT_REAL_MODES)
     double2 *partials;   // energy: one compensated partial per CTA (OUT_REAL_MODES)
 };
@@ -152,5 +154,12 @@ cudaError_t launch_energy_partials(int64_t count, const void *u, const void *rho
                                    double2 *partials, int nblocks, cudaStream_t s);
 cudaError_t launch_energy_final(const double2 *partials, int nparts, double scale, double *E,
                                 cudaStream_t s);
+// Toeplitz kernel assembly: an N^d block into an n^d array at cell offsets off = (slowest,
+// middle, fastest array axis; 2D: slowest, -, fastest)
+template <typename T>
+cudaError_t launch_place_block(int d, int64_t N, int64_t n, int3 off, const void *u, double scale,
+                               void *K, cudaStream_t s);
+template <typename T>
+cudaError_t launch_extract_real(int64_t cnt, const void *G, double scale, void *khat, cudaStream_t s);
 
 }  // namespace nlint

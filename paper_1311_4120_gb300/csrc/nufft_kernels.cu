@@ -68,7 +68,50 @@ __global__ void __launch_bounds__(1024) energy_final_kernel(const double2 *__res
     if (threadIdx.x == 0) *E = scale * tot.value();
 }
 
+// Toeplitz kernel assembly: K[a] = scale * u[i] for an N^d block u placed in an n^d array at
+// cell offsets off = (slowest axis, middle axis, fastest axis); in 2D off.y is unused.
+template <typename T>
+__global__ void place_block_kernel(int d, int64_t N, int64_t n, int3 off, const T *__restrict__ u,
+                                   double scale, T *__restrict__ K) {
+    const int64_t cnt = (d == 3) ? N * N * N : N * N;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cnt) return;
+    const int64_t ix = i % N, r = i / N;
+    int64_t a;
+    if (d == 3) {
+        const int64_t iy = r % N, iz = r / N;
+        a = ((iz + off.x) * n + (iy + off.y)) * n + (ix + off.z);
+    } else {
+        a = (r + off.x) * n + (ix + off.z);
+    }
+    K[a] = (T)(scale * (double)u[i]);
+}
+
+// khat[i] = scale * Re(G[i])
+template <typename T>
+__global__ void extract_real_kernel(int64_t cnt, const cx_t<T> *__restrict__ G, double scale,
+                                    T *__restrict__ khat) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < cnt) khat[i] = (T)(scale * (double)G[i].x);
+}
+
 // --------------------------------------------------------------------------- launchers
+template <typename T>
+cudaError_t launch_place_block(int d, int64_t N, int64_t n, int3 off, const void *u, double scale,
+                               void *K, cudaStream_t s) {
+    const int64_t cnt = (d == 3) ? N * N * N : N * N;
+    place_block_kernel<T><<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(d, N, n, off, (const T *)u,
+                                                                       scale, (T *)K);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_extract_real(int64_t cnt, const void *G, double scale, void *khat, cudaStream_t s) {
+    extract_real_kernel<T><<<(unsigned)((cnt + 255) / 256), 256, 0, s>>>(cnt, (const cx_t<T> *)G, scale,
+                                                                         (T *)khat);
+    return cudaGetLastError();
+}
+
 static inline unsigned nblk(int64_t M, int t) { return (unsigned)((M + t - 1) / t); }
 
 template <typename T>
@@ -125,6 +168,9 @@ cudaError_t launch_energy_final(const double2 *partials, int nparts, double scal
                                           double2 *);                                             \
     template cudaError_t launch_spread<T>(const NodeDesc &, const void *, void *, cudaStream_t);      \
     template cudaError_t launch_crowd_merge<T>(const NodeDesc &, void *, cudaStream_t);              \
+    template cudaError_t launch_place_block<T>(int, int64_t, int64_t, int3, const void *, double,    \
+                                               void *, cudaStream_t);                                \
+    template cudaError_t launch_extract_real<T>(int64_t, const void *, double, void *, cudaStream_t); \
     template cudaError_t launch_scatter_canonical<T>(int64_t, const void *, const int32_t *,         \
                                                      const int32_t *, double, void *, cudaStream_t); \
     template cudaError_t launch_gather_canonical<T>(int64_t, const void *, const int32_t *,          \

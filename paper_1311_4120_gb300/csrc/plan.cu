@@ -131,6 +131,10 @@ struct nlint_plan_s {
     size_t bytes_A = 0, bytes_B = 0, bytes_G = 0, bytes_Hext = 0, bytes_c = 0;
     size_t ws_bytes = 0;
     nlint::PassDesc P1, P2, P3, Q1, Q2, Q3;
+    // precomputed Toeplitz kernel (nlint_plan_toeplitz): K_hat on the Hermitian half grid
+    void *d_fac1 = nullptr, *d_khat = nullptr;
+    bool toeplitz = false;
+    nlint::PassDesc T1, U1, U3;
     // host copies for inspection (canonical order)
     std::vector<double> k_canon, W_canon;
     // stage timing
@@ -203,7 +207,7 @@ static int upload(void **dst, const std::vector<double> &v, size_t &acc) {
 
 static void plan_free(nlint_plan_s *p) {
     void *ptrs[] = {p->d_l0, p->d_frac, p->d_W, p->d_fac, p->d_tw, p->d_perm, p->d_mirror,
-                    p->d_subs, p->d_bins, p->d_crowd_bin, p->d_crowd, p->d_pairs, p->d_epart,
+                    p->d_subs, p->d_bins, p->d_crowd_bin, p->d_crowd, p->d_pairs, p->d_epart, p->d_fac1, p->d_khat,
                     p->d_bufA, p->d_bufB, p->d_bufG, p->d_c, p->d_partials, p->d_E,
                     p->d_rho_io, p->d_u_io};
     for (void *q : ptrs)
@@ -688,6 +692,39 @@ static int run_eval(nlint_plan_s *p, const void *rho, void *u, double lambda, do
     return NLINT_OK;
 }
 
+template <typename T>
+static int run_toeplitz(nlint_plan_s *p, const void *rho, void *u, double lambda, double *E,
+                        cudaStream_t s) {
+    p->ev_used = 0;
+    stage_mark(p, s, "start");
+    CK(launch_colpass<T>(p->T1, rho, p->d_bufA, p->d_tw, s));
+    if (p->d == 3) {
+        CK(launch_colpass<T>(p->P2, p->d_bufA, p->d_bufB, p->d_tw, s));
+        CK(launch_rowpass<T>(p->P3, p->d_bufB, p->d_bufG, p->d_tw, s));
+    } else {
+        CK(launch_rowpass<T>(p->P3, p->d_bufA, p->d_bufG, p->d_tw, s));
+    }
+    stage_mark(p, s, "fwd_fft");
+    PassDesc u3 = p->U3;
+    u3.rho = E ? rho : nullptr;
+    u3.partials = E ? p->d_partials : nullptr;
+    if (p->d == 3) {
+        CK(launch_rowpass<T>(p->U1, p->d_bufG, p->d_bufB, p->d_tw, s));
+        CK(launch_colpass<T>(p->Q2, p->d_bufB, p->d_bufA, p->d_tw, s));
+    } else {
+        CK(launch_rowpass<T>(p->U1, p->d_bufG, p->d_bufA, p->d_tw, s));
+    }
+    CK(launch_colpass<T>(u3, p->d_bufA, u, p->d_tw, s));
+    stage_mark(p, s, "multiply_inv_fft");
+    p->launches += (p->d == 3) ? 6 : 4;
+    if (E) {
+        CK(launch_energy_final(p->d_partials, p->n_partials, 0.5 * lambda * std::pow(p->h, p->d), E, s));
+        p->launches += 1;
+        stage_mark(p, s, "energy");
+    }
+    return NLINT_OK;
+}
+
 static int check_plan(nlint_plan p) {
     if (!p) return fail(NLINT_EINVAL, "plan is NULL");
     cudaError_t e = cudaSetDevice(p->device);
@@ -834,6 +871,159 @@ int nlint_energy(nlint_plan p, const void *rho, const void *u, double lambda, do
         CK(cudaStreamSynchronize(s));
     }
     return NLINT_OK;
+}
+
+int nlint_plan_toeplitz(nlint_plan p, void *stream) {
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (p->toeplitz) return NLINT_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int d = p->d, n = p->n_fine;
+    const int64_t N = p->N, nh = n / 2 + 1;
+    const size_t es = p->prec == NLINT_FP32 ? 4 : 8, cs = 2 * es;
+    const int64_t half_cells = (d == 3) ? nh * n * n : nh * n;
+    const int64_t full_cells = (d == 3) ? (int64_t)n * n * n : (int64_t)n * n;
+    const int64_t grid = (d == 3) ? N * N * N : N * N;
+    // ones (the convolution needs no deconvolution), the kernel's real half grid
+    {
+        std::vector<double> ones((size_t)std::max<int64_t>(N, n), 1.0);
+        size_t acc = 0;
+        if ((rc = p->prec == NLINT_FP32 ? upload<float>(&p->d_fac1, ones, acc) : upload<double>(&p->d_fac1, ones, acc)))
+            return rc;
+    }
+    CK(cudaMalloc(&p->d_khat, (size_t)half_cells * es));
+    struct Tmp {
+        void *kbuf = nullptr, *c = nullptr, *u = nullptr;
+        ~Tmp() {
+            if (kbuf) cudaFree(kbuf);
+            if (c) cudaFree(c);
+            if (u) cudaFree(u);
+        }
+    } t;
+    CK(cudaMalloc(&t.kbuf, (size_t)half_cells * cs));
+    CK(cudaMalloc(&t.c, (size_t)p->Nf * cs));
+    CK(cudaMalloc(&t.u, (size_t)grid * es));
+    CK(cudaMemsetAsync(t.kbuf, 0, (size_t)full_cells * es, s));
+
+    // K(dx) = h^d Re sum_j W_j exp(i k_j . dx) for dx in [-N, N)^d cells, assembled from 2^d
+    // type-1 evaluations of W_j exp(i k_j . delta) (delta = +-N/2 cells per axis) on the grid
+    const double hd = std::pow(p->h, d);
+    std::vector<double> ch(2 * (size_t)p->Nf);
+    std::vector<float> cf;
+    for (int sh = 0; sh < (1 << d); sh++) {
+        int sgn[3] = {0, 0, 0};  // per node component (x, y, z)
+        for (int c = 0; c < d; c++) sgn[c] = (sh >> c) & 1 ? 1 : -1;
+        for (int64_t j = 0; j < p->Nf; j++) {
+            double ph = 0.0;
+            for (int c = 0; c < d; c++) ph += p->k_canon[(size_t)j * d + c] * sgn[c] * 0.5 * (double)N * p->h;
+            ch[2 * j] = p->W_canon[j] * std::cos(ph);
+            ch[2 * j + 1] = p->W_canon[j] * std::sin(ph);
+        }
+        if (p->prec == NLINT_FP32) {
+            cf.assign(ch.begin(), ch.end());
+            CK(cudaMemcpyAsync(t.c, cf.data(), cf.size() * 4, cudaMemcpyHostToDevice, s));
+        } else {
+            CK(cudaMemcpyAsync(t.c, ch.data(), ch.size() * 8, cudaMemcpyHostToDevice, s));
+        }
+        rc = nlint_type1(p, t.c, t.u, s);
+        if (rc) return rc;
+        // block cell i (centred index m = i - N/2) holds dx = m + sgn N/2; centred n-array index
+        // dx + n/2; array axis a pairs with node component d - 1 - a
+        int offs[3] = {0, 0, 0};
+        for (int a = 0; a < d; a++) offs[a] = (int)(n / 2 - N / 2 + sgn[d - 1 - a] * (N / 2));
+        const int3 off = (d == 3) ? make_int3(offs[0], offs[1], offs[2]) : make_int3(offs[0], 0, offs[1]);
+        if (p->prec == NLINT_FP32) CK(launch_place_block<float>(d, N, n, off, t.u, hd, t.kbuf, s));
+        else CK(launch_place_block<double>(d, N, n, off, t.u, hd, t.kbuf, s));
+        CK(cudaStreamSynchronize(s));  // the host buffer is rewritten for the next shift
+    }
+
+    // K_hat = DFT of the circular kernel (forward passes, all n entries, no deconvolution)
+    auto kpass = [&](PassDesc &pd, int in_kind, int out_kind) {
+        std::memset(&pd, 0, sizeof(pd));
+        pd.n = n;
+        make_radix(n, pd);
+        pd.sign = -1;
+        pd.N = n;
+        pd.dim = d;
+        pd.fac = p->d_fac1;
+        pd.in_kind = in_kind;
+        pd.out_kind = out_kind;
+    };
+    PassDesc K1, K2, K3;
+    kpass(K1, IN_REAL_MODES, OUT_CPLX_HALF);
+    kpass(K3, IN_CPLX_MODES, OUT_CPLX_FULL);
+    const void *kout;
+    if (d == 3) {
+        K1.I = (int64_t)n * n; K1.n_outer = 1; K1.in_sa = (int64_t)n * n; K1.out_sa = (int64_t)n * n;
+        kpass(K2, IN_CPLX_MODES, OUT_CPLX_FULL);
+        K2.I = n; K2.n_outer = nh; K2.in_so = (int64_t)n * n; K2.in_sa = n; K2.out_so = (int64_t)n * n; K2.out_sa = n;
+        K3.I = nh * n; K3.in_so = n; K3.out_so = n;
+        config_pass(K1, p->prec, false);
+        config_pass(K2, p->prec, false);
+        config_pass(K3, p->prec, true);
+        if (p->prec == NLINT_FP32) {
+            CK(launch_colpass<float>(K1, t.kbuf, p->d_bufG, p->d_tw, s));
+            CK(launch_colpass<float>(K2, p->d_bufG, t.kbuf, p->d_tw, s));
+            CK(launch_rowpass<float>(K3, t.kbuf, p->d_bufG, p->d_tw, s));
+        } else {
+            CK(launch_colpass<double>(K1, t.kbuf, p->d_bufG, p->d_tw, s));
+            CK(launch_colpass<double>(K2, p->d_bufG, t.kbuf, p->d_tw, s));
+            CK(launch_rowpass<double>(K3, t.kbuf, p->d_bufG, p->d_tw, s));
+        }
+        kout = p->d_bufG;
+    } else {
+        K1.I = n; K1.n_outer = 1; K1.in_sa = n; K1.out_sa = n;
+        K3.I = nh; K3.in_so = n; K3.out_so = n;
+        config_pass(K1, p->prec, false);
+        config_pass(K3, p->prec, true);
+        if (p->prec == NLINT_FP32) {
+            CK(launch_colpass<float>(K1, t.kbuf, p->d_bufG, p->d_tw, s));
+            CK(launch_rowpass<float>(K3, p->d_bufG, t.kbuf, p->d_tw, s));
+        } else {
+            CK(launch_colpass<double>(K1, t.kbuf, p->d_bufG, p->d_tw, s));
+            CK(launch_rowpass<double>(K3, p->d_bufG, t.kbuf, p->d_tw, s));
+        }
+        kout = t.kbuf;
+    }
+    // the inverse passes are unnormalised: fold 1/n^d into K_hat
+    const double inv = 1.0 / (double)full_cells;
+    if (p->prec == NLINT_FP32) CK(launch_extract_real<float>(half_cells, kout, inv, p->d_khat, s));
+    else CK(launch_extract_real<double>(half_cells, kout, inv, p->d_khat, s));
+    CK(cudaStreamSynchronize(s));
+
+    // evaluation passes: the NUFFT passes with unit factors and the multiply fused into the
+    // first inverse pass
+    p->T1 = p->P1;
+    p->T1.fac = p->d_fac1;
+    p->U3 = p->Q3;
+    p->U3.fac = p->d_fac1;
+    std::memset(&p->U1, 0, sizeof(p->U1));
+    p->U1.n = n;
+    make_radix(n, p->U1);
+    p->U1.sign = +1;
+    p->U1.N = (int)N;
+    p->U1.dim = d;
+    p->U1.in_kind = IN_CPLX_MULT;
+    p->U1.out_kind = OUT_CPLX_MODES;
+    p->U1.I = (d == 3) ? nh * n : nh;
+    p->U1.in_so = n;
+    p->U1.out_so = N;
+    p->U1.mult = p->d_khat;
+    config_pass(p->U1, p->prec, true);
+    p->ws_bytes += (size_t)half_cells * es + (size_t)std::max<int64_t>(N, n) * es;
+    p->toeplitz = true;
+    return NLINT_OK;
+}
+
+int nlint_eval_toeplitz(nlint_plan p, const void *rho, void *u, double lambda, double *E_dev,
+                        void *stream) {
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (!rho || !u) return fail(NLINT_EINVAL, "NULL rho or u");
+    if (!p->toeplitz) return fail(NLINT_EINVAL, "nlint_plan_toeplitz has not been called on this plan");
+    cudaStream_t s = (cudaStream_t)stream;
+    return p->prec == NLINT_FP32 ? run_toeplitz<float>(p, rho, u, lambda, E_dev, s)
+                                 : run_toeplitz<double>(p, rho, u, lambda, E_dev, s);
 }
 
 int nlint_energy_only(nlint_plan p, const void *rho, double lambda, double *E_dev, double *E_host,

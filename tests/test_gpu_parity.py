@@ -260,3 +260,49 @@ def test_energy_only_matches_oracle_dual_energy(pkg, name):
     tol = wl.tol
     assert abs(E - ref["E_dual"]) <= tol * ref["E_scale"], (E, ref["E_dual"])
     assert abs(E - float(E2.item())) <= tol * ref["E_scale"]
+
+
+# --------------------------------------------------------------------------- Toeplitz form
+@pytest.mark.parametrize("name", ["c1", "c2", "c3"])
+def test_toeplitz_form_matches_oracle_and_nufft_path(pkg, name):
+    wl = synth.CONFIGS[name]()
+    rho = wl.rho()
+    setting = "fp32ref" if wl.precision == "fp32" else "parity"
+    ref = pipeline.oracle_eval(rho, wl.L, wl.nodes, wl.kernel, axis=wl.axis, setting=setting, lam=0.8)
+    plan = pkg.Plan(wl.d, wl.n, wl.L, wl.kernel, axis=wl.axis, nodes=wl.nodes, precision=wl.precision,
+                    eps=1e-6 if wl.precision == "fp32" else 1e-12, device=0)
+    dt = torch.float32 if wl.precision == "fp32" else torch.float64
+    r = torch.from_numpy(rho).to("cuda:0", dt)
+    plan.toeplitz()
+    ut, Et = plan.eval_toeplitz(r, lam=0.8)
+    un, En = plan.eval_energy(r, lam=0.8)
+    torch.cuda.synchronize()
+    ut = ut.double().cpu().numpy()
+    assert rel_inf(ut, ref["u"]) <= wl.tol
+    assert rel_inf(ut, un.double().cpu().numpy()) <= wl.tol
+    assert abs(float(Et.item()) - ref["E"]) <= wl.tol * ref["E_scale"]
+
+
+@pytest.mark.parametrize("case", SMALL[:4] + [SMALL[5]])
+def test_toeplitz_small_ragged(pkg, case):
+    d, n, L, kernel, nodes, prec = case
+    rng = np.random.default_rng(n * 11 + d)
+    axis = synth.random_unit(rng, 3) if kernel == "dipole" else None
+    cen, wid, wts = synth.mixture_params(rng, 5, d, L / 6, 0.6, 1.4, 0.5, 1.0)
+    rho = synth.mixture(d, n, L, cen, wid, wts) + 0.05 * rng.standard_normal((n,) * d)
+    tol = 1e-5 if prec == "fp32" else 1e-10
+    ref = pipeline.oracle_eval(rho, L, nodes, kernel, axis=axis, setting="parity")
+    plan = pkg.Plan(d, n, L, kernel, axis=axis, nodes=nodes, precision=prec,
+                    eps=1e-6 if prec == "fp32" else 1e-12, device=0)
+    plan.toeplitz()
+    dt = torch.float32 if prec == "fp32" else torch.float64
+    u, E = plan.eval_toeplitz(torch.from_numpy(rho).to("cuda:0", dt))
+    torch.cuda.synchronize()
+    assert rel_inf(u.double().cpu().numpy(), ref["u"]) <= tol
+    assert abs(float(E.item()) - ref["E"]) <= tol * ref["E_scale"]
+
+
+def test_toeplitz_requires_precompute(pkg):
+    plan = pkg.Plan(3, 32, 12.0, nodes=(8, 8, 16), device=0)
+    with pytest.raises(pkg.NlintError):
+        plan.eval_toeplitz(torch.zeros((32, 32, 32), device="cuda:0"))
