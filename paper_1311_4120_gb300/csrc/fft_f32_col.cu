@@ -1,8 +1,8 @@
-// FFT pass kernels for float, column passes, every supported length (one
-// translation unit per precision and direction so that they compile in parallel).
+// FFT column-pass kernels for float, every supported length (one translation unit per
+// precision and pass mode so that they compile in parallel).
 #include "fft_kernels.cuh"
 
 namespace nlint {
-template cudaError_t launch_pass_impl<float, false>(const PassDesc &, const void *, void *,
-                                                   const void *, cudaStream_t);
+template cudaError_t launch_pass_mode<float, 0>(const PassDesc &, const void *, void *, const void *,
+                                            cudaStream_t);
 }  // namespace nlint

@@ -1,8 +1,8 @@
-// FFT pass kernels for double, row passes, every supported length (one
-// translation unit per precision and direction so that they compile in parallel).
+// FFT row-pass kernels for double, every supported length (one translation unit per
+// precision and pass mode so that they compile in parallel).
 #include "fft_kernels.cuh"
 
 namespace nlint {
-template cudaError_t launch_pass_impl<double, true>(const PassDesc &, const void *, void *,
-                                                   const void *, cudaStream_t);
+template cudaError_t launch_pass_mode<double, 1>(const PassDesc &, const void *, void *, const void *,
+                                            cudaStream_t);
 }  // namespace nlint

@@ -37,8 +37,12 @@ __host__ __device__ constexpr int fft_radix(int n, int s) {
 __host__ __device__ constexpr int fft_pprod(int n, int s) {  // product of the radices before s
     return s == 0 ? 1 : fft_pprod(n, s - 1) * fft_radix(n, s - 1);
 }
-__host__ __device__ constexpr int fft_vpt(int n) { return fft_has3(n) ? 24 : (n <= 512 ? 16 : 32); }
-__host__ __device__ constexpr int fft_tpl(int n) { return n / fft_vpt(n); }  // a power of 2
+// Pass modes: 0 column pass; 1 row pass; 2 row pass that reads more than it writes (the fold
+// and multiply inputs of the first inverse pass), which wants more threads per line.
+__host__ __device__ constexpr int fft_vpt(int n, int mode = 0) {
+    return fft_has3(n) ? 24 : (n <= 512 ? (mode == 2 ? 8 : 16) : 32);
+}
+__host__ __device__ constexpr int fft_tpl(int n, int mode = 0) { return n / fft_vpt(n, mode); }  // 2^k
 __host__ __device__ constexpr int fft_row_ld(int n) { return n + n / 16; }  // padded row line
 // Lines per CTA.  Column pass: 128-byte rows (16 FP32 / 8 FP64 complex), fewer for the
 // longest lines (shared memory <= 192 KB), at least one warp.
@@ -50,26 +54,28 @@ __host__ __device__ constexpr int fft_col_b_raw(int n, int cs) {  // <= 192 KB o
 __host__ __device__ constexpr int fft_col_b(int n, int cs) {
     return fft_col_b_raw(n, cs) * fft_tpl(n) >= 32 ? fft_col_b_raw(n, cs) : 32 / fft_tpl(n);
 }
-__host__ __device__ constexpr int fft_row_b_raw(int n, int cs) {
-    return (512 / fft_tpl(n)) < (96 * 1024) / (fft_row_ld(n) * cs) ? 512 / fft_tpl(n)
-                                                                    : (96 * 1024) / (fft_row_ld(n) * cs);
+// Row pass: about 256 threads (mode 1) or 512 threads (mode 2) per CTA.
+__host__ __device__ constexpr int fft_row_thr(int mode) { return mode == 2 ? 512 : 256; }
+__host__ __device__ constexpr int fft_row_b_raw(int n, int cs, int mode) {
+    return (fft_row_thr(mode) / fft_tpl(n, mode)) < (96 * 1024) / (fft_row_ld(n) * cs)
+               ? fft_row_thr(mode) / fft_tpl(n, mode)
+               : (96 * 1024) / (fft_row_ld(n) * cs);
 }
-__host__ __device__ constexpr int fft_row_b(int n, int cs) {
-    return fft_row_b_raw(n, cs) < 1 ? 1
-         : (fft_tpl(n) < 32 && fft_row_b_raw(n, cs) >= 32 / fft_tpl(n))
-               ? fft_row_b_raw(n, cs) / (32 / fft_tpl(n)) * (32 / fft_tpl(n))
-               : fft_row_b_raw(n, cs);
+__host__ __device__ constexpr int fft_row_b(int n, int cs, int mode = 1) {
+    return fft_row_b_raw(n, cs, mode) < 1 ? 1
+         : (fft_tpl(n, mode) < 32 && fft_row_b_raw(n, cs, mode) >= 32 / fft_tpl(n, mode))
+               ? fft_row_b_raw(n, cs, mode) / (32 / fft_tpl(n, mode)) * (32 / fft_tpl(n, mode))
+               : fft_row_b_raw(n, cs, mode);
 }
 
-template <typename T, int NF>
+template <typename T, int NF, int MODE>
 struct FftCfg {
     static constexpr int CS = (int)(2 * sizeof(T));
-    static constexpr int TPL = fft_tpl(NF);  // threads per line
+    static constexpr int TPL = fft_tpl(NF, MODE);  // threads per line
     static constexpr int NST = fft_nstages(NF);
-    static constexpr int COL_B = fft_col_b(NF, CS);
-    static constexpr int ROW_B = fft_row_b(NF, CS);
+    static constexpr int B = MODE == 0 ? fft_col_b(NF, CS) : fft_row_b(NF, CS, MODE);  // lines per CTA
     static constexpr int ROW_LD = fft_row_ld(NF);
-    static constexpr int threads(bool row) { return (row ? ROW_B : COL_B) * TPL; }
+    static constexpr int THREADS = B * TPL;
 };
 
 // ------------------------------------------------------------------ butterflies
@@ -170,14 +176,15 @@ struct LineIO {
 };
 
 // ------------------------------------------------------------------ the pass kernel
-// ROW = false: column pass, the CTA's COL_B lines are adjacent in memory (128-byte rows);
-// ROW = true: row pass, each line is contiguous (ROW_B lines per CTA).
-template <typename T, int NF, bool ROW>
-__global__ void __launch_bounds__(FftCfg<T, NF>::threads(ROW)) fft_pass_kernel(
+// MODE 0: column pass, the CTA's B lines are adjacent in memory (128-byte rows);
+// MODE 1, 2: row pass, each line is contiguous (B lines per CTA).
+template <typename T, int NF, int MODE>
+__global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS) fft_pass_kernel(
     PassDesc P, const void *__restrict__ vin, void *__restrict__ vout, const cx_t<T> *__restrict__ tw) {
     using T2 = cx_t<T>;
-    using C = FftCfg<T, NF>;
-    constexpr int B = ROW ? C::ROW_B : C::COL_B;
+    using C = FftCfg<T, NF, MODE>;
+    constexpr bool ROW = MODE != 0;
+    constexpr int B = C::B;
     constexpr int TPL = C::TPL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T2 *buf = reinterpret_cast<T2 *>(smem_raw);
@@ -329,37 +336,37 @@ __global__ void __launch_bounds__(FftCfg<T, NF>::threads(ROW)) fft_pass_kernel(
 }
 
 // ------------------------------------------------------------------ launchers
-template <typename T, int NF, bool ROW>
+template <typename T, int NF, int MODE>
 cudaError_t launch_nf(const PassDesc &p, const void *in, void *out, const void *tw, cudaStream_t s) {
     const size_t smem = pass_smem(p, sizeof(T) == 4 ? NLINT_FP32 : NLINT_FP64);
-    cudaError_t e = cudaFuncSetAttribute(fft_pass_kernel<T, NF, ROW>,
+    cudaError_t e = cudaFuncSetAttribute(fft_pass_kernel<T, NF, MODE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int64_t nb = pass_blocks(p, ROW);
+    const int64_t nb = pass_blocks(p, MODE != 0);
     if (nb == 0) return cudaSuccess;
-    fft_pass_kernel<T, NF, ROW><<<(unsigned)nb, FftCfg<T, NF>::threads(ROW), smem, s>>>(
+    fft_pass_kernel<T, NF, MODE><<<(unsigned)nb, FftCfg<T, NF, MODE>::THREADS, smem, s>>>(
         p, in, out, reinterpret_cast<const cx_t<T> *>(tw));
     return cudaGetLastError();
 }
 
-template <typename T, bool ROW>
-cudaError_t launch_pass_impl(const PassDesc &p, const void *in, void *out, const void *tw, cudaStream_t s) {
+template <typename T, int MODE>
+cudaError_t launch_pass_mode(const PassDesc &p, const void *in, void *out, const void *tw, cudaStream_t s) {
     switch (p.n) {
-        case 16: return launch_nf<T, 16, ROW>(p, in, out, tw, s);
-        case 24: return launch_nf<T, 24, ROW>(p, in, out, tw, s);
-        case 32: return launch_nf<T, 32, ROW>(p, in, out, tw, s);
-        case 48: return launch_nf<T, 48, ROW>(p, in, out, tw, s);
-        case 64: return launch_nf<T, 64, ROW>(p, in, out, tw, s);
-        case 96: return launch_nf<T, 96, ROW>(p, in, out, tw, s);
-        case 128: return launch_nf<T, 128, ROW>(p, in, out, tw, s);
-        case 192: return launch_nf<T, 192, ROW>(p, in, out, tw, s);
-        case 256: return launch_nf<T, 256, ROW>(p, in, out, tw, s);
-        case 384: return launch_nf<T, 384, ROW>(p, in, out, tw, s);
-        case 512: return launch_nf<T, 512, ROW>(p, in, out, tw, s);
-        case 768: return launch_nf<T, 768, ROW>(p, in, out, tw, s);
-        case 1024: return launch_nf<T, 1024, ROW>(p, in, out, tw, s);
-        case 1536: return launch_nf<T, 1536, ROW>(p, in, out, tw, s);
-        case 2048: return launch_nf<T, 2048, ROW>(p, in, out, tw, s);
+        case 16: return launch_nf<T, 16, MODE>(p, in, out, tw, s);
+        case 24: return launch_nf<T, 24, MODE>(p, in, out, tw, s);
+        case 32: return launch_nf<T, 32, MODE>(p, in, out, tw, s);
+        case 48: return launch_nf<T, 48, MODE>(p, in, out, tw, s);
+        case 64: return launch_nf<T, 64, MODE>(p, in, out, tw, s);
+        case 96: return launch_nf<T, 96, MODE>(p, in, out, tw, s);
+        case 128: return launch_nf<T, 128, MODE>(p, in, out, tw, s);
+        case 192: return launch_nf<T, 192, MODE>(p, in, out, tw, s);
+        case 256: return launch_nf<T, 256, MODE>(p, in, out, tw, s);
+        case 384: return launch_nf<T, 384, MODE>(p, in, out, tw, s);
+        case 512: return launch_nf<T, 512, MODE>(p, in, out, tw, s);
+        case 768: return launch_nf<T, 768, MODE>(p, in, out, tw, s);
+        case 1024: return launch_nf<T, 1024, MODE>(p, in, out, tw, s);
+        case 1536: return launch_nf<T, 1536, MODE>(p, in, out, tw, s);
+        case 2048: return launch_nf<T, 2048, MODE>(p, in, out, tw, s);
         default: return cudaErrorInvalidValue;
     }
 }

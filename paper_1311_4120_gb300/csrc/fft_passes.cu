@@ -5,10 +5,17 @@
 namespace nlint {
 
 // the kernels are instantiated in fft_{f32,f64}_{col,row}.cu
-extern template cudaError_t launch_pass_impl<float, false>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
-extern template cudaError_t launch_pass_impl<float, true>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
-extern template cudaError_t launch_pass_impl<double, false>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
-extern template cudaError_t launch_pass_impl<double, true>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
+extern template cudaError_t launch_pass_mode<float, 0>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
+extern template cudaError_t launch_pass_mode<float, 1>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
+extern template cudaError_t launch_pass_mode<float, 2>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
+extern template cudaError_t launch_pass_mode<double, 0>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
+extern template cudaError_t launch_pass_mode<double, 1>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
+extern template cudaError_t launch_pass_mode<double, 2>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
+
+int pass_mode(const PassDesc &p, bool row) {
+    if (!row) return 0;
+    return (p.in_kind == IN_CPLX_FOLD || p.in_kind == IN_CPLX_MULT) ? 2 : 1;
+}
 
 bool fft_size_supported(int n) {
     if (n < 16 || n > 2048) return false;
@@ -42,8 +49,9 @@ void make_radix(int n, PassDesc &p) {
 
 void config_pass(PassDesc &p, int prec, bool row) {
     const int cs = prec == NLINT_FP32 ? 8 : 16;
-    p.TPC = fft_tpl(p.n);
-    p.B = row ? fft_row_b(p.n, cs) : fft_col_b(p.n, cs);
+    const int mode = pass_mode(p, row);
+    p.TPC = fft_tpl(p.n, mode);
+    p.B = row ? fft_row_b(p.n, cs, mode) : fft_col_b(p.n, cs);
     p.LD = row ? fft_row_ld(p.n) : p.B;
 }
 
@@ -65,12 +73,13 @@ size_t pass_smem(const PassDesc &p, int prec) {
 
 template <typename T>
 cudaError_t launch_colpass(const PassDesc &p, const void *in, void *out, const void *tw, cudaStream_t s) {
-    return launch_pass_impl<T, false>(p, in, out, tw, s);
+    return launch_pass_mode<T, 0>(p, in, out, tw, s);
 }
 
 template <typename T>
 cudaError_t launch_rowpass(const PassDesc &p, const void *in, void *out, const void *tw, cudaStream_t s) {
-    return launch_pass_impl<T, true>(p, in, out, tw, s);
+    return pass_mode(p, true) == 2 ? launch_pass_mode<T, 2>(p, in, out, tw, s)
+                                   : launch_pass_mode<T, 1>(p, in, out, tw, s);
 }
 
 template cudaError_t launch_colpass<float>(const PassDesc &, const void *, void *, const void *, cudaStream_t);

@@ -64,8 +64,10 @@ size_t pass_smem(const PassDesc &p, int prec);
 void config_pass(PassDesc &p, int prec, bool row);
 bool pass_fits(const PassDesc &p);
 
-template <typename T, bool ROW>
-cudaError_t launch_pass_impl(const PassDesc &p, const void *in, void *out, const void *tw,
+// pass mode 0: column pass; 1: row pass; 2: row pass reading fold / multiply input
+int pass_mode(const PassDesc &p, bool row);
+template <typename T, int MODE>
+cudaError_t launch_pass_mode(const PassDesc &p, const void *in, void *out, const void *tw,
                              cudaStream_t s);
 template <typename T>
 cudaError_t launch_colpass(const PassDesc &p, const void *in, void *out, const void *tw,
