@@ -89,8 +89,8 @@ struct NodeDesc {
     int w;               // stencil width
     int pad;             // extended planes below/above the half grid (slowest axis)
     double beta;         // ES kernel shape parameter
-    const int32_t *l0;   // d x M, first stencil cell per axis (array-axis order)
-    const void *frac;    // d x M, g - l0 per axis (plan precision)
+    const int32_t *rel;  // M: first stencil cell relative to the bin origin, r0 | r1 << 8 | r2 << 16
+    const void *ker;     // M x (d w): kernel values phi((q - frac_a)/(w/2)), row per node
     const void *W;       // M, h^d W_j (plan precision), may be NULL (type-2 only)
     int B[3], T[3];      // bin and tile extents per array axis
     int64_t nsub;        // number of subproblems

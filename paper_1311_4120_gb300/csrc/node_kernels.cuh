@@ -4,7 +4,8 @@
 //
 // Spreading function: the "exponential of semicircle" of Barnett, Magland and af Klinteberg
 // (SIAM J. Sci. Comput. 2019), phi(z) = exp(beta (sqrt(1 - z^2) - 1)) on |z| <= 1, with
-// z = (l - g) / (w/2) for fine cell l and node position g in fine-cell units.
+// z = (l - g) / (w/2) for fine cell l and node position g in fine-cell units.  The nodes are
+// fixed per plan, so the plan evaluates phi for every node and axis once, in FP64.
 //
 // Only the half node set (k on the non-negative side of array axis 0) is processed:
 // rho_hat(-k) = conj(rho_hat(k)) for a real density, and the mirrored nodes' spreading is
@@ -48,12 +49,6 @@ struct Geo {
     static constexpr int PASSES = (PAIRS + LPN - 1) / LPN;
 };
 
-template <typename T>
-__device__ __forceinline__ T es_kernel(T z, T beta) {
-    const T s = T(1) - z * z;
-    return s > T(0) ? exp(beta * (sqrt(s) - T(1))) : T(0);
-}
-
 // l mod n for l in [-n, 2n)
 __device__ __forceinline__ int wrap1(int l, int n) { return l < 0 ? l + n : (l >= n ? l - n : l); }
 
@@ -78,48 +73,45 @@ __device__ __forceinline__ cx_t<T> fetch_half(const cx_t<T> *__restrict__ G, int
 }
 
 // A warp works on NPW = 32 / LPN nodes at a time (one per LPN-lane group): per node its lanes
-// share the w*w stencil columns, and the nodes share the warp's per-node work (kernel values,
-// loads, shuffle reductions).  NodeGroup holds this lane's view: the stencil origin of its
-// group's node, and the fractional offsets it needs for its share of the NPW*D*w kernel values.
+// share the w*w stencil columns, and the nodes share the warp's per-node work (loads, shuffle
+// reductions).  NodeGroup holds this lane's view: the stencil origin of its group's node
+// (relative to the bin) and its share of the group's NPW*D*w kernel values, which the plan
+// computed once (the nodes are fixed).
 template <typename T, int D, int W>
 struct NodeGroup {
     static constexpr int LPN = Geo<T, D, W>::LPN, NPW = Geo<T, D, W>::NPW;
     static constexpr int NKV = NPW * D * W;        // kernel values of the group
     static constexpr int KV = (NKV + 31) / 32;     // ... per lane
     int r0, r1, r2;
-    T fr[KV];
+    T kv[KV];
     // nodes j .. j + NPW - 1 of the chunk ending at jb, node j + lane / LPN for this lane
-    __device__ __forceinline__ void load(const NodeDesc &nd, int j, int jb, int lane, int4 bo) {
-        const int64_t M = nd.M;
+    __device__ __forceinline__ void load(const NodeDesc &nd, int j, int jb, int lane) {
         const int mine = (NPW == 1) ? j : j + lane / LPN;
-        if (NPW == 1 || mine < jb) {
-            r0 = nd.l0[mine] - bo.x;
-            r1 = nd.l0[M + mine] - bo.y;
-            r2 = (D == 3) ? nd.l0[2 * M + mine] - bo.z : 0;
-        } else {
-            r0 = r1 = r2 = 0;
-        }
+        const int rl = (NPW == 1 || mine < jb) ? nd.rel[mine] : 0;
+        r0 = rl & 255;
+        r1 = (rl >> 8) & 255;
+        r2 = (rl >> 16) & 255;
+        const T *ker = reinterpret_cast<const T *>(nd.ker) + (int64_t)j * (D * W);
+        const int navail = (jb - j) * (D * W);  // kernel values left in the chunk
 #pragma unroll
         for (int v = 0; v < KV; v++) {
             const int t = lane + 32 * v;
-            const int h = (NPW == 1) ? 0 : t / (D * W), a = (t - h * D * W) / W;
-            fr[v] = (t < NKV && (NPW == 1 || j + h < jb)) ? reinterpret_cast<const T *>(nd.frac)[a * M + j + h] : T(0);
+            kv[v] = (t < NKV && t < navail) ? ker[t] : T(0);
         }
     }
 };
 
-// Kernel values of the group into the warp's table ker[h*3*MAXW + a*MAXW + q] =
-// phi((q - frac_a)/(w/2)) for node h of the group, stencil cell q of axis a.
+// Kernel values of the group into the warp's table ker[h*3*MAXW + a*MAXW + q] for node h of
+// the group, stencil cell q of axis a.
 template <typename T, int D, int W>
-__device__ __forceinline__ void warp_kernel_values(const NodeGroup<T, D, W> &np, T beta, int lane, T *ker) {
-    const T inv_half = T(2) / T(W);
+__device__ __forceinline__ void warp_kernel_values(const NodeGroup<T, D, W> &np, int lane, T *ker) {
 #pragma unroll
     for (int v = 0; v < NodeGroup<T, D, W>::KV; v++) {
         const int t = lane + 32 * v;
         if (t < NodeGroup<T, D, W>::NKV) {
             const int h = (NodeGroup<T, D, W>::NPW == 1) ? 0 : t / (D * W);
             const int rem = t - h * D * W, a = rem / W, q = rem - a * W;
-            ker[h * 3 * MAXW + a * MAXW + q] = es_kernel<T>((T(q) - np.fr[v]) * inv_half, beta);
+            ker[h * 3 * MAXW + a * MAXW + q] = np.kv[v];
         }
     }
 }
@@ -185,7 +177,6 @@ __global__ void __launch_bounds__(SUB_THREADS) interp_sub_kernel(NodeDesc nd,
     const int4 sb = nd.subs[blockIdx.x];
     const int4 bo = nd.bins[sb.z];
     const int n = nd.n;
-    const T beta = T(nd.beta);
     int pairs[PASSES];  // this lane's stencil columns, one per pass (-1: idle)
 #pragma unroll
     for (int ps = 0; ps < PASSES; ps++) pairs[ps] = nd.pair_order[ps * G_::LPN + lane % G_::LPN];
@@ -213,13 +204,13 @@ __global__ void __launch_bounds__(SUB_THREADS) interp_sub_kernel(NodeDesc nd,
     const T *kh = ker + half * 3 * MAXW;  // this lane's node's kernel values
     NodeGroup<T, D, W> cur, nxt;
     EAcc<T> eacc;  // energy-only mode: sum of W_j |rho_hat_j|^2 over this lane's nodes
-    if (ja < jb) cur.load(nd, ja, jb, lane, bo);
+    if (ja < jb) cur.load(nd, ja, jb, lane);
     for (int j = ja; j < jb; j += G_::NPW) {
-        if (j + G_::NPW < jb) nxt.load(nd, j + G_::NPW, jb, lane, bo);  // prefetch the next group
+        if (j + G_::NPW < jb) nxt.load(nd, j + G_::NPW, jb, lane);  // prefetch the next group
         const int mine = j + half;
         const bool act = (G_::NPW == 1) || mine < jb;
         const T Wj = (act && apply_W) ? reinterpret_cast<const T *>(nd.W)[mine] : T(1);
-        warp_kernel_values<T, D, W>(cur, beta, lane, ker);
+        warp_kernel_values<T, D, W>(cur, lane, ker);
         __syncwarp();
         T accr = T(0), acci = T(0);
         if (act) {
@@ -288,7 +279,6 @@ __global__ void __launch_bounds__(SUB_THREADS) spread_sub_kernel(NodeDesc nd,
     const int4 sb = nd.subs[blockIdx.x];
     const int4 bo = nd.bins[sb.z];
     const int n = nd.n, pad = nd.pad;
-    const T beta = T(nd.beta);
     int pairs[PASSES];
 #pragma unroll
     for (int ps = 0; ps < PASSES; ps++) pairs[ps] = nd.pair_order[ps * G_::LPN + lane % G_::LPN];
@@ -336,16 +326,16 @@ __global__ void __launch_bounds__(SUB_THREADS) spread_sub_kernel(NodeDesc nd,
     NodeGroup<T, D, W> cur, nxt;
     T2 c = czero<T2>(), cn = czero<T2>();
     if (ja < jb) {
-        cur.load(nd, ja, jb, lane, bo);
+        cur.load(nd, ja, jb, lane);
         if (ja + half < jb) c = c_in[ja + half];
     }
     for (int j = ja; j < jb; j += G_::NPW) {
         if (j + G_::NPW < jb) {  // prefetch the next group
-            nxt.load(nd, j + G_::NPW, jb, lane, bo);
+            nxt.load(nd, j + G_::NPW, jb, lane);
             cn = (j + G_::NPW + half < jb) ? c_in[j + G_::NPW + half] : czero<T2>();
         }
         const bool act = (G_::NPW == 1) || j + half < jb;
-        warp_kernel_values<T, D, W>(cur, beta, lane, ker);
+        warp_kernel_values<T, D, W>(cur, lane, ker);
         __syncwarp();
         if (act) {
             T k0[L];

@@ -9,6 +9,7 @@
 #include <cstring>
 #include <numeric>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "internal.h"
@@ -111,8 +112,8 @@ struct nlint_plan_s {
     double axis[3], axis2[3], alpha;
     int device;
     // device memory
-    int32_t *d_l0 = nullptr;
-    void *d_frac = nullptr, *d_W = nullptr, *d_fac = nullptr, *d_tw = nullptr;
+    int32_t *d_rel = nullptr;
+    void *d_ker = nullptr, *d_W = nullptr, *d_fac = nullptr, *d_tw = nullptr;
     int32_t *d_perm = nullptr, *d_mirror = nullptr;
     int4 *d_subs = nullptr, *d_bins = nullptr;
     int16_t *d_pairs = nullptr;
@@ -206,7 +207,7 @@ static int upload(void **dst, const std::vector<double> &v, size_t &acc) {
 }
 
 static void plan_free(nlint_plan_s *p) {
-    void *ptrs[] = {p->d_l0, p->d_frac, p->d_W, p->d_fac, p->d_tw, p->d_perm, p->d_mirror,
+    void *ptrs[] = {p->d_rel, p->d_ker, p->d_W, p->d_fac, p->d_tw, p->d_perm, p->d_mirror,
                     p->d_subs, p->d_bins, p->d_crowd_bin, p->d_crowd, p->d_pairs, p->d_epart, p->d_fac1, p->d_khat,
                     p->d_bufA, p->d_bufB, p->d_bufG, p->d_c, p->d_partials, p->d_E,
                     p->d_rho_io, p->d_u_io};
@@ -404,6 +405,7 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
     const int max_sub_crowd = std::min(max_sub, 512);
     const int64_t crowd_min = q.crowd_min > 0 ? q.crowd_min : 4096;
     std::vector<int4> bins, subs;
+    std::vector<int32_t> rel(Mh);
     std::vector<int32_t> crowd_bin;
     for (int64_t o = 0; o < Mh;) {
         int64_t e = o;
@@ -419,6 +421,11 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
         b.x = org[0];
         b.y = org[1];
         b.z = org[2];
+        for (int64_t q = o; q < e; q++) {  // stencil origins relative to the bin
+            int32_t r = 0;
+            for (int ax = 0; ax < d; ax++) r |= (l0s[(size_t)ax * Mh + q] - org[ax]) << (8 * ax);
+            rel[q] = r;
+        }
         const bool crowd = (p->prec == NLINT_FP32) && (e - o > crowd_min);
         b.w = crowd ? (int)crowd_bin.size() : -1;
         const int bi = (int)bins.size();
@@ -436,6 +443,27 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
     p->nbins = (int64_t)bins.size();
     p->ncrowd = (int)crowd_bin.size();
     if (p->nsub > (int64_t)INT32_MAX) return fail(NLINT_EUNSUPPORTED, "too many subproblems");
+
+    // ---------------- kernel values phi((q - frac_a) / (w/2)) per node, axis and cell, in FP64
+    const int dw = d * w;
+    std::vector<double> kerv((size_t)Mh * dw);
+    {
+        const double beta = p->beta, inv_half = 2.0 / w;
+        auto work = [&](int64_t a0, int64_t a1) {
+            for (int64_t o = a0; o < a1; o++)
+                for (int ax = 0; ax < d; ax++) {
+                    const double fr = frs[(size_t)ax * Mh + o];
+                    for (int q = 0; q < w; q++) {
+                        const double z = (q - fr) * inv_half, s2 = 1.0 - z * z;
+                        kerv[(size_t)o * dw + ax * w + q] = s2 > 0.0 ? std::exp(beta * (std::sqrt(s2) - 1.0)) : 0.0;
+                    }
+                }
+        };
+        const int nt = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+        std::vector<std::thread> th;
+        for (int t = 0; t < nt; t++) th.emplace_back(work, Mh * t / nt, Mh * (t + 1) / nt);
+        for (auto &t : th) t.join();
+    }
 
     // ---------------- deconvolution factors f[m'] = (2 pi / n) / psi_hat(m), m = m' - N/2
     std::vector<double> qx, qw;
@@ -457,13 +485,13 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
     // ---------------- upload
     size_t acc = 0;
     int rc;
-    CK(cudaMalloc((void **)&p->d_l0, l0s.size() * sizeof(int32_t) + 4));
-    CK(cudaMemcpy(p->d_l0, l0s.data(), l0s.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CK(cudaMalloc((void **)&p->d_rel, rel.size() * sizeof(int32_t) + 4));
+    CK(cudaMemcpy(p->d_rel, rel.data(), rel.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     CK(cudaMalloc((void **)&p->d_perm, perm.size() * sizeof(int32_t) + 4));
     CK(cudaMemcpy(p->d_perm, perm.data(), perm.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     CK(cudaMalloc((void **)&p->d_mirror, mirror.size() * sizeof(int32_t) + 4));
     CK(cudaMemcpy(p->d_mirror, mirror.data(), mirror.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-    acc += (l0s.size() + perm.size() + mirror.size()) * 4;
+    acc += (rel.size() + perm.size() + mirror.size()) * 4;
     CK(cudaMalloc((void **)&p->d_subs, sizeof(int4) * std::max<size_t>(subs.size(), 1)));
     if (!subs.empty()) CK(cudaMemcpy(p->d_subs, subs.data(), sizeof(int4) * subs.size(), cudaMemcpyHostToDevice));
     CK(cudaMalloc((void **)&p->d_bins, sizeof(int4) * std::max<size_t>(bins.size(), 1)));
@@ -490,12 +518,12 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
         }
     }
     if (p->prec == NLINT_FP32) {
-        if ((rc = upload<float>(&p->d_frac, frs, acc))) return rc;
+        if ((rc = upload<float>(&p->d_ker, kerv, acc))) return rc;
         if ((rc = upload<float>(&p->d_W, Ws, acc))) return rc;
         if ((rc = upload<float>(&p->d_fac, fac, acc))) return rc;
         if ((rc = upload<float>(&p->d_tw, tw, acc))) return rc;
     } else {
-        if ((rc = upload<double>(&p->d_frac, frs, acc))) return rc;
+        if ((rc = upload<double>(&p->d_ker, kerv, acc))) return rc;
         if ((rc = upload<double>(&p->d_W, Ws, acc))) return rc;
         if ((rc = upload<double>(&p->d_fac, fac, acc))) return rc;
         if ((rc = upload<double>(&p->d_tw, tw, acc))) return rc;
@@ -627,8 +655,8 @@ static NodeDesc node_desc(nlint_plan_s *p) {
     nd.w = p->w;
     nd.pad = p->pad;
     nd.beta = p->beta;
-    nd.l0 = p->d_l0;
-    nd.frac = p->d_frac;
+    nd.rel = p->d_rel;
+    nd.ker = p->d_ker;
     nd.W = p->d_W;
     for (int a = 0; a < 3; a++) {
         nd.B[a] = p->B[a];
