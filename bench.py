@@ -37,6 +37,7 @@ import synth  # noqa: E402
 METRIC = "grid points/s per potential eval (FP32 & batched vs FP64 GPU) at stated rel L-inf err"
 UNIT = "grid points/s"
 L2_FLUSH_BYTES = 256 << 20          # > 129 MB L2: written between timed steps
+TOL = 1e-5                          # stated relative L-inf tolerance of the FP32 path
 
 # DRAM bytes per launch from an ncu capture of the kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum), keyed by stage name, with the hash of the kernel source the capture
@@ -291,8 +292,14 @@ def run_ours(args, rank, world, local_rank):
 
     wl = synth.config4()
     rho_np = wl.rho().astype(np.float32)
-    plan = pkg.Plan(wl.d, wl.n, wl.L, wl.kernel, nodes=wl.nodes, eps=1e-6, precision="fp32",
-                    device=local_rank)
+    # the FP32 plan for the stated tolerance: the autotuner measures the stencil width that
+    # meets TOL/2 against an FP64 plan and the fastest subproblem size (NLINT_TUNE_CACHE reuses it)
+    prm = pkg.make_params(wl.d, wl.n, wl.L, wl.kernel, nodes=wl.nodes, precision="fp32",
+                          device=local_rank)
+    t0 = time.perf_counter()
+    tuned, tune_rep = pkg.autotune(prm, TOL, os.environ.get("NLINT_TUNE_CACHE"))
+    tune_rep["seconds"] = time.perf_counter() - t0
+    plan = pkg.Plan(wl.d, wl.n, wl.L, params=tuned, device=local_rank)
     info = plan.info
     rho = torch.from_numpy(rho_np).to(dev)
     u = torch.empty_like(rho)
@@ -445,6 +452,7 @@ def run_ours(args, rank, world, local_rank):
                                "160x160x320 spherical nodes, FP32 path (FP64 nodes/weights, "
                                "compensated FP64 energy)",
                    "w": info["w"], "sigma": info["sigma"], "n_fine": info["n_fine"],
+                   "max_sub": tuned.max_sub, "tolerance": TOL, "autotune": tune_rep,
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "energy": E32,
