@@ -68,14 +68,22 @@ __host__ __device__ constexpr int fft_row_b(int n, int cs, int mode = 1) {
                : fft_row_b_raw(n, cs, mode);
 }
 
+// Modes 3 and 4 are column passes that carry two real lines per complex FFT line: mode 3
+// transforms real input to the Hermitian half (z = x + i y, then X, Y from Z(k) and Z(n-k)),
+// mode 4 the Hermitian half back to real output (Z = X + i Y, then x = Re z, y = Im z).
+__host__ __device__ constexpr bool fft_is_row(int mode) { return mode == 1 || mode == 2; }
+__host__ __device__ constexpr int fft_pack(int mode) { return mode >= 3 ? 2 : 1; }
+
 template <typename T, int NF, int MODE>
 struct FftCfg {
     static constexpr int CS = (int)(2 * sizeof(T));
     static constexpr int TPL = fft_tpl(NF, MODE);  // threads per line
     static constexpr int NST = fft_nstages(NF);
-    static constexpr int B = MODE == 0 ? fft_col_b(NF, CS) : fft_row_b(NF, CS, MODE);  // lines per CTA
+    static constexpr int B = fft_is_row(MODE) ? fft_row_b(NF, CS, MODE) : fft_col_b(NF, CS);  // lines
     static constexpr int ROW_LD = fft_row_ld(NF);
     static constexpr int THREADS = B * TPL;
+    // packed passes hold two lines' loads in flight: ask for two resident CTAs of 512 threads
+    static constexpr int MIN_BLOCKS = (MODE >= 3 && THREADS == 512 && NF <= 512 && sizeof(T) == 4) ? 2 : 0;
 };
 
 // ------------------------------------------------------------------ butterflies
@@ -177,13 +185,15 @@ struct LineIO {
 
 // ------------------------------------------------------------------ the pass kernel
 // MODE 0: column pass, the CTA's B lines are adjacent in memory (128-byte rows);
-// MODE 1, 2: row pass, each line is contiguous (B lines per CTA).
+// MODE 1, 2: row pass, each line is contiguous (B lines per CTA);
+// MODE 3, 4: column pass with two data columns per FFT line (2B adjacent columns per CTA).
 template <typename T, int NF, int MODE>
-__global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS) fft_pass_kernel(
+__global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MODE>::MIN_BLOCKS) fft_pass_kernel(
     PassDesc P, const void *__restrict__ vin, void *__restrict__ vout, const cx_t<T> *__restrict__ tw) {
     using T2 = cx_t<T>;
     using C = FftCfg<T, NF, MODE>;
-    constexpr bool ROW = MODE != 0;
+    constexpr bool ROW = fft_is_row(MODE);
+    constexpr bool PACK = MODE >= 3;
     constexpr int B = C::B;
     constexpr int TPL = C::TPL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -203,18 +213,37 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS) fft_pass_kernel(
     io.mirror_base = -1;
     io.mult = reinterpret_cast<const T *>(P.mult);
     io.bfac = T(1);
+    LineIO<T> io2;  // packed modes: the second data column of this FFT line (set field by field)
+    io2.n = P.n;
+    io2.h = h;
+    io2.kind = P.in_kind;
+    io2.fac = io.fac;
+    io2.mirror_base = -1;
+    io2.mult = io.mult;
+    io2.bfac = T(1);
+    io2.valid = false;
+    io2.in_base = io2.out_base = 0;
+    io2.in_st = P.in_sa;
+    io2.out_st = P.out_sa;
     if (!ROW) {
-        const int64_t tiles = (P.I + B - 1) / B;
+        constexpr int CPT = B * fft_pack(MODE);  // data columns per CTA
+        const int64_t tiles = (P.I + CPT - 1) / CPT;
         const int64_t o = blockIdx.x / tiles;
-        const int64_t i = (blockIdx.x % tiles) * B + ll;
+        const int64_t i = (blockIdx.x % tiles) * CPT + ll;
         io.valid = i < P.I;
         io.in_base = o * P.in_so + i;
         io.out_base = o * P.out_so + i;
         io.in_st = P.in_sa;
         io.out_st = P.out_sa;
-        if (io.valid && (P.in_kind == IN_REAL_MODES || P.out_kind == OUT_REAL_MODES)) {
-            const T *fac = reinterpret_cast<const T *>(P.fac);
+        const T *fac = reinterpret_cast<const T *>(P.fac);
+        if (io.valid && (P.in_kind == IN_REAL_MODES || P.out_kind == OUT_REAL_MODES))
             io.bfac = (P.dim == 3) ? fac[i / N] * fac[i % N] : fac[i];
+        if (PACK) {
+            const int64_t i2 = i + B;
+            io2.valid = i2 < P.I;
+            io2.in_base = io.in_base + B;
+            io2.out_base = io.out_base + B;
+            io2.bfac = io2.valid ? ((P.dim == 3) ? fac[i2 / N] * fac[i2 % N] : fac[i2]) : T(1);
         }
     } else {
         const int64_t q = (int64_t)blockIdx.x * B + ll;
@@ -247,7 +276,17 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS) fft_pass_kernel(
 #pragma unroll
         for (int b = 0; b < MB; b++)
 #pragma unroll
-            for (int r = 0; r < R; r++) v[b][r] = io.load(t + b * TPL + r * NB, vin);
+            for (int r = 0; r < R; r++) {
+                const int e = t + b * TPL + r * NB;
+                if constexpr (MODE == 3) {  // z = x + i y from two real columns
+                    v[b][r] = cmake<T2>(io.load(e, vin).x, io2.load(e, vin).x);
+                } else if constexpr (MODE == 4) {  // Z = X + i Y from two Hermitian columns
+                    const T2 X = io.load(e, vin), Y = io2.load(e, vin);
+                    v[b][r] = cmake<T2>(X.x - Y.y, X.y + Y.x);
+                } else {
+                    v[b][r] = io.load(e, vin);
+                }
+            }
 #pragma unroll
         for (int b = 0; b < MB; b++) {
             dft_small<T, R>(v[b], sign);
@@ -273,7 +312,7 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS) fft_pass_kernel(
         for (int b = 0; b < MB; b++)
 #pragma unroll
             for (int r = 0; r < R; r++) v[b][r] = buf[sidx(t + b * TPL + r * NB)];
-        if constexpr (!LAST) __syncthreads();
+        if constexpr (!LAST || PACK) __syncthreads();
 #pragma unroll
         for (int b = 0; b < MB; b++) {
             const int i = t + b * TPL;
@@ -289,6 +328,9 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS) fft_pass_kernel(
                 const int j = (i - k) * R + k;
 #pragma unroll
                 for (int r = 0; r < R; r++) buf[sidx(j + r * PP)] = v[b][r];
+            } else if constexpr (PACK) {  // z in natural order for the epilogue below
+#pragma unroll
+                for (int r = 0; r < R; r++) buf[sidx(i + r * PP)] = v[b][r];
             } else if (io.valid) {
                 // output entry e = i + r PP (here PP R = n and k = i)
 #pragma unroll
@@ -328,6 +370,42 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS) fft_pass_kernel(
     };
     static_for<1, C::NST>(stage);
 
+    if constexpr (MODE == 4) {  // x = Re z, y = Im z at the stored modes (+ energy)
+        __syncthreads();
+        const T *fac = reinterpret_cast<const T *>(P.fac);
+        const T *rho = reinterpret_cast<const T *>(P.rho);
+#pragma unroll 4
+        for (int a = t; a < N; a += TPL) {
+            const int m = a - h;
+            const T2 z = buf[sidx(m < 0 ? m + NF : m)];
+            const T f = fac[a];
+            if (io.valid) {
+                const int64_t idx = io.out_base + a * io.out_st;
+                const T val = z.x * f * io.bfac;
+                reinterpret_cast<T *>(vout)[idx] = val;
+                if (rho) eacc.add(val, rho[idx]);
+            }
+            if (io2.valid) {
+                const int64_t idx = io2.out_base + a * io2.out_st;
+                const T val = z.y * f * io2.bfac;
+                reinterpret_cast<T *>(vout)[idx] = val;
+                if (rho) eacc.add(val, rho[idx]);
+            }
+        }
+    }
+    if constexpr (MODE == 3) {  // X(k) = (Z(k) + conj Z(n-k)) / 2, Y(k) = (Z(k) - conj Z(n-k)) / 2i
+        __syncthreads();
+        for (int k = t; k <= NF / 2; k += TPL) {
+            const T2 zk = buf[sidx(k)], zn = buf[sidx(k == 0 ? 0 : NF - k)];
+            if (io.valid)
+                reinterpret_cast<T2 *>(vout)[io.out_base + k * io.out_st] =
+                    cmake<T2>(T(0.5) * (zk.x + zn.x), T(0.5) * (zk.y - zn.y));
+            if (io2.valid)
+                reinterpret_cast<T2 *>(vout)[io2.out_base + k * io2.out_st] =
+                    cmake<T2>(T(0.5) * (zk.y + zn.y), T(0.5) * (zn.x - zk.x));
+        }
+    }
+
     if (P.out_kind == OUT_REAL_MODES && P.partials) {
         __syncthreads();  // the shared buffer becomes the reduction scratch
         const double2 tot = energy_block_sum(eacc, reinterpret_cast<double *>(smem_raw));
@@ -342,7 +420,7 @@ cudaError_t launch_nf(const PassDesc &p, const void *in, void *out, const void *
     cudaError_t e = cudaFuncSetAttribute(fft_pass_kernel<T, NF, MODE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int64_t nb = pass_blocks(p, MODE != 0);
+    const int64_t nb = pass_blocks(p, fft_is_row(MODE));
     if (nb == 0) return cudaSuccess;
     fft_pass_kernel<T, NF, MODE><<<(unsigned)nb, FftCfg<T, NF, MODE>::THREADS, smem, s>>>(
         p, in, out, reinterpret_cast<const cx_t<T> *>(tw));

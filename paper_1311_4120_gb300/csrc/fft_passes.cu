@@ -11,9 +11,17 @@ extern template cudaError_t launch_pass_mode<float, 2>(const PassDesc &, const v
 extern template cudaError_t launch_pass_mode<double, 0>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
 extern template cudaError_t launch_pass_mode<double, 1>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
 extern template cudaError_t launch_pass_mode<double, 2>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
+extern template cudaError_t launch_pass_mode<float, 3>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
+extern template cudaError_t launch_pass_mode<float, 4>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
+extern template cudaError_t launch_pass_mode<double, 3>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
+extern template cudaError_t launch_pass_mode<double, 4>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
 
 int pass_mode(const PassDesc &p, bool row) {
-    if (!row) return 0;
+    if (!row) {
+        if (p.in_kind == IN_REAL_MODES && p.out_kind == OUT_CPLX_HALF) return 3;
+        if (p.in_kind == IN_CPLX_HERM && p.out_kind == OUT_REAL_MODES) return 4;
+        return 0;
+    }
     return (p.in_kind == IN_CPLX_FOLD || p.in_kind == IN_CPLX_MULT) ? 2 : 1;
 }
 
@@ -61,7 +69,8 @@ bool pass_fits(const PassDesc &p) { return p.nrad > 0 && pass_threads(p) <= 1024
 
 int64_t pass_blocks(const PassDesc &p, bool row) {
     if (row) return (p.I + p.B - 1) / p.B;
-    return p.n_outer * ((p.I + p.B - 1) / p.B);
+    const int cpt = p.B * fft_pack(pass_mode(p, false));  // data columns per CTA
+    return p.n_outer * ((p.I + cpt - 1) / cpt);
 }
 
 size_t pass_smem(const PassDesc &p, int prec) {
@@ -73,7 +82,11 @@ size_t pass_smem(const PassDesc &p, int prec) {
 
 template <typename T>
 cudaError_t launch_colpass(const PassDesc &p, const void *in, void *out, const void *tw, cudaStream_t s) {
-    return launch_pass_mode<T, 0>(p, in, out, tw, s);
+    switch (pass_mode(p, false)) {
+        case 3: return launch_pass_mode<T, 3>(p, in, out, tw, s);
+        case 4: return launch_pass_mode<T, 4>(p, in, out, tw, s);
+        default: return launch_pass_mode<T, 0>(p, in, out, tw, s);
+    }
 }
 
 template <typename T>

@@ -64,7 +64,8 @@ size_t pass_smem(const PassDesc &p, int prec);
 void config_pass(PassDesc &p, int prec, bool row);
 bool pass_fits(const PassDesc &p);
 
-// pass mode 0: column pass; 1: row pass; 2: row pass reading fold / multiply input
+// pass mode 0: column pass; 1: row pass; 2: row pass reading fold / multiply input;
+// 3: column pass real -> Hermitian half, two lines per FFT; 4: Hermitian half -> real, two lines
 int pass_mode(const PassDesc &p, bool row);
 template <typename T, int MODE>
 cudaError_t launch_pass_mode(const PassDesc &p, const void *in, void *out, const void *tw,
