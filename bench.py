@@ -42,17 +42,16 @@ TOL = 1e-5                          # stated relative L-inf tolerance of the FP3
 # DRAM bytes per launch from an ncu capture of the kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum), keyed by stage name, with the hash of the kernel source the capture
 # was taken on: a changed source reports traffic null until it is captured again.
-# Measured on the 256^3 FP32 workload (profiles/spread_interp_c4_fp32.md,
-# profiles/fft_passes_c4_fp32.md).
+# Measured on the 256^3 FP32 workload (profiles/dram_traffic_c4_fp32.md).
 TRAFFIC = {
-    "interp": {"bytes": 471.3e6, "src": "da2c9d1b1cfcb447"},
-    "spread": {"bytes": 684.8e6, "src": "da2c9d1b1cfcb447"},
-    "fwd_fft_z": {"bytes": 148.0e6, "src": "00cab7524e8772fd"},
-    "fwd_fft_y": {"bytes": 345.4e6, "src": "00cab7524e8772fd"},
-    "fwd_fft_x": {"bytes": 749.6e6, "src": "00cab7524e8772fd"},
-    "inv_fft_x": {"bytes": 797.9e6, "src": "00cab7524e8772fd"},
-    "inv_fft_y": {"bytes": 373.5e6, "src": "00cab7524e8772fd"},
-    "inv_fft_z": {"bytes": 250.5e6, "src": "00cab7524e8772fd"},
+    "interp": {"bytes": 734.7e6, "src": "2259cb6543bd27fb"},
+    "spread": {"bytes": 971.8e6, "src": "2259cb6543bd27fb"},
+    "fwd_fft_z": {"bytes": 145.3e6, "src": "0ef5805e4c77e3b3"},
+    "fwd_fft_y": {"bytes": 341.5e6, "src": "0ef5805e4c77e3b3"},
+    "fwd_fft_x": {"bytes": 745.1e6, "src": "0ef5805e4c77e3b3"},
+    "inv_fft_x": {"bytes": 795.1e6, "src": "0ef5805e4c77e3b3"},
+    "inv_fft_y": {"bytes": 370.0e6, "src": "0ef5805e4c77e3b3"},
+    "inv_fft_z": {"bytes": 246.2e6, "src": "0ef5805e4c77e3b3"},
 }
 
 
