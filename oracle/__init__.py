@@ -15,6 +15,8 @@ nufft        O2: the Gaussian-gridding NUFFT of Section 2 (periodic heat kernel,
              FFT, deconvolution by the heat kernel's Fourier coefficients), FP64, in C.
 closed_forms O3: analytic potentials and energies of Section 4 and of the benchmark densities.
 pipeline     Algorithm 1 assembled from the above: type-2 -> multiply -> type-1 -> energy.
+alg2         Algorithm 2 (eq. 3.9): the partition of unity u = I_1 + I_2, I_1 by the
+             2x zero-padded FFT with U_hat (1 - p_d), I_2 by Algorithm 1 with weights times p_d.
 
 Every function is pinned in ``tests/test_oracle_*.py`` against something other than itself:
 library special cases (the uniform DFT), brute force, closed forms, the paper's printed
