@@ -11,11 +11,12 @@ oversampling factor 2 (Algorithm 2, step 3); I_2 by the NUFFT of Algorithm 1 on 
 set, since p_d confines it to a ball of radius P2 around the origin (step 4).
 
 Discrete definitions (the readings this oracle fixes; the GPU path computes the same):
-  * I_1 is the trapezoidal rule in k on the grid of the 2n-point DFT, k_g = g pi / (n h) with
-    g in numpy's fftfreq order (index n is frequency -n).  With rho zero-padded to 2n points
-    per axis and F = DFT_{2n}(rho_pad),
-        u1_m = (2n)^{-d} sum_g e^{2 pi i g.m / (2n)} M_g F_g,    m = 0..n-1 (array index),
-    because (2 pi)^{-d} (pi / (n h))^d h^d = (2n)^{-d}.  M_g = U_hat(k_g) (1 - p_d(k_g)) on
+  * I_1 is the trapezoidal rule in k on the grid of the n_pad-point DFT (n_pad >= 2n: the
+    oversampling factor 2 of step 3; n_pad = 2n unless given), k_g = 2 pi g / (n_pad h) with
+    g in numpy's fftfreq order (index n_pad/2 is frequency -n_pad/2).  With rho zero-padded to
+    n_pad points per axis and F = DFT_{n_pad}(rho_pad),
+        u1_m = n_pad^{-d} sum_g e^{2 pi i g.m / n_pad} M_g F_g,    m = 0..n-1 (array index),
+    because (2 pi)^{-d} (2 pi / (n_pad h))^d h^d = n_pad^{-d}.  M_g = U_hat(k_g) (1 - p_d(k_g)) on
     the closed ball |k_g| <= P (points on the sphere are included; the test uses a relative
     margin of 1e-12) and 0 outside it.  At k = 0 the symbol takes its limit: 1/a for the 3D
     Coulomb kernel ((1 - e^{-k^2/a}) / k^2 -> 1/a), 0 for the dipole kernels (1 - p_3 ~ k^2/a
@@ -84,15 +85,16 @@ def default_parameters(d: int, n: int, L: float, precision: str = "fp64") -> dic
     return {"r0": r0, "r1": r1, "P2": min(P, r1), "nodes2": (48, 96) if fp32 else (64, 128)}
 
 
-def frequencies(d: int, n: int, L: float) -> list:
-    """k values per axis of the 2n-point DFT grid, fftfreq order: 2 pi g / (2 n h)."""
+def frequencies(d: int, n: int, L: float, n_pad: int | None = None) -> list:
+    """k values per axis of the n_pad-point DFT grid, fftfreq order: 2 pi g / (n_pad h)."""
     h = L / n
-    return [2.0 * np.pi * np.fft.fftfreq(2 * n, d=h)] * d
+    return [2.0 * np.pi * np.fft.fftfreq(n_pad or 2 * n, d=h)] * d
 
 
 def multiplier_I1(d: int, n: int, L: float, kernel: str = "coulomb", axis=None, axis2=None,
-                  alpha: float = 0.0, a=None, r0=None, r1=None, P=None) -> np.ndarray:
-    """M_g = U_hat(k_g) (1 - p_d(k_g)) on |k_g| <= P, shape (2n,)*d in fftfreq order.
+                  alpha: float = 0.0, a=None, r0=None, r1=None, P=None,
+                  n_pad: int | None = None) -> np.ndarray:
+    """M_g = U_hat(k_g) (1 - p_d(k_g)) on |k_g| <= P, shape (n_pad,)*d in fftfreq order.
 
     Array axis 0 is the slowest (z in 3D, y in 2D), as for the densities."""
     h = L / n
@@ -100,7 +102,10 @@ def multiplier_I1(d: int, n: int, L: float, kernel: str = "coulomb", axis=None, 
         P = math.pi / h
     if P > math.pi / h * (1.0 + SPHERE_MARGIN):
         raise ValueError("Algorithm 2 needs P <= pi / h")
-    ks = np.meshgrid(*frequencies(d, n, L), indexing="ij")
+    n_pad = n_pad or 2 * n
+    if n_pad < 2 * n:
+        raise ValueError("I_1 needs n_pad >= 2n (oversampling factor 2)")
+    ks = np.meshgrid(*frequencies(d, n, L, n_pad), indexing="ij")
     # arrays are C-order over (z, y[, x]); U_hat takes k in (k_x, k_y[, k_z]) order
     k = np.stack([ks[d - 1 - i].ravel() for i in range(d)], axis=1)
     k2 = np.sum(k * k, axis=1)
@@ -116,14 +121,15 @@ def multiplier_I1(d: int, n: int, L: float, kernel: str = "coulomb", axis=None, 
     M = uh * one_minus_p
     M[zero] = (1.0 / a) if (d == 3 and kernel == "coulomb") else 0.0
     M[~inside] = 0.0
-    return M.reshape((2 * n,) * d)
+    return M.reshape((n_pad,) * d)
 
 
 def I1(rho: np.ndarray, M: np.ndarray) -> np.ndarray:
-    """u1 = (IDFT_{2n} (M DFT_{2n}(rho_pad)))[:n]^d, real part (imaginary part is rounding)."""
+    """u1 = (IDFT (M DFT(rho_pad)))[:n]^d on M's n_pad grid, real part (the imaginary part is
+    rounding); also returns F = DFT(rho_pad)."""
     rho = np.asarray(rho, dtype=np.float64)
     d, n = rho.ndim, rho.shape[0]
-    pad = np.zeros((2 * n,) * d)
+    pad = np.zeros((M.shape[0],) * d)
     pad[(slice(0, n),) * d] = rho
     F = np.fft.fftn(pad)
     v = np.fft.ifftn(M * F)
@@ -139,7 +145,7 @@ def I2_nodes(d: int, n: int, L: float, nodes2, kernel="coulomb", axis=None, axis
 
 def alg2_eval(rho: np.ndarray, L: float, nodes2, kernel: str = "coulomb", axis=None, axis2=None,
               alpha: float = 0.0, a=None, r0=None, r1=None, P=None, P2=None, lam: float = 1.0,
-              method: str = "nufft", setting: str = "parity") -> dict:
+              method: str = "nufft", setting: str = "parity", n_pad: int | None = None) -> dict:
     """Algorithm 2: u = I_1 + I_2 and E on the grid; also the parts and the dual energies."""
     rho = np.asarray(rho, dtype=np.float64)
     d, n = rho.ndim, rho.shape[0]
@@ -148,17 +154,18 @@ def alg2_eval(rho: np.ndarray, L: float, nodes2, kernel: str = "coulomb", axis=N
         P = math.pi / h
     if P2 is None or P2 > P:
         raise ValueError("P2 must be given and at most P")
-    M = multiplier_I1(d, n, L, kernel, axis, axis2, alpha, a, r0, r1, P)
+    M = multiplier_I1(d, n, L, kernel, axis, axis2, alpha, a, r0, r1, P, n_pad)
     u1, F = I1(rho, M)
+    npd = M.shape[0]
     k, W = I2_nodes(d, n, L, nodes2, kernel, axis, axis2, alpha, a, r0, r1, P2)
     rh = pipeline.type2(rho, L, k, method, setting)
     f = pipeline.type1(W * rh, d, n, L, k, method, setting)
     u2 = f.real.copy()
     u = u1 + u2
-    # dual energies: sum_m u1_m rho_m = (2n)^{-d} sum_g M_g |F_g|^2 (rho real)
-    e1 = 0.5 * lam * h ** d * (2 * n) ** (-d) * math.fsum((M * np.abs(F) ** 2).ravel().tolist())
+    # dual energies: sum_m u1_m rho_m = n_pad^{-d} sum_g M_g |F_g|^2 (rho real)
+    e1 = 0.5 * lam * h ** d * float(npd) ** (-d) * math.fsum((M * np.abs(F) ** 2).ravel().tolist())
     e2 = pipeline.energy_dual(rh, W, lam)
-    s1 = 0.5 * lam * h ** d * (2 * n) ** (-d) * math.fsum((np.abs(M) * np.abs(F) ** 2).ravel().tolist())
+    s1 = 0.5 * lam * h ** d * float(npd) ** (-d) * math.fsum((np.abs(M) * np.abs(F) ** 2).ravel().tolist())
     s2 = pipeline.energy_scale(rh, W, lam)
     return {
         "u": u, "u1": u1, "u2": u2,

@@ -64,27 +64,27 @@ def test_multiplier_entries_by_hand():
 
 # ----------------------------------------------------------------- I_1 against brute force
 def _I1_brute(rho, M):
-    """u1_m = (2n)^{-d} sum_g e^{2 pi i g.m/(2n)} M_g sum_l rho_l e^{-2 pi i g.l/(2n)}."""
-    d, n = rho.ndim, rho.shape[0]
-    g1 = np.concatenate([np.arange(0, n), np.arange(-n, 0)])       # fftfreq integers of 2n
+    """u1_m = q^{-d} sum_g e^{2 pi i g.m/q} M_g sum_l rho_l e^{-2 pi i g.l/q}, q = n_pad."""
+    d, n, q = rho.ndim, rho.shape[0], M.shape[0]
+    g1 = np.concatenate([np.arange(0, q // 2), np.arange(-(q // 2), 0)])  # fftfreq integers
     G = np.stack([a.ravel() for a in np.meshgrid(*([g1] * d), indexing="ij")], 1)
     Lx = np.stack([a.ravel() for a in np.meshgrid(*([np.arange(n)] * d), indexing="ij")], 1)
-    ph = np.exp(-2j * np.pi * (G @ Lx.T) / (2 * n))                 # ((2n)^d, n^d)
+    ph = np.exp(-2j * np.pi * (G @ Lx.T) / q)                       # (q^d, n^d)
     F = ph @ rho.ravel()
-    u = (ph.conj().T @ (M.ravel() * F)) / (2 * n) ** d
+    u = (ph.conj().T @ (M.ravel() * F)) / q ** d
     return u.real.reshape((n,) * d), float(np.max(np.abs(u.imag)))
 
 
-@pytest.mark.parametrize("d,n", [(3, 6), (2, 10)])
-def test_I1_matches_brute_force_sums(d, n):
+@pytest.mark.parametrize("d,n,n_pad", [(3, 6, None), (2, 10, None), (3, 5, 12), (2, 10, 24)])
+def test_I1_matches_brute_force_sums(d, n, n_pad):
     L = 3.0 * n / 4
     rng = np.random.default_rng(7 + d)
     rho = rng.standard_normal((n,) * d)
     if d == 3:
-        M = alg2.multiplier_I1(3, n, L, "dipole", axis=AX, a=1.3)
+        M = alg2.multiplier_I1(3, n, L, "dipole", axis=AX, a=1.3, n_pad=n_pad)
     else:
         M = alg2.multiplier_I1(2, n, L, "dipole", axis=AX, axis2=(0.2, 0.9, 0.1), alpha=0.4,
-                               r0=0.2, r1=3.0)
+                               r0=0.2, r1=3.0, n_pad=n_pad)
     u, _ = alg2.I1(rho, M)
     ub, im = _I1_brute(rho, M)
     assert np.max(np.abs(u - ub)) < 1e-13 * np.max(np.abs(ub))
@@ -173,7 +173,8 @@ def test_alg2_with_p_equal_one_is_algorithm_1(d):
 def test_dropping_one_minus_p_in_I1_is_caught(monkeypatch):
     monkeypatch.setattr(alg2, "multiplier_I1",
                         lambda d, n, L, kernel="coulomb", axis=None, axis2=None, alpha=0.0,
-                        a=None, r0=None, r1=None, P=None: _full_symbol(d, n, L, kernel, axis, P))
+                        a=None, r0=None, r1=None, P=None, n_pad=None:
+                        _full_symbol(d, n, L, kernel, axis, P))
     e1, _, e, _, _ = _coulomb_parts_err(n=24, L=12.0, s=1.5)
     assert e1 > 1e-6 and e > 1e-6
 
