@@ -76,6 +76,16 @@ typedef struct nlint_params {
     double alpha;        /* 2.5D dipole constant alpha (eq. dipkernelF2d); 0 in 3D         */
     int max_sub;         /* nodes per interpolation/spreading CTA; 0 = 1024 (FP32), 512 (FP64) */
     int crowd_min;       /* bins above this many nodes sum their tiles in FP64; 0 = 4096    */
+    /* Algorithm 2 (Section 3.3): algorithm = 2 evaluates u = I_1 + I_2 (eq. 3.9) with the
+     * partition p_3(k) = exp(-|k|^2/a) (eq. 3.10, 3D) or p_2(k) = erfc(12 (|k| - (R0+R1)/2) /
+     * (R1-R0)) / 2 (eq. 3.12, 2D): I_1 by the zero-padded FFT on the fine grid (n_fine >= 2n)
+     * with the multiplier U_hat (1 - p) on |k| <= P, I_2 by the NUFFT path on nodes of radius P2
+     * with weights W_j p(k_j).  n_r, n_theta, n_phi are then I_2's node counts (0 = 32x32x64 /
+     * 40x40x80 in 3D, 48x96 / 64x128 in 2D for FP32 / FP64).                                 */
+    int algorithm;       /* 1 (default, also for 0) or 2                                      */
+    double pu_a;         /* 3D: a of p_3; 0 = (11.8 / L)^2                                    */
+    double pu_r0, pu_r1; /* 2D: R0 < R1 of p_2; 0 = 12 / L and 160 / L                        */
+    double P2;           /* radius of I_2's nodes; 0 = min(P, 6.1 sqrt(a)) (3D), min(P, R1) (2D) */
 } nlint_params;
 
 /* Read-only description of a plan. */
@@ -90,6 +100,8 @@ typedef struct nlint_info {
     int64_t n_crowd_bins;   /* bins whose tiles are summed in FP64 (FP32 plans)         */
     int bin[3];             /* bin extent per array axis, in fine cells                 */
     int device;             /* CUDA device ordinal the plan lives on                    */
+    int algorithm;          /* 1 or 2; for 2 the node fields describe I_2's nodes       */
+    double pu_a, pu_r0, pu_r1, P2; /* Algorithm 2's partition parameters (0 if unused)  */
 } nlint_info;
 
 /* Fill *p with defaults (d = 3, Coulomb, eps = 1e-6, everything else automatic). */
@@ -109,7 +121,8 @@ int nlint_plan_info(nlint_plan plan, nlint_info *info);
 void nlint_plan_destroy(nlint_plan plan); /* NULL is a no-op; waits for the plan's work */
 
 /* u = U * rho on the grid (Algorithm 1 steps 4-5: type-2 NUFFT, multiply by W_j, type-1
- * NUFFT).  rho_dev, u_dev: n^d reals in the plan precision; they may not alias. */
+ * NUFFT; for an Algorithm 2 plan, u = I_1 + I_2 of eq. 3.9).  rho_dev, u_dev: n^d reals in the
+ * plan precision; they may not alias. */
 int nlint_eval(nlint_plan plan, const void *rho_dev, void *u_dev, void *stream);
 
 /* nlint_eval followed by the energy (lambda/2) h^d sum u rho, written as one double to
@@ -142,6 +155,8 @@ int nlint_energy_only(nlint_plan plan, const void *rho_dev, double lambda, doubl
  * inverse pass), inverse FFT, crop.  The result equals nlint_eval_energy's to the NUFFT
  * tolerance; no interpolation or spreading runs per evaluation.  This form is not in the paper:
  * it follows from the operator's Toeplitz structure. */
+/* Both return NLINT_EUNSUPPORTED for an Algorithm 2 plan (whose I_1 part already is an FFT
+ * convolution).  nlint_energy_only does the same. */
 int nlint_plan_toeplitz(nlint_plan plan, void *stream);
 int nlint_eval_toeplitz(nlint_plan plan, const void *rho_dev, void *u_dev, double lambda,
                         double *E_dev, void *stream);
@@ -154,7 +169,8 @@ int nlint_eval_host(nlint_plan plan, const void *rho_host, void *u_host, double 
 
 /* Stage entry points.  nlint_type2: rho (n^d reals) -> rho_hat_dev (n_nodes complex, the
  * canonical node order, eq. 3.2).  nlint_type1: c_dev (n_nodes complex, canonical order)
- * -> u_dev = Re sum_j c_j exp(+i k_j . x) (eq. 3.7 with c_j in place of W_j rho_hat_j). */
+ * -> u_dev = Re sum_j c_j exp(+i k_j . x) (eq. 3.7 with c_j in place of W_j rho_hat_j).
+ * For an Algorithm 2 plan the nodes are I_2's (and nlint_plan_nodes' W includes p(k_j)). */
 int nlint_type2(nlint_plan plan, const void *rho_dev, void *rho_hat_dev, void *stream);
 int nlint_type1(nlint_plan plan, const void *c_dev, void *u_dev, void *stream);
 

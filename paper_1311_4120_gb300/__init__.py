@@ -47,7 +47,9 @@ class nlint_params(ctypes.Structure):
                 ("P", ctypes.c_double), ("eps", ctypes.c_double), ("precision", ctypes.c_int),
                 ("w", ctypes.c_int), ("sigma", ctypes.c_double), ("device", ctypes.c_int),
                 ("axis2", ctypes.c_double * 3), ("alpha", ctypes.c_double),
-                ("max_sub", ctypes.c_int), ("crowd_min", ctypes.c_int)]
+                ("max_sub", ctypes.c_int), ("crowd_min", ctypes.c_int),
+                ("algorithm", ctypes.c_int), ("pu_a", ctypes.c_double),
+                ("pu_r0", ctypes.c_double), ("pu_r1", ctypes.c_double), ("P2", ctypes.c_double)]
 
 
 class nlint_tune_report(ctypes.Structure):
@@ -64,7 +66,9 @@ class nlint_info(ctypes.Structure):
                 ("sigma", ctypes.c_double), ("beta", ctypes.c_double),
                 ("workspace_bytes", ctypes.c_size_t), ("n_bins", ctypes.c_int64),
                 ("n_subproblems", ctypes.c_int64), ("n_crowd_bins", ctypes.c_int64),
-                ("bin", ctypes.c_int * 3), ("device", ctypes.c_int)]
+                ("bin", ctypes.c_int * 3), ("device", ctypes.c_int),
+                ("algorithm", ctypes.c_int), ("pu_a", ctypes.c_double),
+                ("pu_r0", ctypes.c_double), ("pu_r1", ctypes.c_double), ("P2", ctypes.c_double)]
 
 
 _lib = None
@@ -141,7 +145,8 @@ def _stream_ptr(stream) -> int:
 def make_params(d: int, n: int, L: float, kernel: str = "coulomb", axis=None, axis2=None,
                 alpha: float = 0.0, eps: float = 1e-6, precision: Optional[str] = None, nodes=None,
                 w: int = 0, sigma: float = 0.0, P: float = 0.0, device: int = -1,
-                max_sub: int = 0, crowd_min: int = 0) -> nlint_params:
+                max_sub: int = 0, crowd_min: int = 0, algorithm: int = 1, pu_a: float = 0.0,
+                pu_r0: float = 0.0, pu_r1: float = 0.0, P2: float = 0.0) -> nlint_params:
     """A filled nlint_params (the C-ABI's complete parameter set)."""
     lib = load_library()
     prm = nlint_params()
@@ -161,6 +166,8 @@ def make_params(d: int, n: int, L: float, kernel: str = "coulomb", axis=None, ax
     prm.precision = {None: -1, "fp32": NLINT_FP32, "fp64": NLINT_FP64}[precision]
     prm.w, prm.sigma, prm.P, prm.device = int(w), float(sigma), float(P), int(device)
     prm.max_sub, prm.crowd_min = int(max_sub), int(crowd_min)
+    prm.algorithm, prm.pu_a, prm.pu_r0, prm.pu_r1, prm.P2 = (int(algorithm), float(pu_a),
+                                                             float(pu_r0), float(pu_r1), float(P2))
     return prm
 
 
@@ -182,6 +189,9 @@ class Plan:
     ``axis2`` a second orientation, default the same; ``alpha`` the 2.5D constant).
     eps picks the precision (>= 1e-7: FP32, else FP64) and the spreading width unless given.
     nodes: (n_r, n_theta, n_phi) in 3D or (n_r, n_phi) in 2D; default from n.
+    algorithm=2 selects Algorithm 2 (partition of unity, eq. 3.9): ``pu_a`` (3D, p_3 of eq. 3.10)
+    or ``pu_r0``, ``pu_r1`` (2D, p_2 of eq. 3.12), ``P2`` the radius of I_2's nodes (0 = default);
+    ``nodes`` are then I_2's node counts.
     """
 
     def __init__(self, d: int, n: int, L: float, kernel: str = "coulomb",
@@ -189,7 +199,9 @@ class Plan:
                  precision: Optional[str] = None, nodes: Optional[Sequence[int]] = None,
                  w: int = 0, sigma: float = 0.0, P: float = 0.0, device: Optional[int] = None,
                  axis2: Optional[Sequence[float]] = None, alpha: float = 0.0,
-                 max_sub: int = 0, crowd_min: int = 0, params: Optional["nlint_params"] = None):
+                 max_sub: int = 0, crowd_min: int = 0, algorithm: int = 1, pu_a: float = 0.0,
+                 pu_r0: float = 0.0, pu_r1: float = 0.0, P2: float = 0.0,
+                 params: Optional["nlint_params"] = None):
         lib = load_library()
         prm = nlint_params()
         lib.nlint_params_default(ctypes.byref(prm))
@@ -215,6 +227,8 @@ class Plan:
             device = torch.cuda.current_device() if torch.cuda.is_available() else -1
         prm.device = int(device)
         prm.max_sub, prm.crowd_min = int(max_sub), int(crowd_min)
+        prm.algorithm, prm.pu_a, prm.pu_r0, prm.pu_r1, prm.P2 = (
+            int(algorithm), float(pu_a), float(pu_r0), float(pu_r1), float(P2))
         if params is not None:  # a complete parameter set, e.g. from autotune()
             prm = params
             prm.device = int(device)

@@ -356,7 +356,8 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MO
                                 const int a = m + h;
                                 const T *fac = reinterpret_cast<const T *>(P.fac);
                                 const int64_t idx = io.out_base + a * io.out_st;
-                                const T val = x.x * fac[a] * io.bfac;
+                                T val = x.x * fac[a] * io.bfac;
+                                if (P.accum) val += reinterpret_cast<const T *>(vout)[idx];
                                 reinterpret_cast<T *>(vout)[idx] = val;
                                 if (P.rho)
                                     eacc.add(val, reinterpret_cast<const T *>(P.rho)[idx]);
@@ -381,13 +382,15 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MO
             const T f = fac[a];
             if (io.valid) {
                 const int64_t idx = io.out_base + a * io.out_st;
-                const T val = z.x * f * io.bfac;
+                T val = z.x * f * io.bfac;
+                if (P.accum) val += reinterpret_cast<const T *>(vout)[idx];
                 reinterpret_cast<T *>(vout)[idx] = val;
                 if (rho) eacc.add(val, rho[idx]);
             }
             if (io2.valid) {
                 const int64_t idx = io2.out_base + a * io2.out_st;
-                const T val = z.y * f * io2.bfac;
+                T val = z.y * f * io2.bfac;
+                if (P.accum) val += reinterpret_cast<const T *>(vout)[idx];
                 reinterpret_cast<T *>(vout)[idx] = val;
                 if (rho) eacc.add(val, rho[idx]);
             }

@@ -53,6 +53,7 @@ struct PassDesc {
     const void *mult;    // IN_CPLX_MULT: real multiplier, same row layout as the input
     const void *rho;     // energy: density (OUT_REAL_MODES)
     double2 *partials;   // energy: one compensated partial per CTA (OUT_REAL_MODES)
+    int accum;           // OUT_REAL_MODES: add to the output instead of overwriting it
 };
 
 void make_radix(int n, PassDesc &p);

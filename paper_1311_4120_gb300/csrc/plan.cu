@@ -136,6 +136,10 @@ struct nlint_plan_s {
     void *d_fac1 = nullptr, *d_khat = nullptr;
     bool toeplitz = false;
     nlint::PassDesc T1, U1, U3;
+    // Algorithm 2 (eq. 3.9): I_1's multiplier U_hat (1 - p) lives in d_khat and uses the
+    // T1/U1/U3 passes; the node set is I_2's (radius P2, weights times p)
+    int algorithm = 1;
+    double pu_a = 0.0, pu_r0 = 0.0, pu_r1 = 0.0, rad2 = 0.0;  // rad2: I_2's radius P2
     // host copies for inspection (canonical order)
     std::vector<double> k_canon, W_canon;
     // stage timing
@@ -173,6 +177,27 @@ static double u_hat(const nlint_plan_s *p, const double k[3]) {
     }
     const double kn = k[0] * n[0] + k[1] * n[1], km = k[0] * m[0] + k[1] * m[1];
     return -p->alpha + 3.0 * (kn * km - n[2] * m[2] * k2) / (2.0 * std::sqrt(k2));
+}
+
+// Partition of unity of Algorithm 2: p_3(k) = exp(-|k|^2 / a) (eq. 3.10),
+// p_2(k) = erfc(12 (|k| - (R0 + R1)/2) / (R1 - R0)) / 2 (eq. 3.12).
+static double partition(const nlint_plan_s *p, const double k[3]) {
+    const double k2 = k[0] * k[0] + k[1] * k[1] + (p->d == 3 ? k[2] * k[2] : 0.0);
+    if (p->d == 3) return std::exp(-k2 / p->pu_a);
+    return 0.5 * std::erfc(12.0 * (std::sqrt(k2) - 0.5 * (p->pu_r0 + p->pu_r1)) / (p->pu_r1 - p->pu_r0));
+}
+
+// I_1's multiplier of Algorithm 2 (eq. 3.9, step 3): M(k) = U_hat(k) (1 - p(k)) on the closed
+// ball |k| <= P (a relative margin of 1e-12 keeps the sphere's lattice points), 0 outside.  At
+// k = 0 the symbol takes its limit: 1/a for the 3D Coulomb kernel ((1 - e^{-k^2/a}) / k^2),
+// 0 otherwise (1 - p_3 ~ k^2/a against a bounded dipole symbol; 1 - p_2(0) is below rounding).
+static double alg2_multiplier(const nlint_plan_s *p, const double k[3]) {
+    const double k2 = k[0] * k[0] + k[1] * k[1] + (p->d == 3 ? k[2] * k[2] : 0.0);
+    const double pm = p->P * (1.0 + 1e-12);
+    if (k2 > pm * pm) return 0.0;
+    if (k2 == 0.0) return (p->d == 3 && p->prm.kernel == NLINT_COULOMB) ? 1.0 / p->pu_a : 0.0;
+    const double one_minus_p = p->d == 3 ? -std::expm1(-k2 / p->pu_a) : 1.0 - partition(p, k);
+    return u_hat(p, k) * one_minus_p;
 }
 
 // Fourier transform of the ES kernel, Phi(xi) = int_{-1}^{1} phi(z) cos(xi z) dz, by a
@@ -216,6 +241,8 @@ static void plan_free(nlint_plan_s *p) {
     for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
 }
 
+static int alg2_setup(nlint_plan_s *p);
+
 static int build_plan(const nlint_params *in, nlint_plan_s *p) {
     p->prm = *in;
     const nlint_params &q = *in;
@@ -247,6 +274,25 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
     p->P = (q.P > 0.0) ? q.P : pmax;
     if (p->P > pmax * (1.0 + 1e-12))
         return fail(NLINT_EINVAL, "P must not exceed pi/h (nodes beyond the grid's Nyquist radius)");
+    p->algorithm = q.algorithm == 0 ? 1 : q.algorithm;
+    if (p->algorithm != 1 && p->algorithm != 2) return fail(NLINT_EINVAL, "algorithm must be 1 or 2");
+    if (p->algorithm == 2) {
+        // partition of unity (eq. 3.9): p_3 = exp(-|k|^2/a) (eq. 3.10), p_2 of eq. 3.12
+        if (!(q.pu_a >= 0.0) || !(q.pu_r0 >= 0.0) || !(q.pu_r1 >= 0.0) || !(q.P2 >= 0.0) ||
+            !std::isfinite(q.pu_a) || !std::isfinite(q.pu_r0) || !std::isfinite(q.pu_r1) || !std::isfinite(q.P2))
+            return fail(NLINT_EINVAL, "Algorithm 2 parameters (pu_a, pu_r0, pu_r1, P2) must be finite and >= 0");
+        if (q.d == 3) {
+            p->pu_a = q.pu_a > 0.0 ? q.pu_a : (11.8 / q.L) * (11.8 / q.L);
+            p->rad2 = std::min(p->P, 6.1 * std::sqrt(p->pu_a));
+        } else {
+            p->pu_r0 = q.pu_r0 > 0.0 ? q.pu_r0 : 12.0 / q.L;
+            p->pu_r1 = q.pu_r1 > 0.0 ? q.pu_r1 : 160.0 / q.L;
+            if (!(p->pu_r1 > p->pu_r0)) return fail(NLINT_EINVAL, "Algorithm 2 needs pu_r0 < pu_r1");
+            p->rad2 = std::min(p->P, p->pu_r1);
+        }
+        if (q.P2 > 0.0) p->rad2 = q.P2;
+        if (p->rad2 > p->P * (1.0 + 1e-12)) return fail(NLINT_EINVAL, "P2 must not exceed P");
+    }
     double eps = q.eps > 0.0 ? q.eps : 1e-6;
     if (eps < 1e-15) eps = 1e-15;
     p->prec = (q.precision == NLINT_FP32 || q.precision == NLINT_FP64) ? q.precision
@@ -266,7 +312,8 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
     const double sig_eff = (double)p->n_fine / (double)p->N;
     p->beta = 0.97 * M_PI * (1.0 - 1.0 / (2.0 * sig_eff)) * w;  // ES shape parameter
 
-    p->nr = q.n_r > 0 ? q.n_r : default_nr(p->d, p->N);
+    const int64_t nr_alg2 = p->d == 3 ? (p->prec == NLINT_FP32 ? 32 : 40) : (p->prec == NLINT_FP32 ? 48 : 64);
+    p->nr = q.n_r > 0 ? q.n_r : (p->algorithm == 2 ? nr_alg2 : default_nr(p->d, p->N));
     if (p->d == 3) {
         p->nt = q.n_theta > 0 ? q.n_theta : p->nr;
         p->nphi = q.n_phi > 0 ? q.n_phi : 2 * p->nr;
@@ -288,8 +335,9 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
     // ---------------- nodes and weights (eq. 3.7), FP64, canonical order
     std::vector<double> xr, wr, xt, wt;
     gauss_legendre((int)p->nr, xr, wr);
-    for (auto &v : xr) v = p->P * (1.0 + v) / 2.0;
-    for (auto &v : wr) v = p->P * v / 2.0;
+    const double Prad = p->algorithm == 2 ? p->rad2 : p->P;  // Algorithm 2: I_2's nodes
+    for (auto &v : xr) v = Prad * (1.0 + v) / 2.0;
+    for (auto &v : wr) v = Prad * v / 2.0;
     if (p->d == 3) {
         gauss_legendre((int)p->nt, xt, wt);
         for (auto &v : xt) v = M_PI * (1.0 + v) / 2.0;
@@ -318,6 +366,7 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
                 }
                 for (int e = 0; e < p->d; e++) p->k_canon[(size_t)j * p->d + e] = k[e];
                 p->W_canon[j] = wj * u_hat(p, k) / twopi_d;
+                if (p->algorithm == 2) p->W_canon[j] *= partition(p, k);
             }
 
     // ---------------- half node set, stencil origins, tile sort
@@ -612,6 +661,88 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
     acc += p->bytes_A + p->bytes_B + std::max(p->bytes_G, p->bytes_Hext) + p->bytes_c +
            sizeof(double2) * (size_t)std::max(p->n_partials, 1024);
     p->ws_bytes = acc;
+    if (p->algorithm == 2) return alg2_setup(p);
+    return NLINT_OK;
+}
+
+// ------------------------------------------------------------------------- FFT convolution
+// Unit deconvolution factors for the passes of an FFT convolution on the fine grid.
+static int upload_ones(nlint_plan_s *p) {
+    if (p->d_fac1) return NLINT_OK;
+    std::vector<double> ones((size_t)std::max<int64_t>(p->N, p->n_fine), 1.0);
+    size_t acc = 0;
+    return p->prec == NLINT_FP32 ? upload<float>(&p->d_fac1, ones, acc) : upload<double>(&p->d_fac1, ones, acc);
+}
+
+// Passes of u = crop(IFFT(K_hat FFT(rho_pad))) on the fine grid: the NUFFT passes with unit
+// factors, and the multiply by the real half grid d_khat fused into the first inverse pass.
+static void conv_passes(nlint_plan_s *p) {
+    const int d = p->d, n = p->n_fine;
+    const int64_t N = p->N, nh = n / 2 + 1;
+    p->T1 = p->P1;
+    p->T1.fac = p->d_fac1;
+    p->U3 = p->Q3;
+    p->U3.fac = p->d_fac1;
+    std::memset(&p->U1, 0, sizeof(p->U1));
+    p->U1.n = n;
+    make_radix(n, p->U1);
+    p->U1.sign = +1;
+    p->U1.N = (int)N;
+    p->U1.dim = d;
+    p->U1.in_kind = IN_CPLX_MULT;
+    p->U1.out_kind = OUT_CPLX_MODES;
+    p->U1.I = (d == 3) ? nh * n : nh;
+    p->U1.in_so = n;
+    p->U1.out_so = N;
+    p->U1.mult = p->d_khat;
+    config_pass(p->U1, p->prec, true);
+}
+
+// Algorithm 2: I_1's multiplier M(k) / n_fine^d on the real half grid of the fine grid's DFT
+// (axis 0 non-negative frequencies 0..n/2, the others in FFT order; frequency index g <-> k =
+// 2 pi g' / (n_fine h) with g' the signed index, n/2 -> -n/2), in the plan precision.
+template <typename T>
+static int alg2_fill_multiplier(nlint_plan_s *p) {
+    const int d = p->d, n = p->n_fine;
+    const int64_t nh = n / 2 + 1, rows = (d == 3) ? nh * n : nh;
+    const double dk = 2.0 * M_PI / ((double)n * p->h);
+    const double inv = 1.0 / std::pow((double)n, d);
+    std::vector<T> m((size_t)(rows * n));
+    auto sgn = [n](int64_t g) { return (double)(g < n / 2 ? g : g - n); };
+    auto work = [&](int64_t r0, int64_t r1) {
+        for (int64_t r = r0; r < r1; r++) {
+            const int64_t g0 = (d == 3) ? r / n : r, g1 = (d == 3) ? r % n : 0;
+            for (int64_t c = 0; c < n; c++) {
+                double k[3] = {0.0, 0.0, 0.0};
+                if (d == 3) {
+                    k[2] = dk * sgn(g0);  // array axis 0 is z
+                    k[1] = dk * sgn(g1);
+                    k[0] = dk * sgn(c);
+                } else {
+                    k[1] = dk * sgn(g0);  // array axis 0 is y
+                    k[0] = dk * sgn(c);
+                }
+                m[(size_t)(r * n + c)] = (T)(alg2_multiplier(p, k) * inv);
+            }
+        }
+    };
+    const int nt = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; t++) th.emplace_back(work, rows * t / nt, rows * (t + 1) / nt);
+    for (auto &t : th) t.join();
+    CK(cudaMalloc(&p->d_khat, m.size() * sizeof(T)));
+    CK(cudaMemcpy(p->d_khat, m.data(), m.size() * sizeof(T), cudaMemcpyHostToDevice));
+    p->ws_bytes += m.size() * sizeof(T);
+    return NLINT_OK;
+}
+
+static int alg2_setup(nlint_plan_s *p) {
+    int rc = upload_ones(p);
+    if (rc) return rc;
+    p->ws_bytes += (size_t)std::max<int64_t>(p->N, p->n_fine) * (p->prec == NLINT_FP32 ? 4 : 8);
+    rc = p->prec == NLINT_FP32 ? alg2_fill_multiplier<float>(p) : alg2_fill_multiplier<double>(p);
+    if (rc) return rc;
+    conv_passes(p);
     return NLINT_OK;
 }
 
@@ -673,7 +804,8 @@ static NodeDesc node_desc(nlint_plan_s *p) {
 }
 
 template <typename T>
-static int run_type1(nlint_plan_s *p, void *u, const void *rho_energy, cudaStream_t s) {
+static int run_type1(nlint_plan_s *p, void *u, const void *rho_energy, cudaStream_t s,
+                     bool accumulate = false) {
     CK(cudaMemsetAsync(p->d_bufG, 0, p->bytes_Hext, s));
     if (p->ncrowd) CK(cudaMemsetAsync(p->d_crowd, 0, p->bytes_crowd, s));
     CK(launch_spread<T>(node_desc(p), p->d_c, p->d_bufG, s));
@@ -695,14 +827,20 @@ static int run_type1(nlint_plan_s *p, void *u, const void *rho_energy, cudaStrea
     PassDesc q3 = p->Q3;
     q3.rho = rho_energy;
     q3.partials = rho_energy ? p->d_partials : nullptr;
+    q3.accum = accumulate ? 1 : 0;  // u += (Algorithm 2: I_2 onto I_1)
     CK(launch_colpass<T>(q3, p->d_bufA, u, p->d_tw, s));
     stage_mark(p, s, p->d == 3 ? "inv_fft_z" : "inv_fft_y");
     return NLINT_OK;
 }
 
 template <typename T>
+static int run_alg2(nlint_plan_s *p, const void *rho, void *u, double lambda, double *E,
+                    cudaStream_t s);
+
+template <typename T>
 static int run_eval(nlint_plan_s *p, const void *rho, void *u, double lambda, double *E,
                     cudaStream_t s) {
+    if (p->algorithm == 2) return run_alg2<T>(p, rho, u, lambda, E, s);
     p->ev_used = 0;
     stage_mark(p, s, "start");
     int rc = run_type2<T>(p, rho, s);
@@ -753,6 +891,43 @@ static int run_toeplitz(nlint_plan_s *p, const void *rho, void *u, double lambda
     return NLINT_OK;
 }
 
+// Algorithm 2 (Section 3.3, eq. 3.9): u = I_1 + I_2.  I_1 (step 3): zero-padded forward FFT of
+// rho on the fine grid, multiply by U_hat (1 - p) (fused into the first inverse pass), inverse
+// FFT, crop -> u.  I_2 (step 4): the NUFFT path on I_2's nodes (weights W_j p(k_j)), its last
+// pass adding onto u and taking the energy over the sum (step 5 and Remark 3.3).
+template <typename T>
+static int run_alg2(nlint_plan_s *p, const void *rho, void *u, double lambda, double *E,
+                    cudaStream_t s) {
+    p->ev_used = 0;
+    stage_mark(p, s, "start");
+    CK(launch_colpass<T>(p->T1, rho, p->d_bufA, p->d_tw, s));
+    if (p->d == 3) {
+        CK(launch_colpass<T>(p->P2, p->d_bufA, p->d_bufB, p->d_tw, s));
+        CK(launch_rowpass<T>(p->P3, p->d_bufB, p->d_bufG, p->d_tw, s));
+        CK(launch_rowpass<T>(p->U1, p->d_bufG, p->d_bufB, p->d_tw, s));
+        CK(launch_colpass<T>(p->Q2, p->d_bufB, p->d_bufA, p->d_tw, s));
+    } else {
+        CK(launch_rowpass<T>(p->P3, p->d_bufA, p->d_bufG, p->d_tw, s));
+        CK(launch_rowpass<T>(p->U1, p->d_bufG, p->d_bufA, p->d_tw, s));
+    }
+    CK(launch_colpass<T>(p->U3, p->d_bufA, u, p->d_tw, s));
+    p->launches += (p->d == 3) ? 6 : 4;
+    stage_mark(p, s, "I1_fft_conv");
+    int rc = run_type2<T>(p, rho, s);
+    if (rc) return rc;
+    CK(launch_interp<T>(node_desc(p), p->d_bufG, p->d_c, 1, s));
+    p->launches += 1;
+    stage_mark(p, s, "interp");
+    rc = run_type1<T>(p, u, E ? rho : nullptr, s, true);
+    if (rc) return rc;
+    if (E) {
+        CK(launch_energy_final(p->d_partials, p->n_partials, 0.5 * lambda * std::pow(p->h, p->d), E, s));
+        p->launches += 1;
+        stage_mark(p, s, "energy");
+    }
+    return NLINT_OK;
+}
+
 static int check_plan(nlint_plan p) {
     if (!p) return fail(NLINT_EINVAL, "plan is NULL");
     cudaError_t e = cudaSetDevice(p->device);
@@ -777,6 +952,7 @@ void nlint_params_default(nlint_params *p) {
     p->eps = 1e-6;
     p->precision = -1;
     p->device = -1;
+    p->algorithm = 1;
 }
 
 int nlint_plan_create_ex(const nlint_params *prm, nlint_plan *out) {
@@ -850,6 +1026,11 @@ int nlint_plan_info(nlint_plan p, nlint_info *info) {
     info->n_crowd_bins = p->ncrowd;
     for (int a = 0; a < 3; a++) info->bin[a] = p->B[a];
     info->device = p->device;
+    info->algorithm = p->algorithm;
+    info->pu_a = p->pu_a;
+    info->pu_r0 = p->pu_r0;
+    info->pu_r1 = p->pu_r1;
+    info->P2 = p->rad2;
     return NLINT_OK;
 }
 
@@ -904,6 +1085,8 @@ int nlint_energy(nlint_plan p, const void *rho, const void *u, double lambda, do
 int nlint_plan_toeplitz(nlint_plan p, void *stream) {
     int rc = check_plan(p);
     if (rc) return rc;
+    if (p->algorithm == 2)
+        return fail(NLINT_EUNSUPPORTED, "nlint_plan_toeplitz: not for an Algorithm 2 plan");
     if (p->toeplitz) return NLINT_OK;
     cudaStream_t s = (cudaStream_t)stream;
     const int d = p->d, n = p->n_fine;
@@ -913,12 +1096,7 @@ int nlint_plan_toeplitz(nlint_plan p, void *stream) {
     const int64_t full_cells = (d == 3) ? (int64_t)n * n * n : (int64_t)n * n;
     const int64_t grid = (d == 3) ? N * N * N : N * N;
     // ones (the convolution needs no deconvolution), the kernel's real half grid
-    {
-        std::vector<double> ones((size_t)std::max<int64_t>(N, n), 1.0);
-        size_t acc = 0;
-        if ((rc = p->prec == NLINT_FP32 ? upload<float>(&p->d_fac1, ones, acc) : upload<double>(&p->d_fac1, ones, acc)))
-            return rc;
-    }
+    if ((rc = upload_ones(p))) return rc;
     CK(cudaMalloc(&p->d_khat, (size_t)half_cells * es));
     struct Tmp {
         void *kbuf = nullptr, *c = nullptr, *u = nullptr;
@@ -1019,25 +1197,7 @@ int nlint_plan_toeplitz(nlint_plan p, void *stream) {
     else CK(launch_extract_real<double>(half_cells, kout, inv, p->d_khat, s));
     CK(cudaStreamSynchronize(s));
 
-    // evaluation passes: the NUFFT passes with unit factors and the multiply fused into the
-    // first inverse pass
-    p->T1 = p->P1;
-    p->T1.fac = p->d_fac1;
-    p->U3 = p->Q3;
-    p->U3.fac = p->d_fac1;
-    std::memset(&p->U1, 0, sizeof(p->U1));
-    p->U1.n = n;
-    make_radix(n, p->U1);
-    p->U1.sign = +1;
-    p->U1.N = (int)N;
-    p->U1.dim = d;
-    p->U1.in_kind = IN_CPLX_MULT;
-    p->U1.out_kind = OUT_CPLX_MODES;
-    p->U1.I = (d == 3) ? nh * n : nh;
-    p->U1.in_so = n;
-    p->U1.out_so = N;
-    p->U1.mult = p->d_khat;
-    config_pass(p->U1, p->prec, true);
+    conv_passes(p);
     p->ws_bytes += (size_t)half_cells * es + (size_t)std::max<int64_t>(N, n) * es;
     p->toeplitz = true;
     return NLINT_OK;
@@ -1048,6 +1208,8 @@ int nlint_eval_toeplitz(nlint_plan p, const void *rho, void *u, double lambda, d
     int rc = check_plan(p);
     if (rc) return rc;
     if (!rho || !u) return fail(NLINT_EINVAL, "NULL rho or u");
+    if (p->algorithm == 2)
+        return fail(NLINT_EUNSUPPORTED, "nlint_eval_toeplitz: not for an Algorithm 2 plan");
     if (!p->toeplitz) return fail(NLINT_EINVAL, "nlint_plan_toeplitz has not been called on this plan");
     cudaStream_t s = (cudaStream_t)stream;
     return p->prec == NLINT_FP32 ? run_toeplitz<float>(p, rho, u, lambda, E_dev, s)
@@ -1059,6 +1221,8 @@ int nlint_energy_only(nlint_plan p, const void *rho, double lambda, double *E_de
     int rc = check_plan(p);
     if (rc) return rc;
     if (!rho) return fail(NLINT_EINVAL, "NULL rho");
+    if (p->algorithm == 2)
+        return fail(NLINT_EUNSUPPORTED, "nlint_energy_only: not for an Algorithm 2 plan");
     cudaStream_t s = (cudaStream_t)stream;
     p->ev_used = 0;
     // E = (lambda/2) sum_j W_j |rho_hat_j|^2 over the full node set = lambda sum over the half

@@ -71,6 +71,11 @@ def _create(lib, **kw):
     (dict(n_phi=63), -1, "n_phi"),
     (dict(n_theta=31, n_r=16, n_phi=32), -1, "n_theta"),
     (dict(sigma=1.1), -1, "sigma"),
+    (dict(algorithm=3), -1, "algorithm"),
+    (dict(algorithm=2, pu_a=-1.0), -1, "Algorithm 2"),
+    (dict(algorithm=2, pu_a=float("nan")), -1, "Algorithm 2"),
+    (dict(algorithm=2, P2=100.0), -1, "P2"),
+    (dict(algorithm=2, d=2, pu_r0=2.0, pu_r1=1.0), -1, "pu_r0 < pu_r1"),
 ])
 def test_bad_arguments_are_rejected_before_any_gpu_work(lib, kw, code, word):
     rc, msg = _create(lib, **kw)
@@ -91,3 +96,9 @@ def test_params_default(lib):
     lib.nlint_params_default(ctypes.byref(prm))
     assert prm.d == 3 and prm.kernel == 0 and prm.precision == -1 and prm.device == -1
     assert prm.eps == 1e-6
+    # the last fields: the ctypes mirror of the struct ends where the C struct does
+    assert prm.algorithm == 1 and prm.pu_a == 0.0 and prm.pu_r0 == 0.0 and prm.P2 == 0.0
+    sentinel = (ctypes.c_char * (ctypes.sizeof(prm) + 64))()
+    ctypes.memset(sentinel, 0x5A, len(sentinel))
+    lib.nlint_params_default(ctypes.cast(sentinel, ctypes.POINTER(pkg.nlint_params)))
+    assert bytes(sentinel[ctypes.sizeof(prm):]) == b"\x5a" * 64
