@@ -144,6 +144,7 @@ struct LineIO {
     T bfac;                     // deconvolution product over the other axes
     int64_t mirror_base;        // fold: the mirrored line of H+, or -1
     const T *mult;              // IN_CPLX_MULT: multiplier row (same layout as the input)
+    int win;                    // frequency window (0 = none), see PassDesc
 
     // FFT-index entry e of the input line (zero outside the stored modes)
     __device__ __forceinline__ T2 load(int e, const void *vin) const {
@@ -167,9 +168,15 @@ struct LineIO {
                 v = reinterpret_cast<const T2 *>(vin)[in_base + e * in_st];
                 break;
             case IN_CPLX_HERM:
+                if (win > 0 && (e <= n / 2 ? e : n - e) > win) break;  // outside the window
                 v = (e <= n / 2) ? reinterpret_cast<const T2 *>(vin)[in_base + e * in_st]
                                  : cconj(reinterpret_cast<const T2 *>(vin)[in_base + (n - e) * in_st]);
                 break;
+            case IN_CPLX_WIN: {
+                const int c = e <= win ? e : (e >= n - win ? e - n + 2 * win + 1 : -1);
+                if (c >= 0) v = reinterpret_cast<const T2 *>(vin)[in_base + c * in_st];
+                break;
+            }
             case IN_CPLX_MULT:
                 v = cscale(reinterpret_cast<const T2 *>(vin)[in_base + e], mult[in_base + e]);
                 break;
@@ -212,6 +219,7 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MO
     io.fac = reinterpret_cast<const T *>(P.fac);
     io.mirror_base = -1;
     io.mult = reinterpret_cast<const T *>(P.mult);
+    io.win = P.win;
     io.bfac = T(1);
     LineIO<T> io2;  // packed modes: the second data column of this FFT line (set field by field)
     io2.n = P.n;
@@ -220,6 +228,7 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MO
     io2.fac = io.fac;
     io2.mirror_base = -1;
     io2.mult = io.mult;
+    io2.win = P.win;
     io2.bfac = T(1);
     io2.valid = false;
     io2.in_base = io2.out_base = 0;
@@ -251,9 +260,18 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MO
         io.in_st = 1;
         io.out_st = 1;
         io.out_base = q * P.out_so;
+        // windowed 3D row pass: compact row q -> plane, full-grid row
+        int64_t wz = 0, wy = 0;
+        if (P.win_rows > 0) {
+            wz = q / P.win_rows;
+            const int64_t c = q % P.win_rows;
+            wy = c <= P.win ? c : P.n - (P.win_rows - c);
+            if (P.out_kind == OUT_CPLX_FULL) io.out_base = (wz * P.n + wy) * P.out_so;
+        }
         if (P.in_kind == IN_CPLX_FOLD) {
             const int n = P.n;
-            const int64_t lz = q / P.fold_rows_per_plane, ly = q % P.fold_rows_per_plane;
+            const int64_t lz = P.win_rows > 0 ? wz : q / P.fold_rows_per_plane;
+            const int64_t ly = P.win_rows > 0 ? wy : q % P.fold_rows_per_plane;
             io.in_base = (lz + P.fold_pad) * P.fold_plane + ly * n;
             if (lz <= P.fold_pad || lz >= n / 2 - P.fold_pad) {
                 const int64_t mz = (lz <= P.fold_pad) ? -lz : n - lz;
@@ -339,11 +357,18 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MO
                     const T2 x = v[b][r];
                     switch (P.out_kind) {
                         case OUT_CPLX_FULL:
-                            reinterpret_cast<T2 *>(vout)[io.out_base + e * io.out_st] = x;
+                            if (P.win == 0 || e <= P.win || e >= NF - P.win)
+                                reinterpret_cast<T2 *>(vout)[io.out_base + e * io.out_st] = x;
                             break;
                         case OUT_CPLX_HALF:
-                            if (e <= NF / 2) reinterpret_cast<T2 *>(vout)[io.out_base + e * io.out_st] = x;
+                            if (e <= (P.win > 0 ? P.win : NF / 2))
+                                reinterpret_cast<T2 *>(vout)[io.out_base + e * io.out_st] = x;
                             break;
+                        case OUT_CPLX_WIN: {
+                            const int c = e <= P.win ? e : (e >= NF - P.win ? e - NF + 2 * P.win + 1 : -1);
+                            if (c >= 0) reinterpret_cast<T2 *>(vout)[io.out_base + c * io.out_st] = x;
+                            break;
+                        }
                         case OUT_CPLX_MODES: {
                             const int m = e < NF / 2 ? e : e - NF;
                             if (m >= -h && m < h)
@@ -398,7 +423,8 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MO
     }
     if constexpr (MODE == 3) {  // X(k) = (Z(k) + conj Z(n-k)) / 2, Y(k) = (Z(k) - conj Z(n-k)) / 2i
         __syncthreads();
-        for (int k = t; k <= NF / 2; k += TPL) {
+        const int klim = P.win > 0 ? P.win : NF / 2;  // OUT_CPLX_HALF (within the window)
+        for (int k = t; k <= klim; k += TPL) {
             const T2 zk = buf[sidx(k)], zn = buf[sidx(k == 0 ? 0 : NF - k)];
             if (io.valid)
                 reinterpret_cast<T2 *>(vout)[io.out_base + k * io.out_st] =

@@ -23,13 +23,16 @@ enum InKind {
     IN_CPLX_FULL = 2,    // n complex
     IN_CPLX_HERM = 3,    // n/2+1 complex of a Hermitian line (rest by conjugate symmetry)
     IN_CPLX_FOLD = 4,    // row pass only: n complex plus the conjugated mirror row (fold)
-    IN_CPLX_MULT = 5     // row pass only: n complex times a real n-entry row of `mult`
+    IN_CPLX_MULT = 5,    // row pass only: n complex times a real n-entry row of `mult`
+    IN_CPLX_WIN = 6      // the 2 win + 1 window entries (FFT index e <= win or e >= n - win),
+                         // stored compactly (e, then e - n + 2 win + 1); zero elsewhere
 };
 enum OutKind {
     OUT_CPLX_FULL = 0,   // n complex
     OUT_CPLX_HALF = 1,   // first n/2+1 complex
     OUT_CPLX_MODES = 2,  // N complex at centred mode positions
-    OUT_REAL_MODES = 3   // N reals (real part) times the deconvolution product, + energy
+    OUT_REAL_MODES = 3,  // N reals (real part) times the deconvolution product, + energy
+    OUT_CPLX_WIN = 4     // the 2 win + 1 window entries, compact (as IN_CPLX_WIN)
 };
 
 struct PassDesc {
@@ -54,6 +57,14 @@ struct PassDesc {
     const void *rho;     // energy: density (OUT_REAL_MODES)
     double2 *partials;   // energy: one compensated partial per CTA (OUT_REAL_MODES)
     int accum;           // OUT_REAL_MODES: add to the output instead of overwriting it
+    // frequency window (0 = none): only FFT indices e <= win or e >= n - win are nonzero or
+    // needed.  IN_CPLX_HERM reads zero outside it, OUT_CPLX_HALF writes e <= win only,
+    // OUT_CPLX_FULL writes the window entries only (at their full-line index).
+    int win;
+    // 3D row passes over a window (win_rows = 2 win + 1): row q is plane q / win_rows and
+    // window row q % win_rows, i.e. full-grid row c (c <= win) or n - (win_rows - c); the fold
+    // reads, and an OUT_CPLX_FULL pass writes, that full-grid row
+    int win_rows;
 };
 
 void make_radix(int n, PassDesc &p);

@@ -140,6 +140,11 @@ struct nlint_plan_s {
     // T1/U1/U3 passes; the node set is I_2's (radius P2, weights times p)
     int algorithm = 1;
     double pu_a = 0.0, pu_r0 = 0.0, pu_r1 = 0.0, rad2 = 0.0;  // rad2: I_2's radius P2
+    // I_2's frequency window: its nodes' stencils lie within |l_a| <= win fine cells, so its
+    // FFT passes transform only the window's lines (0 = the full passes P1..Q3)
+    int win = 0;
+    size_t bytes_Hwin = 0;  // the planes of the spread grid the window touches
+    nlint::PassDesc P1w, P2w, P3w, Q1w, Q2w, Q3w;
     // host copies for inspection (canonical order)
     std::vector<double> k_canon, W_canon;
     // stage timing
@@ -736,9 +741,75 @@ static int alg2_fill_multiplier(nlint_plan_s *p) {
     return NLINT_OK;
 }
 
+// I_2's windowed passes: the nodes of I_2 lie within |k| <= P2, so with t = k h their stencils
+// cover fine cells |l| <= P2 h n / (2 pi) + w/2 + 1 on every axis.  The forward passes compute
+// only those frequencies (the last one writes them at their place in the fine grid, where the
+// interpolation reads them), and the inverse passes transform only those lines of the spread
+// grid.  Needs the window well inside the half grid (no fold at the Nyquist planes).
+static void alg2_window(nlint_plan_s *p) {
+    const int d = p->d, n = p->n_fine;
+    const int64_t N = p->N;
+    const double g = p->rad2 * p->h * (double)n / (2.0 * M_PI);
+    const int win = (int)std::ceil(g) + p->w / 2 + 2;
+    if (win + p->pad + 1 >= n / 2 - p->pad || 2 * win + 1 > n) return;  // window too wide
+    const int wr = 2 * win + 1;
+    const size_t cs = p->prec == NLINT_FP32 ? 8 : 16;
+    auto base = [&](PassDesc &pd, int sign, int in_kind, int out_kind) {
+        std::memset(&pd, 0, sizeof(pd));
+        pd.n = n;
+        make_radix(n, pd);
+        pd.sign = sign;
+        pd.N = (int)N;
+        pd.dim = d;
+        pd.fac = p->d_fac;
+        pd.in_kind = in_kind;
+        pd.out_kind = out_kind;
+        pd.win = win;
+    };
+    if (d == 3) {
+        base(p->P1w, -1, IN_REAL_MODES, OUT_CPLX_HALF);
+        p->P1w.I = N * N; p->P1w.n_outer = 1; p->P1w.in_sa = N * N; p->P1w.out_sa = N * N;
+        base(p->P2w, -1, IN_CPLX_MODES, OUT_CPLX_WIN);
+        p->P2w.I = N; p->P2w.n_outer = win + 1; p->P2w.in_so = N * N; p->P2w.in_sa = N;
+        p->P2w.out_so = (int64_t)wr * N; p->P2w.out_sa = N;
+        base(p->P3w, -1, IN_CPLX_MODES, OUT_CPLX_FULL);
+        p->P3w.I = (int64_t)(win + 1) * wr; p->P3w.in_so = N; p->P3w.out_so = n; p->P3w.win_rows = wr;
+        base(p->Q1w, +1, IN_CPLX_FOLD, OUT_CPLX_MODES);
+        p->Q1w.I = (int64_t)(win + 1) * wr; p->Q1w.out_so = N; p->Q1w.fold_pad = p->pad;
+        p->Q1w.fold_plane = (int64_t)n * n; p->Q1w.fold_rows_per_plane = n; p->Q1w.win_rows = wr;
+        base(p->Q2w, +1, IN_CPLX_WIN, OUT_CPLX_MODES);
+        p->Q2w.I = N; p->Q2w.n_outer = win + 1; p->Q2w.in_so = (int64_t)wr * N; p->Q2w.in_sa = N;
+        p->Q2w.out_so = N * N; p->Q2w.out_sa = N;
+        base(p->Q3w, +1, IN_CPLX_HERM, OUT_REAL_MODES);
+        p->Q3w.I = N * N; p->Q3w.n_outer = 1; p->Q3w.in_sa = N * N; p->Q3w.out_sa = N * N;
+        config_pass(p->P2w, p->prec, false);
+        config_pass(p->P3w, p->prec, true);
+        config_pass(p->Q2w, p->prec, false);
+        p->bytes_Hwin = (size_t)(win + 2 * p->pad + 1) * n * n * cs;
+    } else {
+        base(p->P1w, -1, IN_REAL_MODES, OUT_CPLX_HALF);
+        p->P1w.I = N; p->P1w.n_outer = 1; p->P1w.in_sa = N; p->P1w.out_sa = N;
+        base(p->P3w, -1, IN_CPLX_MODES, OUT_CPLX_FULL);
+        p->P3w.I = win + 1; p->P3w.in_so = N; p->P3w.out_so = n;
+        base(p->Q1w, +1, IN_CPLX_FOLD, OUT_CPLX_MODES);
+        p->Q1w.I = win + 1; p->Q1w.out_so = N; p->Q1w.fold_pad = p->pad;
+        p->Q1w.fold_plane = n; p->Q1w.fold_rows_per_plane = 1;
+        base(p->Q3w, +1, IN_CPLX_HERM, OUT_REAL_MODES);
+        p->Q3w.I = N; p->Q3w.n_outer = 1; p->Q3w.in_sa = N; p->Q3w.out_sa = N;
+        config_pass(p->P3w, p->prec, true);
+        p->bytes_Hwin = (size_t)(win + 2 * p->pad + 1) * n * cs;
+    }
+    config_pass(p->P1w, p->prec, false);
+    config_pass(p->Q1w, p->prec, true);
+    config_pass(p->Q3w, p->prec, false);
+    if (pass_blocks(p->Q3w, false) > p->n_partials) return;  // (same grid as Q3: never)
+    p->win = win;
+}
+
 static int alg2_setup(nlint_plan_s *p) {
     int rc = upload_ones(p);
     if (rc) return rc;
+    alg2_window(p);
     p->ws_bytes += (size_t)std::max<int64_t>(p->N, p->n_fine) * (p->prec == NLINT_FP32 ? 4 : 8);
     rc = p->prec == NLINT_FP32 ? alg2_fill_multiplier<float>(p) : alg2_fill_multiplier<double>(p);
     if (rc) return rc;
@@ -913,13 +984,48 @@ static int run_alg2(nlint_plan_s *p, const void *rho, void *u, double lambda, do
     CK(launch_colpass<T>(p->U3, p->d_bufA, u, p->d_tw, s));
     p->launches += (p->d == 3) ? 6 : 4;
     stage_mark(p, s, "I1_fft_conv");
-    int rc = run_type2<T>(p, rho, s);
-    if (rc) return rc;
-    CK(launch_interp<T>(node_desc(p), p->d_bufG, p->d_c, 1, s));
-    p->launches += 1;
-    stage_mark(p, s, "interp");
-    rc = run_type1<T>(p, u, E ? rho : nullptr, s, true);
-    if (rc) return rc;
+    if (p->win > 0) {
+        // I_2 on its frequency window
+        CK(launch_colpass<T>(p->P1w, rho, p->d_bufA, p->d_tw, s));
+        if (p->d == 3) {
+            CK(launch_colpass<T>(p->P2w, p->d_bufA, p->d_bufB, p->d_tw, s));
+            CK(launch_rowpass<T>(p->P3w, p->d_bufB, p->d_bufG, p->d_tw, s));
+        } else {
+            CK(launch_rowpass<T>(p->P3w, p->d_bufA, p->d_bufG, p->d_tw, s));
+        }
+        stage_mark(p, s, "I2_fwd_fft");
+        CK(launch_interp<T>(node_desc(p), p->d_bufG, p->d_c, 1, s));
+        stage_mark(p, s, "interp");
+        CK(cudaMemsetAsync(p->d_bufG, 0, p->bytes_Hwin, s));
+        if (p->ncrowd) CK(cudaMemsetAsync(p->d_crowd, 0, p->bytes_crowd, s));
+        CK(launch_spread<T>(node_desc(p), p->d_c, p->d_bufG, s));
+        if (p->ncrowd) {
+            CK(launch_crowd_merge<T>(node_desc(p), p->d_bufG, s));
+            p->launches += 1;
+        }
+        stage_mark(p, s, "spread");
+        PassDesc q3 = p->Q3w;
+        q3.rho = E ? rho : nullptr;
+        q3.partials = E ? p->d_partials : nullptr;
+        q3.accum = 1;
+        if (p->d == 3) {
+            CK(launch_rowpass<T>(p->Q1w, p->d_bufG, p->d_bufB, p->d_tw, s));
+            CK(launch_colpass<T>(p->Q2w, p->d_bufB, p->d_bufA, p->d_tw, s));
+        } else {
+            CK(launch_rowpass<T>(p->Q1w, p->d_bufG, p->d_bufA, p->d_tw, s));
+        }
+        CK(launch_colpass<T>(q3, p->d_bufA, u, p->d_tw, s));
+        stage_mark(p, s, "I2_inv_fft");
+        p->launches += (p->d == 3) ? 8 : 6;
+    } else {
+        int rc = run_type2<T>(p, rho, s);
+        if (rc) return rc;
+        CK(launch_interp<T>(node_desc(p), p->d_bufG, p->d_c, 1, s));
+        p->launches += 1;
+        stage_mark(p, s, "interp");
+        rc = run_type1<T>(p, u, E ? rho : nullptr, s, true);
+        if (rc) return rc;
+    }
     if (E) {
         CK(launch_energy_final(p->d_partials, p->n_partials, 0.5 * lambda * std::pow(p->h, p->d), E, s));
         p->launches += 1;

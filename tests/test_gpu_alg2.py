@@ -37,6 +37,10 @@ CASES = [
     (3, 24, 10.0, "dipole", "fp64", {"axis": AX, "axis2": (0.3118, 0.9378, -0.1521)}),
     (2, 64, 16.0, "coulomb", "fp64", {}),
     (2, 100, 20.0, "dipole", "fp32", {"axis": (0.5246, -0.85135, 0.0), "alpha": 0.7}),
+    # grids wide enough for I_2's frequency window (windowed I_2 passes)
+    (3, 48, 16.0, "dipole", "fp32", {"axis": AX}),
+    (3, 64, 16.0, "coulomb", "fp64", {}),
+    (2, 128, 16.0, "coulomb", "fp64", {}),
 ]
 
 
