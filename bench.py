@@ -159,6 +159,58 @@ def stage_bytes(info: dict, stage: str) -> float:
     return float(table[stage])
 
 
+def run_alg2(pkg, torch, dev, wl, rho32, flush, stream, args, ms_step, ms64=None, u64=None):
+    """Algorithm 2 (eq. 3.9) on the benchmark workload in FP32 and FP64: time per evaluation
+    (L2 flushed), the FP32 result against the FP64 one (same operator), and the FP64 result
+    against the FP64 Algorithm 1 result in the interior |x| < 8 (both resolve it; Algorithm 1's
+    node set does not resolve the box corners to 1e-5)."""
+    res, us = {}, {}
+    for prec in ("fp32", "fp64"):
+        if prec == "fp64" and args.no_fp64:
+            continue
+        torch.cuda.nvtx.range_push(f"alg2_{prec}")  # ncu --nvtx-include selects a leg
+        p2 = pkg.Plan(wl.d, wl.n, wl.L, wl.kernel, precision=prec,
+                      eps=1e-6 if prec == "fp32" else 1e-12, algorithm=2, device=dev.index)
+        r = rho32 if prec == "fp32" else torch.from_numpy(wl.rho()).to(dev)
+        uu = torch.empty_like(r)
+        EE = torch.empty((), dtype=torch.float64, device=dev)
+        for _ in range(max(2, args.warmup)):
+            p2.eval_energy(r, lam=wl.lam, out=uu, E_out=EE)
+        k2 = args.steps if prec == "fp32" else max(2, min(args.steps, 5))
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * k2)]
+        for k in range(k2):
+            flush.fill_(float(k))
+            ev[2 * k].record(stream)
+            p2.eval_energy(r, lam=wl.lam, out=uu, E_out=EE)
+            ev[2 * k + 1].record(stream)
+        torch.cuda.synchronize()
+        ms = statistics.median(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(k2))
+        inf = p2.info
+        res[prec] = {"value": wl.n_points / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+                     "energy": float(EE.item()), "w": inf["w"], "I2_nodes": inf["n_nodes"],
+                     "a": inf["pu_a"], "P2": inf["P2"]}
+        us[prec] = uu.double()
+        p2.close()
+        torch.cuda.nvtx.range_pop()
+    out = {"workload": "same as the headline (3D Coulomb 256^3, 16-Gaussian mixture); "
+                       "I_1 by the 2x zero-padded FFT, I_2 by the NUFFT on 32x32x64 (FP32) / "
+                       "40x40x80 (FP64) nodes of radius P2 = 6.1 sqrt(a), a = (11.8/L)^2",
+           "fp32": res["fp32"], "fp64": res.get("fp64"),
+           "speedup_vs_algorithm1_fp32": ms_step / res["fp32"]["ms_per_step"]}
+    if "fp64" in res:
+        out["rel_linf_fp32_vs_fp64"] = float((us["fp32"] - us["fp64"]).abs().max() / us["fp64"].abs().max())
+        out["speedup_fp32_vs_fp64"] = res["fp64"]["ms_per_step"] / res["fp32"]["ms_per_step"]
+        if ms64:
+            out["speedup_vs_algorithm1_fp64"] = ms64 / res["fp64"]["ms_per_step"]
+        if u64 is not None:
+            z, y, x = synth.grid_coords(3, wl.n, wl.L)
+            inner = torch.from_numpy((x * x + y * y + z * z) < 64.0).to(dev)
+            d = (us["fp64"] - u64).abs()
+            out["rel_linf_vs_algorithm1_fp64_interior"] = float(d[inner].max() / u64.abs().max())
+            out["rel_linf_vs_algorithm1_fp64_whole_box"] = float(d.max() / u64.abs().max())
+    return out
+
+
 def path_bytes(info: dict) -> float:
     """Whole-path algorithmic bytes per evaluation: s (51.4 N^3 + 2 N_f) in 3D."""
     s = 4.0 if info["precision"] == 0 else 8.0
@@ -322,6 +374,7 @@ def run_ours(args, rank, world, local_rank):
     launches0 = plan.launch_count()
     barrier()
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("headline")
     with ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else
                       int(os.environ["CUDA_VISIBLE_DEVICES"].split(",")[local_rank])) as clk:
         t_wall0 = time.perf_counter()
@@ -335,6 +388,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         barrier()
         t_wall = time.perf_counter() - t_wall0
+    torch.cuda.nvtx.range_pop()
     launches = plan.launch_count() - launches0
     plan.set_stage_timing(False)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
@@ -414,7 +468,15 @@ def run_ours(args, rank, world, local_rank):
                 "rel_linf_fp32_vs_fp64": float((u32.double() - u64).abs().max() / u64.abs().max()),
                 "rel_energy_fp32_vs_fp64": abs(E32 - float(E64.item())) / abs(float(E64.item()))}
         plan64.close()
-        del rho64, u64
+        del rho64
+
+    # ---- Algorithm 2 (partition of unity, eq. 3.9) on the same workload
+    alg2 = None
+    if not args.no_alg2:
+        alg2 = run_alg2(pkg, torch, dev, wl, rho, flush, stream, args, ms_step=1e3 * t_max / args.steps,
+                        ms64=fp64["ms_per_step"] if fp64 else None, u64=u64 if fp64 else None)
+    if fp64:
+        del u64
 
     if rank != 0:
         return 0
@@ -459,6 +521,7 @@ def run_ours(args, rank, world, local_rank):
         "speedup_fp32_vs_fp64_gpu": (fp64["ms_per_step"] / ms_step) if fp64 else None,
         "batched": batched,
         "toeplitz_form": toep,
+        "algorithm2": alg2,
         "stages_ms": {k: round(v, 4) for k, v in mean_stage.items()},
         "path_bytes_per_step": path_bytes(info),
         "path_frac_of_hbm": path_gbs / peak,
@@ -483,6 +546,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-density batched form")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
     ap.add_argument("--no-toeplitz", action="store_true", help="skip the precomputed-kernel form")
+    ap.add_argument("--no-alg2", action="store_true", help="skip the Algorithm 2 leg")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
