@@ -71,8 +71,11 @@ __host__ __device__ constexpr int fft_row_b(int n, int cs, int mode = 1) {
 // Modes 3 and 4 are column passes that carry two real lines per complex FFT line: mode 3
 // transforms real input to the Hermitian half (z = x + i y, then X, Y from Z(k) and Z(n-k)),
 // mode 4 the Hermitian half back to real output (Z = X + i Y, then x = Re z, y = Im z).
-__host__ __device__ constexpr bool fft_is_row(int mode) { return mode == 1 || mode == 2; }
-__host__ __device__ constexpr int fft_pack(int mode) { return mode >= 3 ? 2 : 1; }
+// Mode 5 is a row pass that convolves each line: forward FFT, times a real row of `mult`,
+// inverse FFT (the multiply of an FFT convolution fused between two transforms of one axis).
+__host__ __device__ constexpr bool fft_is_row(int mode) { return mode == 1 || mode == 2 || mode == 5; }
+__host__ __device__ constexpr bool fft_packed(int mode) { return mode == 3 || mode == 4; }
+__host__ __device__ constexpr int fft_pack(int mode) { return fft_packed(mode) ? 2 : 1; }
 
 template <typename T, int NF, int MODE>
 struct FftCfg {
@@ -83,7 +86,8 @@ struct FftCfg {
     static constexpr int ROW_LD = fft_row_ld(NF);
     static constexpr int THREADS = B * TPL;
     // packed passes hold two lines' loads in flight: ask for two resident CTAs of 512 threads
-    static constexpr int MIN_BLOCKS = (MODE >= 3 && THREADS == 512 && NF <= 512 && sizeof(T) == 4) ? 2 : 0;
+    static constexpr int MIN_BLOCKS = (fft_packed(MODE) && THREADS == 512 && NF <= 512 && sizeof(T) == 4) ? 2
+                                      : (MODE == 5 && NF <= 512 && sizeof(T) == 4) ? 3 : 0;
 };
 
 // ------------------------------------------------------------------ butterflies
@@ -200,7 +204,7 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MO
     using T2 = cx_t<T>;
     using C = FftCfg<T, NF, MODE>;
     constexpr bool ROW = fft_is_row(MODE);
-    constexpr bool PACK = MODE >= 3;
+    constexpr bool PACK = fft_packed(MODE);
     constexpr int B = C::B;
     constexpr int TPL = C::TPL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -221,6 +225,7 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MO
     io.mult = reinterpret_cast<const T *>(P.mult);
     io.win = P.win;
     io.bfac = T(1);
+    int64_t mbase = 0;
     LineIO<T> io2;  // packed modes: the second data column of this FFT line (set field by field)
     io2.n = P.n;
     io2.h = h;
@@ -260,6 +265,7 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MO
         io.in_st = 1;
         io.out_st = 1;
         io.out_base = q * P.out_so;
+        mbase = q * P.n;  // mode 5: the line's multiplier row
         // windowed 3D row pass: compact row q -> plane, full-grid row
         int64_t wz = 0, wy = 0;
         if (P.win_rows > 0) {
@@ -285,8 +291,10 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MO
 
     auto sidx = [&](int e) -> int { return ROW ? ll * C::ROW_LD + e + (e >> 4) : e * B + ll; };
 
-    // ---- stage 0: global -> registers -> DFT -> shared
-    {
+    // ---- stage 0: global (or, for the inverse half of mode 5, shared) -> registers -> DFT
+    // -> shared
+    int sgn = MODE == 5 ? -1 : sign;  // mode 5: forward transform first
+    auto stage0 = [&](bool from_smem) {
         constexpr int R = fft_radix(NF, 0);
         constexpr int NB = NF / R;
         constexpr int MB = NB / TPL;
@@ -301,19 +309,23 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MO
                 } else if constexpr (MODE == 4) {  // Z = X + i Y from two Hermitian columns
                     const T2 X = io.load(e, vin), Y = io2.load(e, vin);
                     v[b][r] = cmake<T2>(X.x - Y.y, X.y + Y.x);
+                } else if constexpr (MODE == 5) {
+                    v[b][r] = from_smem ? buf[sidx(e)] : io.load(e, vin);
                 } else {
                     v[b][r] = io.load(e, vin);
                 }
             }
+        if (MODE == 5 && from_smem) __syncthreads();  // every input read before buf is rewritten
 #pragma unroll
         for (int b = 0; b < MB; b++) {
-            dft_small<T, R>(v[b], sign);
+            dft_small<T, R>(v[b], sgn);
             const int i = t + b * TPL;
 #pragma unroll
             for (int r = 0; r < R; r++) buf[sidx(i * R + r)] = v[b][r];
         }
-    }
-    __syncthreads();
+        __syncthreads();
+    };
+    stage0(false);
 
     // ---- stages 1 .. NST-1; the last one writes the output
     EAcc<T> eacc;  // this thread's u*rho products
@@ -330,7 +342,7 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MO
         for (int b = 0; b < MB; b++)
 #pragma unroll
             for (int r = 0; r < R; r++) v[b][r] = buf[sidx(t + b * TPL + r * NB)];
-        if constexpr (!LAST || PACK) __syncthreads();
+        if (!LAST || PACK || (MODE == 5 && sgn < 0)) __syncthreads();
 #pragma unroll
         for (int b = 0; b < MB; b++) {
             const int i = t + b * TPL;
@@ -338,10 +350,10 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MO
 #pragma unroll
             for (int r = 1; r < R; r++) {
                 T2 w = tw[r * k * STEP];
-                if (sign > 0) w = cconj(w);
+                if (sgn > 0) w = cconj(w);
                 v[b][r] = cmul(v[b][r], w);
             }
-            dft_small<T, R>(v[b], sign);
+            dft_small<T, R>(v[b], sgn);
             if constexpr (!LAST) {
                 const int j = (i - k) * R + k;
 #pragma unroll
@@ -349,6 +361,13 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MO
             } else if constexpr (PACK) {  // z in natural order for the epilogue below
 #pragma unroll
                 for (int r = 0; r < R; r++) buf[sidx(i + r * PP)] = v[b][r];
+            } else if (MODE == 5 && sgn < 0) {  // spectrum times the multiplier row, natural order
+                const T *mrow = reinterpret_cast<const T *>(P.mult) + mbase;
+#pragma unroll
+                for (int r = 0; r < R; r++) {
+                    const int e = i + r * PP;
+                    buf[sidx(e)] = cscale(v[b][r], io.valid ? mrow[e] : T(0));
+                }
             } else if (io.valid) {
                 // output entry e = i + r PP (here PP R = n and k = i)
 #pragma unroll
@@ -395,6 +414,12 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MO
         if constexpr (!LAST) __syncthreads();
     };
     static_for<1, C::NST>(stage);
+    if constexpr (MODE == 5) {  // the inverse transform of the multiplied line
+        __syncthreads();
+        sgn = +1;
+        stage0(true);
+        static_for<1, C::NST>(stage);
+    }
 
     if constexpr (MODE == 4) {  // x = Re z, y = Im z at the stored modes (+ energy)
         __syncthreads();

@@ -15,6 +15,8 @@ extern template cudaError_t launch_pass_mode<float, 3>(const PassDesc &, const v
 extern template cudaError_t launch_pass_mode<float, 4>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
 extern template cudaError_t launch_pass_mode<double, 3>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
 extern template cudaError_t launch_pass_mode<double, 4>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
+extern template cudaError_t launch_pass_mode<float, 5>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
+extern template cudaError_t launch_pass_mode<double, 5>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
 
 int pass_mode(const PassDesc &p, bool row) {
     if (!row) {
@@ -22,6 +24,7 @@ int pass_mode(const PassDesc &p, bool row) {
         if (p.in_kind == IN_CPLX_HERM && p.out_kind == OUT_REAL_MODES) return 4;
         return 0;
     }
+    if (p.conv) return 5;
     return (p.in_kind == IN_CPLX_FOLD || p.in_kind == IN_CPLX_MULT) ? 2 : 1;
 }
 
@@ -91,8 +94,11 @@ cudaError_t launch_colpass(const PassDesc &p, const void *in, void *out, const v
 
 template <typename T>
 cudaError_t launch_rowpass(const PassDesc &p, const void *in, void *out, const void *tw, cudaStream_t s) {
-    return pass_mode(p, true) == 2 ? launch_pass_mode<T, 2>(p, in, out, tw, s)
-                                   : launch_pass_mode<T, 1>(p, in, out, tw, s);
+    switch (pass_mode(p, true)) {
+        case 2: return launch_pass_mode<T, 2>(p, in, out, tw, s);
+        case 5: return launch_pass_mode<T, 5>(p, in, out, tw, s);
+        default: return launch_pass_mode<T, 1>(p, in, out, tw, s);
+    }
 }
 
 template cudaError_t launch_colpass<float>(const PassDesc &, const void *, void *, const void *, cudaStream_t);

@@ -65,6 +65,9 @@ struct PassDesc {
     // window row q % win_rows, i.e. full-grid row c (c <= win) or n - (win_rows - c); the fold
     // reads, and an OUT_CPLX_FULL pass writes, that full-grid row
     int win_rows;
+    // row pass that convolves each line (mode 5): forward FFT of the N input modes, times the
+    // real n-entry row `mult` + q n, inverse FFT, N output modes
+    int conv;
 };
 
 void make_radix(int n, PassDesc &p);
@@ -77,7 +80,8 @@ void config_pass(PassDesc &p, int prec, bool row);
 bool pass_fits(const PassDesc &p);
 
 // pass mode 0: column pass; 1: row pass; 2: row pass reading fold / multiply input;
-// 3: column pass real -> Hermitian half, two lines per FFT; 4: Hermitian half -> real, two lines
+// 3: column pass real -> Hermitian half, two lines per FFT; 4: Hermitian half -> real, two lines;
+// 5: row pass forward FFT, multiply, inverse FFT
 int pass_mode(const PassDesc &p, bool row);
 template <typename T, int MODE>
 cudaError_t launch_pass_mode(const PassDesc &p, const void *in, void *out, const void *tw,

@@ -136,6 +136,7 @@ struct nlint_plan_s {
     void *d_fac1 = nullptr, *d_khat = nullptr;
     bool toeplitz = false;
     nlint::PassDesc T1, U1, U3;
+    nlint::PassDesc X;  // P3 and U1 fused: forward FFT along x, multiply, inverse FFT
     // Algorithm 2 (eq. 3.9): I_1's multiplier U_hat (1 - p) lives in d_khat and uses the
     // T1/U1/U3 passes; the node set is I_2's (radius P2, weights times p)
     int algorithm = 1;
@@ -701,6 +702,20 @@ static void conv_passes(nlint_plan_s *p) {
     p->U1.out_so = N;
     p->U1.mult = p->d_khat;
     config_pass(p->U1, p->prec, true);
+    std::memset(&p->X, 0, sizeof(p->X));
+    p->X.n = n;
+    make_radix(n, p->X);
+    p->X.sign = -1;
+    p->X.N = (int)N;
+    p->X.dim = d;
+    p->X.in_kind = IN_CPLX_MODES;
+    p->X.out_kind = OUT_CPLX_MODES;
+    p->X.I = (d == 3) ? nh * n : nh;
+    p->X.in_so = N;
+    p->X.out_so = N;
+    p->X.mult = p->d_khat;
+    p->X.conv = 1;
+    config_pass(p->X, p->prec, true);
 }
 
 // Algorithm 2: I_1's multiplier M(k) / n_fine^d on the real half grid of the fine grid's DFT
@@ -937,23 +952,22 @@ static int run_toeplitz(nlint_plan_s *p, const void *rho, void *u, double lambda
     CK(launch_colpass<T>(p->T1, rho, p->d_bufA, p->d_tw, s));
     if (p->d == 3) {
         CK(launch_colpass<T>(p->P2, p->d_bufA, p->d_bufB, p->d_tw, s));
-        CK(launch_rowpass<T>(p->P3, p->d_bufB, p->d_bufG, p->d_tw, s));
+        CK(launch_rowpass<T>(p->X, p->d_bufB, p->d_bufG, p->d_tw, s));  // x: FFT, K_hat, IFFT
     } else {
-        CK(launch_rowpass<T>(p->P3, p->d_bufA, p->d_bufG, p->d_tw, s));
+        CK(launch_rowpass<T>(p->X, p->d_bufA, p->d_bufG, p->d_tw, s));
     }
-    stage_mark(p, s, "fwd_fft");
+    stage_mark(p, s, "fwd_fft_conv_x");
     PassDesc u3 = p->U3;
     u3.rho = E ? rho : nullptr;
     u3.partials = E ? p->d_partials : nullptr;
     if (p->d == 3) {
-        CK(launch_rowpass<T>(p->U1, p->d_bufG, p->d_bufB, p->d_tw, s));
-        CK(launch_colpass<T>(p->Q2, p->d_bufB, p->d_bufA, p->d_tw, s));
+        CK(launch_colpass<T>(p->Q2, p->d_bufG, p->d_bufA, p->d_tw, s));
+        CK(launch_colpass<T>(u3, p->d_bufA, u, p->d_tw, s));
     } else {
-        CK(launch_rowpass<T>(p->U1, p->d_bufG, p->d_bufA, p->d_tw, s));
+        CK(launch_colpass<T>(u3, p->d_bufG, u, p->d_tw, s));
     }
-    CK(launch_colpass<T>(u3, p->d_bufA, u, p->d_tw, s));
-    stage_mark(p, s, "multiply_inv_fft");
-    p->launches += (p->d == 3) ? 6 : 4;
+    stage_mark(p, s, "inv_fft");
+    p->launches += (p->d == 3) ? 5 : 3;
     if (E) {
         CK(launch_energy_final(p->d_partials, p->n_partials, 0.5 * lambda * std::pow(p->h, p->d), E, s));
         p->launches += 1;
@@ -974,15 +988,14 @@ static int run_alg2(nlint_plan_s *p, const void *rho, void *u, double lambda, do
     CK(launch_colpass<T>(p->T1, rho, p->d_bufA, p->d_tw, s));
     if (p->d == 3) {
         CK(launch_colpass<T>(p->P2, p->d_bufA, p->d_bufB, p->d_tw, s));
-        CK(launch_rowpass<T>(p->P3, p->d_bufB, p->d_bufG, p->d_tw, s));
-        CK(launch_rowpass<T>(p->U1, p->d_bufG, p->d_bufB, p->d_tw, s));
-        CK(launch_colpass<T>(p->Q2, p->d_bufB, p->d_bufA, p->d_tw, s));
+        CK(launch_rowpass<T>(p->X, p->d_bufB, p->d_bufG, p->d_tw, s));  // x: FFT, M, IFFT
+        CK(launch_colpass<T>(p->Q2, p->d_bufG, p->d_bufA, p->d_tw, s));
+        CK(launch_colpass<T>(p->U3, p->d_bufA, u, p->d_tw, s));
     } else {
-        CK(launch_rowpass<T>(p->P3, p->d_bufA, p->d_bufG, p->d_tw, s));
-        CK(launch_rowpass<T>(p->U1, p->d_bufG, p->d_bufA, p->d_tw, s));
+        CK(launch_rowpass<T>(p->X, p->d_bufA, p->d_bufG, p->d_tw, s));
+        CK(launch_colpass<T>(p->U3, p->d_bufG, u, p->d_tw, s));
     }
-    CK(launch_colpass<T>(p->U3, p->d_bufA, u, p->d_tw, s));
-    p->launches += (p->d == 3) ? 6 : 4;
+    p->launches += (p->d == 3) ? 5 : 3;
     stage_mark(p, s, "I1_fft_conv");
     if (p->win > 0) {
         // I_2 on its frequency window
