@@ -38,7 +38,7 @@ __host__ __device__ constexpr int fft_pprod(int n, int s) {  // product of the r
     return s == 0 ? 1 : fft_pprod(n, s - 1) * fft_radix(n, s - 1);
 }
 // Pass modes: 0 column pass; 1 row pass; 2 row pass that reads more than it writes (the fold
-// and multiply inputs of the first inverse pass), which wants more threads per line.
+// input of the first inverse pass), which wants more threads per line.
 __host__ __device__ constexpr int fft_vpt(int n, int mode = 0) {
     return fft_has3(n) ? 24 : (n <= 512 ? (mode == 2 ? 8 : 16) : 32);
 }
@@ -76,6 +76,23 @@ __host__ __device__ constexpr int fft_row_b(int n, int cs, int mode = 1) {
 __host__ __device__ constexpr bool fft_is_row(int mode) { return mode == 1 || mode == 2 || mode == 5; }
 __host__ __device__ constexpr bool fft_packed(int mode) { return mode == 3 || mode == 4; }
 __host__ __device__ constexpr int fft_pack(int mode) { return fft_packed(mode) ? 2 : 1; }
+
+// Input and output kinds each mode is launched with (compile-time, so a single-kind mode has no
+// branch on the kind; the launcher rejects anything else).
+__host__ __device__ constexpr unsigned fft_in_mask(int mode) {
+    return mode == 0 ? (1u << IN_CPLX_MODES) | (1u << IN_CPLX_FULL) | (1u << IN_CPLX_WIN)
+         : mode == 2 ? (1u << IN_CPLX_FOLD)
+         : mode == 3 ? (1u << IN_REAL_MODES)
+         : mode == 4 ? (1u << IN_CPLX_HERM)
+                     : (1u << IN_CPLX_MODES);  // 1, 5
+}
+__host__ __device__ constexpr unsigned fft_out_mask(int mode) {
+    return mode == 0 ? (1u << OUT_CPLX_FULL) | (1u << OUT_CPLX_MODES) | (1u << OUT_CPLX_WIN)
+         : mode == 1 ? (1u << OUT_CPLX_FULL)
+         : mode == 3 ? (1u << OUT_CPLX_HALF)
+         : mode == 4 ? (1u << OUT_REAL_MODES)
+                     : (1u << OUT_CPLX_MODES);  // 2, 5
+}
 
 template <typename T, int NF, int MODE>
 struct FftCfg {
@@ -147,48 +164,39 @@ struct LineIO {
     int64_t in_st, out_st;      // element stride along the line
     T bfac;                     // deconvolution product over the other axes
     int64_t mirror_base;        // fold: the mirrored line of H+, or -1
-    const T *mult;              // IN_CPLX_MULT: multiplier row (same layout as the input)
     int win;                    // frequency window (0 = none), see PassDesc
 
-    // FFT-index entry e of the input line (zero outside the stored modes)
+    // FFT-index entry e of the input line (zero outside the stored modes); KM: the kinds the
+    // calling pass can have (one kind: no test of `kind` at all)
+    template <unsigned KM>
     __device__ __forceinline__ T2 load(int e, const void *vin) const {
+        constexpr bool ONE = (KM & (KM - 1)) == 0;
+        auto is = [&](int k) { return (KM & (1u << k)) != 0 && (ONE || kind == k); };
         T2 v = czero<T2>();
         if (!valid) return v;
-        switch (kind) {
-            case IN_REAL_MODES:
-            case IN_CPLX_MODES: {
-                const int m = e < n / 2 ? e : e - n;
-                if (m >= -h && m < h) {
-                    const int a = m + h;
-                    if (kind == IN_REAL_MODES) {
-                        v.x = reinterpret_cast<const T *>(vin)[in_base + a * in_st] * fac[a] * bfac;
-                    } else {
-                        v = reinterpret_cast<const T2 *>(vin)[in_base + a * in_st];
-                    }
+        if (is(IN_REAL_MODES) || is(IN_CPLX_MODES)) {
+            const int m = e < n / 2 ? e : e - n;
+            if (m >= -h && m < h) {
+                const int a = m + h;
+                if (is(IN_REAL_MODES)) {
+                    v.x = reinterpret_cast<const T *>(vin)[in_base + a * in_st] * fac[a] * bfac;
+                } else {
+                    v = reinterpret_cast<const T2 *>(vin)[in_base + a * in_st];
                 }
-                break;
             }
-            case IN_CPLX_FULL:
-                v = reinterpret_cast<const T2 *>(vin)[in_base + e * in_st];
-                break;
-            case IN_CPLX_HERM:
-                if (win > 0 && (e <= n / 2 ? e : n - e) > win) break;  // outside the window
-                v = (e <= n / 2) ? reinterpret_cast<const T2 *>(vin)[in_base + e * in_st]
-                                 : cconj(reinterpret_cast<const T2 *>(vin)[in_base + (n - e) * in_st]);
-                break;
-            case IN_CPLX_WIN: {
-                const int c = e <= win ? e : (e >= n - win ? e - n + 2 * win + 1 : -1);
-                if (c >= 0) v = reinterpret_cast<const T2 *>(vin)[in_base + c * in_st];
-                break;
-            }
-            case IN_CPLX_MULT:
-                v = cscale(reinterpret_cast<const T2 *>(vin)[in_base + e], mult[in_base + e]);
-                break;
-            default: {  // IN_CPLX_FOLD: H[l] = H+[l] + conj(H+[-l])
-                const T2 *in = reinterpret_cast<const T2 *>(vin);
-                v = in[in_base + e];
-                if (mirror_base >= 0) v = cadd(v, cconj(in[mirror_base + (e == 0 ? 0 : n - e)]));
-            }
+        } else if (is(IN_CPLX_FULL)) {
+            v = reinterpret_cast<const T2 *>(vin)[in_base + e * in_st];
+        } else if (is(IN_CPLX_HERM)) {
+            if (win > 0 && (e <= n / 2 ? e : n - e) > win) return v;  // outside the window
+            v = (e <= n / 2) ? reinterpret_cast<const T2 *>(vin)[in_base + e * in_st]
+                             : cconj(reinterpret_cast<const T2 *>(vin)[in_base + (n - e) * in_st]);
+        } else if (is(IN_CPLX_WIN)) {
+            const int c = e <= win ? e : (e >= n - win ? e - n + 2 * win + 1 : -1);
+            if (c >= 0) v = reinterpret_cast<const T2 *>(vin)[in_base + c * in_st];
+        } else if (is(IN_CPLX_FOLD)) {  // H[l] = H+[l] + conj(H+[-l])
+            const T2 *in = reinterpret_cast<const T2 *>(vin);
+            v = in[in_base + e];
+            if (mirror_base >= 0) v = cadd(v, cconj(in[mirror_base + (e == 0 ? 0 : n - e)]));
         }
         return v;
     }
@@ -222,7 +230,6 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MO
     io.kind = P.in_kind;
     io.fac = reinterpret_cast<const T *>(P.fac);
     io.mirror_base = -1;
-    io.mult = reinterpret_cast<const T *>(P.mult);
     io.win = P.win;
     io.bfac = T(1);
     int64_t mbase = 0;
@@ -232,7 +239,6 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MO
     io2.kind = P.in_kind;
     io2.fac = io.fac;
     io2.mirror_base = -1;
-    io2.mult = io.mult;
     io2.win = P.win;
     io2.bfac = T(1);
     io2.valid = false;
@@ -291,10 +297,10 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MO
 
     auto sidx = [&](int e) -> int { return ROW ? ll * C::ROW_LD + e + (e >> 4) : e * B + ll; };
 
-    // ---- stage 0: global (or, for the inverse half of mode 5, shared) -> registers -> DFT
-    // -> shared
+    constexpr unsigned KM = fft_in_mask(MODE), OM = fft_out_mask(MODE);
+    // ---- stage 0: global -> registers -> DFT -> shared
     int sgn = MODE == 5 ? -1 : sign;  // mode 5: forward transform first
-    auto stage0 = [&](bool from_smem) {
+    {
         constexpr int R = fft_radix(NF, 0);
         constexpr int NB = NF / R;
         constexpr int MB = NB / TPL;
@@ -305,17 +311,33 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MO
             for (int r = 0; r < R; r++) {
                 const int e = t + b * TPL + r * NB;
                 if constexpr (MODE == 3) {  // z = x + i y from two real columns
-                    v[b][r] = cmake<T2>(io.load(e, vin).x, io2.load(e, vin).x);
+                    v[b][r] = cmake<T2>(io.template load<KM>(e, vin).x, io2.template load<KM>(e, vin).x);
                 } else if constexpr (MODE == 4) {  // Z = X + i Y from two Hermitian columns
-                    const T2 X = io.load(e, vin), Y = io2.load(e, vin);
+                    const T2 X = io.template load<KM>(e, vin), Y = io2.template load<KM>(e, vin);
                     v[b][r] = cmake<T2>(X.x - Y.y, X.y + Y.x);
-                } else if constexpr (MODE == 5) {
-                    v[b][r] = from_smem ? buf[sidx(e)] : io.load(e, vin);
+                } else if constexpr (MODE == 2) {  // fold: the row here, the mirror row below
+                    v[b][r] = io.valid ? reinterpret_cast<const T2 *>(vin)[io.in_base + e] : czero<T2>();
                 } else {
-                    v[b][r] = io.load(e, vin);
+                    v[b][r] = io.template load<KM>(e, vin);
                 }
             }
-        if (MODE == 5 && from_smem) __syncthreads();  // every input read before buf is rewritten
+        if constexpr (MODE == 2) {  // H[l] = H+[l] + conj(H+[-l]): all mirror loads in one batch
+            if (io.valid && io.mirror_base >= 0) {
+                const T2 *in = reinterpret_cast<const T2 *>(vin);
+                T2 m[MB][R];
+#pragma unroll
+                for (int b = 0; b < MB; b++)
+#pragma unroll
+                    for (int r = 0; r < R; r++) {
+                        const int e = t + b * TPL + r * NB;
+                        m[b][r] = in[io.mirror_base + (e == 0 ? 0 : NF - e)];
+                    }
+#pragma unroll
+                for (int b = 0; b < MB; b++)
+#pragma unroll
+                    for (int r = 0; r < R; r++) v[b][r] = cadd(v[b][r], cconj(m[b][r]));
+            }
+        }
 #pragma unroll
         for (int b = 0; b < MB; b++) {
             dft_small<T, R>(v[b], sgn);
@@ -323,9 +345,8 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MO
 #pragma unroll
             for (int r = 0; r < R; r++) buf[sidx(i * R + r)] = v[b][r];
         }
-        __syncthreads();
-    };
-    stage0(false);
+    }
+    __syncthreads();
 
     // ---- stages 1 .. NST-1; the last one writes the output
     EAcc<T> eacc;  // this thread's u*rho products
@@ -374,38 +395,31 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MO
                 for (int r = 0; r < R; r++) {
                     const int e = i + r * PP;
                     const T2 x = v[b][r];
-                    switch (P.out_kind) {
-                        case OUT_CPLX_FULL:
-                            if (P.win == 0 || e <= P.win || e >= NF - P.win)
-                                reinterpret_cast<T2 *>(vout)[io.out_base + e * io.out_st] = x;
-                            break;
-                        case OUT_CPLX_HALF:
-                            if (e <= (P.win > 0 ? P.win : NF / 2))
-                                reinterpret_cast<T2 *>(vout)[io.out_base + e * io.out_st] = x;
-                            break;
-                        case OUT_CPLX_WIN: {
-                            const int c = e <= P.win ? e : (e >= NF - P.win ? e - NF + 2 * P.win + 1 : -1);
-                            if (c >= 0) reinterpret_cast<T2 *>(vout)[io.out_base + c * io.out_st] = x;
-                            break;
-                        }
-                        case OUT_CPLX_MODES: {
-                            const int m = e < NF / 2 ? e : e - NF;
-                            if (m >= -h && m < h)
-                                reinterpret_cast<T2 *>(vout)[io.out_base + (m + h) * io.out_st] = x;
-                            break;
-                        }
-                        default: {  // OUT_REAL_MODES (+ energy)
-                            const int m = e < NF / 2 ? e : e - NF;
-                            if (m >= -h && m < h) {
-                                const int a = m + h;
-                                const T *fac = reinterpret_cast<const T *>(P.fac);
-                                const int64_t idx = io.out_base + a * io.out_st;
-                                T val = x.x * fac[a] * io.bfac;
-                                if (P.accum) val += reinterpret_cast<const T *>(vout)[idx];
-                                reinterpret_cast<T *>(vout)[idx] = val;
-                                if (P.rho)
-                                    eacc.add(val, reinterpret_cast<const T *>(P.rho)[idx]);
-                            }
+                    constexpr bool OONE = (OM & (OM - 1)) == 0;
+                    auto os = [&](int k) { return (OM & (1u << k)) != 0 && (OONE || P.out_kind == k); };
+                    if (os(OUT_CPLX_FULL)) {
+                        if (P.win == 0 || e <= P.win || e >= NF - P.win)
+                            reinterpret_cast<T2 *>(vout)[io.out_base + e * io.out_st] = x;
+                    } else if (os(OUT_CPLX_HALF)) {
+                        if (e <= (P.win > 0 ? P.win : NF / 2))
+                            reinterpret_cast<T2 *>(vout)[io.out_base + e * io.out_st] = x;
+                    } else if (os(OUT_CPLX_WIN)) {
+                        const int c = e <= P.win ? e : (e >= NF - P.win ? e - NF + 2 * P.win + 1 : -1);
+                        if (c >= 0) reinterpret_cast<T2 *>(vout)[io.out_base + c * io.out_st] = x;
+                    } else if (os(OUT_CPLX_MODES)) {
+                        const int m = e < NF / 2 ? e : e - NF;
+                        if (m >= -h && m < h)
+                            reinterpret_cast<T2 *>(vout)[io.out_base + (m + h) * io.out_st] = x;
+                    } else if (os(OUT_REAL_MODES)) {  // (+ energy)
+                        const int m = e < NF / 2 ? e : e - NF;
+                        if (m >= -h && m < h) {
+                            const int a = m + h;
+                            const T *fac = reinterpret_cast<const T *>(P.fac);
+                            const int64_t idx = io.out_base + a * io.out_st;
+                            T val = x.x * fac[a] * io.bfac;
+                            if (P.accum) val += reinterpret_cast<const T *>(vout)[idx];
+                            reinterpret_cast<T *>(vout)[idx] = val;
+                            if (P.rho) eacc.add(val, reinterpret_cast<const T *>(P.rho)[idx]);
                         }
                     }
                 }
@@ -414,10 +428,26 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MO
         if constexpr (!LAST) __syncthreads();
     };
     static_for<1, C::NST>(stage);
-    if constexpr (MODE == 5) {  // the inverse transform of the multiplied line
+    if constexpr (MODE == 5) {  // the inverse transform of the multiplied line (natural order)
         __syncthreads();
         sgn = +1;
-        stage0(true);
+        constexpr int R = fft_radix(NF, 0);
+        constexpr int NB = NF / R;
+        constexpr int MB = NB / TPL;
+        T2 v[MB][R];
+#pragma unroll
+        for (int b = 0; b < MB; b++)
+#pragma unroll
+            for (int r = 0; r < R; r++) v[b][r] = buf[sidx(t + b * TPL + r * NB)];
+        __syncthreads();  // every input read before buf is rewritten
+#pragma unroll
+        for (int b = 0; b < MB; b++) {
+            dft_small<T, R>(v[b], sgn);
+            const int i = t + b * TPL;
+#pragma unroll
+            for (int r = 0; r < R; r++) buf[sidx(i * R + r)] = v[b][r];
+        }
+        __syncthreads();
         static_for<1, C::NST>(stage);
     }
 
@@ -470,6 +500,8 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MO
 // ------------------------------------------------------------------ launchers
 template <typename T, int NF, int MODE>
 cudaError_t launch_nf(const PassDesc &p, const void *in, void *out, const void *tw, cudaStream_t s) {
+    if (!(fft_in_mask(MODE) & (1u << p.in_kind)) || !(fft_out_mask(MODE) & (1u << p.out_kind)))
+        return cudaErrorInvalidValue;  // a pass descriptor this mode was not compiled for
     const size_t smem = pass_smem(p, sizeof(T) == 4 ? NLINT_FP32 : NLINT_FP64);
     cudaError_t e = cudaFuncSetAttribute(fft_pass_kernel<T, NF, MODE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -25,7 +25,7 @@ int pass_mode(const PassDesc &p, bool row) {
         return 0;
     }
     if (p.conv) return 5;
-    return (p.in_kind == IN_CPLX_FOLD || p.in_kind == IN_CPLX_MULT) ? 2 : 1;
+    return p.in_kind == IN_CPLX_FOLD ? 2 : 1;
 }
 
 bool fft_size_supported(int n) {

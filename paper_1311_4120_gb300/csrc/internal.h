@@ -23,7 +23,6 @@ enum InKind {
     IN_CPLX_FULL = 2,    // n complex
     IN_CPLX_HERM = 3,    // n/2+1 complex of a Hermitian line (rest by conjugate symmetry)
     IN_CPLX_FOLD = 4,    // row pass only: n complex plus the conjugated mirror row (fold)
-    IN_CPLX_MULT = 5,    // row pass only: n complex times a real n-entry row of `mult`
     IN_CPLX_WIN = 6      // the 2 win + 1 window entries (FFT index e <= win or e >= n - win),
                          // stored compactly (e, then e - n + 2 win + 1); zero elsewhere
 };
@@ -53,7 +52,7 @@ struct PassDesc {
     int64_t fold_plane;  // elements per plane of the slowest axis (rows per plane * n)
     int64_t fold_rows_per_plane;
     const void *fac;     // deconvolution factors, length N (plan precision)
-    const void *mult;    // IN_CPLX_MULT: real multiplier, same row layout as the input
+    const void *mult;    // conv (mode 5): real multiplier, one n-entry row per line
     const void *rho;     // energy: density (OUT_REAL_MODES)
     double2 *partials;   // energy: one compensated partial per CTA (OUT_REAL_MODES)
     int accum;           // OUT_REAL_MODES: add to the output instead of overwriting it
@@ -79,7 +78,7 @@ size_t pass_smem(const PassDesc &p, int prec);
 void config_pass(PassDesc &p, int prec, bool row);
 bool pass_fits(const PassDesc &p);
 
-// pass mode 0: column pass; 1: row pass; 2: row pass reading fold / multiply input;
+// pass mode 0: column pass; 1: row pass; 2: row pass reading the fold input;
 // 3: column pass real -> Hermitian half, two lines per FFT; 4: Hermitian half -> real, two lines;
 // 5: row pass forward FFT, multiply, inverse FFT
 int pass_mode(const PassDesc &p, bool row);
@@ -171,8 +170,11 @@ cudaError_t launch_gather_canonical(int64_t M, const void *c_canon, const int32_
 template <typename T>
 cudaError_t launch_energy_partials(int64_t count, const void *u, const void *rho,
                                    double2 *partials, int nblocks, cudaStream_t s);
+// E = scale * (compensated sum of the nparts partials), in a fixed order.  The buffer must hold
+// nparts + 64 entries: the last 64 are scratch for the two-stage fold.
 cudaError_t launch_energy_final(const double2 *partials, int nparts, double scale, double *E,
                                 cudaStream_t s);
+int energy_final_kernels(int nparts);  // kernels launch_energy_final launches (1 or 2)
 // Toeplitz kernel assembly: an N^d block into an n^d array at cell offsets off = (slowest,
 // middle, fastest array axis; 2D: slowest, -, fastest)
 template <typename T>

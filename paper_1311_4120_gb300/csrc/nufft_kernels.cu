@@ -57,6 +57,20 @@ __global__ void __launch_bounds__(256) energy_partials_kernel(int64_t count, con
 // One CTA of 1024 threads folds the partials: thread t takes partials t, t+1024, ... in
 // order, then a fixed shuffle tree combines the threads.  The result does not depend on
 // timing, so repeated evaluations give identical energies.
+// Energy fold in two stages, so the FP64 compensated arithmetic (a small fraction of the FP32
+// rate on this GPU) is spread over many SMs: warp b folds partials [b per, (b + 1) per) into
+// out[b], then one CTA folds those.  The order is fixed by the indices (deterministic).
+__global__ void __launch_bounds__(32) energy_fold_kernel(const double2 *__restrict__ partials,
+                                                         int nparts, int per,
+                                                         double2 *__restrict__ out) {
+    KSum acc;
+    acc.init();
+    const int a = blockIdx.x * per, e = min(a + per, nparts);
+    for (int q = a + (int)threadIdx.x; q < e; q += 32) acc.merge(partials[q].x, partials[q].y);
+    ksum_warp(acc);
+    if (threadIdx.x == 0) out[blockIdx.x] = make_double2(acc.s, acc.c);
+}
+
 __global__ void __launch_bounds__(1024) energy_final_kernel(const double2 *__restrict__ partials,
                                                             int nparts, double scale,
                                                             double *__restrict__ E) {
@@ -157,9 +171,21 @@ cudaError_t launch_energy_partials(int64_t count, const void *u, const void *rho
     return cudaGetLastError();
 }
 
+static constexpr int FOLD_DIRECT = 128, FOLD_WARPS = 64;
+
+int energy_final_kernels(int nparts) { return nparts <= FOLD_DIRECT ? 1 : 2; }
+
 cudaError_t launch_energy_final(const double2 *partials, int nparts, double scale, double *E,
                                 cudaStream_t s) {
-    energy_final_kernel<<<1, 1024, 0, s>>>(partials, nparts, scale, E);
+    if (nparts <= FOLD_DIRECT) {
+        energy_final_kernel<<<1, FOLD_DIRECT, 0, s>>>(partials, nparts, scale, E);
+        return cudaGetLastError();
+    }
+    const int per = (nparts + FOLD_WARPS - 1) / FOLD_WARPS;
+    const int g = (nparts + per - 1) / per;  // <= FOLD_WARPS
+    double2 *mid = const_cast<double2 *>(partials) + nparts;
+    energy_fold_kernel<<<g, 32, 0, s>>>(partials, nparts, per, mid);
+    energy_final_kernel<<<1, FOLD_WARPS, 0, s>>>(mid, g, scale, E);
     return cudaGetLastError();
 }
 

@@ -135,10 +135,10 @@ struct nlint_plan_s {
     // precomputed Toeplitz kernel (nlint_plan_toeplitz): K_hat on the Hermitian half grid
     void *d_fac1 = nullptr, *d_khat = nullptr;
     bool toeplitz = false;
-    nlint::PassDesc T1, U1, U3;
-    nlint::PassDesc X;  // P3 and U1 fused: forward FFT along x, multiply, inverse FFT
+    nlint::PassDesc T1, U3;
+    nlint::PassDesc X;  // forward FFT along x, multiply by K_hat, inverse FFT (one row pass)
     // Algorithm 2 (eq. 3.9): I_1's multiplier U_hat (1 - p) lives in d_khat and uses the
-    // T1/U1/U3 passes; the node set is I_2's (radius P2, weights times p)
+    // T1/X/U3 passes; the node set is I_2's (radius P2, weights times p)
     int algorithm = 1;
     double pu_a = 0.0, pu_r0 = 0.0, pu_r1 = 0.0, rad2 = 0.0;  // rad2: I_2's radius P2
     // I_2's frequency window: its nodes' stencils lie within |l_a| <= win fine cells, so its
@@ -660,8 +660,9 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
     if (p->bytes_B) CK(cudaMalloc(&p->d_bufB, p->bytes_B));
     CK(cudaMalloc(&p->d_bufG, std::max(p->bytes_G, p->bytes_Hext)));
     CK(cudaMalloc(&p->d_c, p->bytes_c + cs));
-    CK(cudaMalloc((void **)&p->d_partials, sizeof(double2) * (size_t)std::max(p->n_partials, 1024)));
-    CK(cudaMalloc((void **)&p->d_epart, sizeof(double2) * (size_t)std::max<int64_t>(p->nsub, 1)));
+    // + 64: scratch of the two-stage energy fold (launch_energy_final)
+    CK(cudaMalloc((void **)&p->d_partials, sizeof(double2) * ((size_t)std::max(p->n_partials, 1024) + 64)));
+    CK(cudaMalloc((void **)&p->d_epart, sizeof(double2) * ((size_t)std::max<int64_t>(p->nsub, 1) + 64)));
     acc += sizeof(double2) * (size_t)p->nsub;
     CK(cudaMalloc((void **)&p->d_E, sizeof(double)));
     acc += p->bytes_A + p->bytes_B + std::max(p->bytes_G, p->bytes_Hext) + p->bytes_c +
@@ -681,7 +682,9 @@ static int upload_ones(nlint_plan_s *p) {
 }
 
 // Passes of u = crop(IFFT(K_hat FFT(rho_pad))) on the fine grid: the NUFFT passes with unit
-// factors, and the multiply by the real half grid d_khat fused into the first inverse pass.
+// factors along z and y, and one row pass along x that transforms each line forward, multiplies
+// it by its row of the real half grid d_khat and transforms it back (the spectrum never goes to
+// memory).
 static void conv_passes(nlint_plan_s *p) {
     const int d = p->d, n = p->n_fine;
     const int64_t N = p->N, nh = n / 2 + 1;
@@ -689,19 +692,6 @@ static void conv_passes(nlint_plan_s *p) {
     p->T1.fac = p->d_fac1;
     p->U3 = p->Q3;
     p->U3.fac = p->d_fac1;
-    std::memset(&p->U1, 0, sizeof(p->U1));
-    p->U1.n = n;
-    make_radix(n, p->U1);
-    p->U1.sign = +1;
-    p->U1.N = (int)N;
-    p->U1.dim = d;
-    p->U1.in_kind = IN_CPLX_MULT;
-    p->U1.out_kind = OUT_CPLX_MODES;
-    p->U1.I = (d == 3) ? nh * n : nh;
-    p->U1.in_so = n;
-    p->U1.out_so = N;
-    p->U1.mult = p->d_khat;
-    config_pass(p->U1, p->prec, true);
     std::memset(&p->X, 0, sizeof(p->X));
     p->X.n = n;
     make_radix(n, p->X);
@@ -938,7 +928,7 @@ static int run_eval(nlint_plan_s *p, const void *rho, void *u, double lambda, do
     if (rc) return rc;
     if (E) {
         CK(launch_energy_final(p->d_partials, p->n_partials, 0.5 * lambda * std::pow(p->h, p->d), E, s));
-        p->launches += 1;
+        p->launches += energy_final_kernels(p->n_partials);
         stage_mark(p, s, "energy");
     }
     return NLINT_OK;
@@ -970,7 +960,7 @@ static int run_toeplitz(nlint_plan_s *p, const void *rho, void *u, double lambda
     p->launches += (p->d == 3) ? 5 : 3;
     if (E) {
         CK(launch_energy_final(p->d_partials, p->n_partials, 0.5 * lambda * std::pow(p->h, p->d), E, s));
-        p->launches += 1;
+        p->launches += energy_final_kernels(p->n_partials);
         stage_mark(p, s, "energy");
     }
     return NLINT_OK;
@@ -1041,7 +1031,7 @@ static int run_alg2(nlint_plan_s *p, const void *rho, void *u, double lambda, do
     }
     if (E) {
         CK(launch_energy_final(p->d_partials, p->n_partials, 0.5 * lambda * std::pow(p->h, p->d), E, s));
-        p->launches += 1;
+        p->launches += energy_final_kernels(p->n_partials);
         stage_mark(p, s, "energy");
     }
     return NLINT_OK;
@@ -1193,7 +1183,7 @@ int nlint_energy(nlint_plan p, const void *rho, const void *u, double lambda, do
     else CK(launch_energy_partials<double>(count, u, rho, p->d_partials, nb, s));
     double *E = E_dev ? E_dev : p->d_E;
     CK(launch_energy_final(p->d_partials, nb, 0.5 * lambda * std::pow(p->h, p->d), E, s));
-    p->launches += 2;
+    p->launches += 1 + energy_final_kernels(nb);
     if (E_host) {
         CK(cudaMemcpyAsync(E_host, E, sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
@@ -1356,7 +1346,7 @@ int nlint_energy_only(nlint_plan p, const void *rho, double lambda, double *E_de
     }
     double *E = E_dev ? E_dev : p->d_E;
     CK(launch_energy_final(p->d_epart, (int)p->nsub, scale, E, s));
-    p->launches += 2;
+    p->launches += 1 + energy_final_kernels((int)p->nsub);
     if (E_host) {
         CK(cudaMemcpyAsync(E_host, E, sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
