@@ -183,18 +183,42 @@ __global__ void __launch_bounds__(SUB_THREADS) interp_sub_kernel(NodeDesc nd,
 
     // stage the tile; the common case (axis-0 planes inside the stored half) needs no mirror
     const bool inside = bo.x >= 0 && bo.x + G_::T0 - 1 <= n / 2;
-    for (int cell = threadIdx.x; cell < G_::NCELL; cell += blockDim.x) {
-        int a0, a1, a2;
-        cell_coords<G_>(cell, a0, a1, a2);
-        T2 v;
-        if (inside) {
-            const int l0 = bo.x + a0, l1 = wrap1(bo.y + a1, n);
-            v = (D == 3) ? G[((int64_t)l0 * n + l1) * n + wrap1(bo.z + a2, n)] : G[(int64_t)l0 * n + l1];
-        } else {
-            v = fetch_half<T, D>(G, n, bo.x + a0, bo.y + a1, bo.z + a2);
+    if (D == 3 && inside) {
+        // by (axis-1, axis-2) column: its wrapped offsets and base index once, then the T0
+        // planes at a constant stride (no per-cell index decomposition)
+        const int64_t nn = (int64_t)n * n;
+        for (int col = threadIdx.x; col < PLANE; col += blockDim.x) {
+            const int a1 = col / G_::T2, a2 = col - a1 * G_::T2;
+            const T2 *g = G + ((int64_t)bo.x * n + wrap1(bo.y + a1, n)) * n + wrap1(bo.z + a2, n);
+            constexpr int GRP = 4;  // planes in flight per thread (bounds the registers)
+#pragma unroll 1
+            for (int a0b = 0; a0b < G_::T0; a0b += GRP) {
+                T2 v[GRP];
+#pragma unroll
+                for (int k = 0; k < GRP; k++)
+                    if (a0b + k < G_::T0) v[k] = g[(a0b + k) * nn];
+#pragma unroll
+                for (int k = 0; k < GRP; k++)
+                    if (a0b + k < G_::T0) {
+                        tr[(a0b + k) * PLANE + col] = v[k].x;
+                        ti[(a0b + k) * PLANE + col] = v[k].y;
+                    }
+            }
         }
-        tr[cell] = v.x;
-        ti[cell] = v.y;
+    } else {
+        for (int cell = threadIdx.x; cell < G_::NCELL; cell += blockDim.x) {
+            int a0, a1, a2;
+            cell_coords<G_>(cell, a0, a1, a2);
+            T2 v;
+            if (inside) {
+                const int l0 = bo.x + a0, l1 = wrap1(bo.y + a1, n);
+                v = (D == 3) ? G[((int64_t)l0 * n + l1) * n + wrap1(bo.z + a2, n)] : G[(int64_t)l0 * n + l1];
+            } else {
+                v = fetch_half<T, D>(G, n, bo.x + a0, bo.y + a1, bo.z + a2);
+            }
+            tr[cell] = v.x;
+            ti[cell] = v.y;
+        }
     }
     __syncthreads();
 
@@ -366,6 +390,23 @@ __global__ void __launch_bounds__(SUB_THREADS) spread_sub_kernel(NodeDesc nd,
 
     const int slot = bo.w;
     const int nplanes = n / 2 + 1 + 2 * pad;
+    if (D == 3 && slot < 0) {
+        // by (axis-1, axis-2) column, as the interpolation's tile load: wrapped offsets once,
+        // then the planes of the extended grid at a constant stride
+        const int64_t nn = (int64_t)n * n;
+        for (int col = threadIdx.x; col < PLANE; col += blockDim.x) {
+            const int a1 = col / G_::T2, a2 = col - a1 * G_::T2;
+            const int64_t gb = (int64_t)wrap1(bo.y + a1, n) * n + wrap1(bo.z + a2, n);
+#pragma unroll
+            for (int a0 = 0; a0 < G_::T0; a0++) {
+                const A qr = tr[a0 * PLANE + col], qi = ti[a0 * PLANE + col];
+                const int pl = bo.x + a0 + pad;
+                if ((qr == 0 && qi == 0) || pl < 0 || pl >= nplanes) continue;
+                atomic_add_cx(H + pl * nn + gb, (T)qr * inv_s, (T)qi * inv_s);
+            }
+        }
+        return;
+    }
     for (int cell = threadIdx.x; cell < G_::NCELL; cell += blockDim.x) {
         const A qr = tr[cell], qi = ti[cell];
         if (qr == 0 && qi == 0) continue;
