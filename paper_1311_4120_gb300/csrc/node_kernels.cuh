@@ -101,19 +101,24 @@ struct NodeGroup {
     }
 };
 
-// Kernel values of the group into the warp's table ker[h*3*MAXW + a*MAXW + q] for node h of
-// the group, stencil cell q of axis a.
+// Slot of this lane's v-th kernel value in the warp's table ker[h*3*MAXW + a*MAXW + q] (node h
+// of the group, stencil cell q of axis a), or -1; depends on the lane only, so it is computed
+// once per thread.
 template <typename T, int D, int W>
-__device__ __forceinline__ void warp_kernel_values(const NodeGroup<T, D, W> &np, int lane, T *ker) {
+__device__ __forceinline__ int kernel_slot(int lane, int v) {
+    const int t = lane + 32 * v;
+    if (t >= NodeGroup<T, D, W>::NKV) return -1;
+    const int h = (NodeGroup<T, D, W>::NPW == 1) ? 0 : t / (D * W);
+    const int rem = t - h * D * W, a = rem / W, q = rem - a * W;
+    return h * 3 * MAXW + a * MAXW + q;
+}
+
+// Kernel values of the group into the warp's table.
+template <typename T, int D, int W>
+__device__ __forceinline__ void warp_kernel_values(const NodeGroup<T, D, W> &np, const int *slot, T *ker) {
 #pragma unroll
-    for (int v = 0; v < NodeGroup<T, D, W>::KV; v++) {
-        const int t = lane + 32 * v;
-        if (t < NodeGroup<T, D, W>::NKV) {
-            const int h = (NodeGroup<T, D, W>::NPW == 1) ? 0 : t / (D * W);
-            const int rem = t - h * D * W, a = rem / W, q = rem - a * W;
-            ker[h * 3 * MAXW + a * MAXW + q] = np.kv[v];
-        }
-    }
+    for (int v = 0; v < NodeGroup<T, D, W>::KV; v++)
+        if (slot[v] >= 0) ker[slot[v]] = np.kv[v];
 }
 
 // Decompose a tile cell into its per-axis offsets.
@@ -125,10 +130,15 @@ __device__ __forceinline__ void cell_coords(int cell, int &a0, int &a1, int &a2)
     a2 = rem - a1 * G_::T2;
 }
 
-// Tile offset of stencil column (qa, qb) for the origin (r0, r1, r2): axis-0 run start.
+// Tile offset of stencil column (qa, qb) for the origin (r0, r1, r2), axis-0 run start:
+// origin_index(r0, r1, r2) + column_offset(qa, qb).
 template <typename G_, int D>
-__device__ __forceinline__ int col_index(int r0, int r1, int r2, int qa, int qb) {
-    return (D == 3) ? (r0 * G_::T1 + r1 + qa) * G_::T2 + r2 + qb : (r0 + qa) * G_::T1 + r1 + qb;
+__device__ __forceinline__ int origin_index(int r0, int r1, int r2) {
+    return (D == 3) ? (r0 * G_::T1 + r1) * G_::T2 + r2 : r0 * G_::T1 + r1;
+}
+template <typename G_, int D>
+__device__ __forceinline__ int column_offset(int qa, int qb) {
+    return (D == 3) ? qa * G_::T2 + qb : qa * G_::T1 + qb;
 }
 
 // Each warp owns a contiguous run of its subproblem's nodes.
@@ -177,9 +187,18 @@ __global__ void __launch_bounds__(SUB_THREADS) interp_sub_kernel(NodeDesc nd,
     const int4 sb = nd.subs[blockIdx.x];
     const int4 bo = nd.bins[sb.z];
     const int n = nd.n;
-    int pairs[PASSES];  // this lane's stencil columns, one per pass (-1: idle)
+    // this lane's stencil columns, one per pass (-1: idle), as tile offsets and kernel-table
+    // offsets of the two column axes; its slots in the warp's kernel table
+    int coff[PASSES], kab_off[PASSES], kslot[NodeGroup<T, D, W>::KV];
 #pragma unroll
-    for (int ps = 0; ps < PASSES; ps++) pairs[ps] = nd.pair_order[ps * G_::LPN + lane % G_::LPN];
+    for (int ps = 0; ps < PASSES; ps++) {
+        const int pq = nd.pair_order[ps * G_::LPN + lane % G_::LPN];
+        const int qa = pq >> 8, qb = pq & 255;
+        coff[ps] = pq >= 0 ? column_offset<G_, D>(qa, qb) : -1;
+        kab_off[ps] = (D == 3) ? (MAXW + qa) | ((2 * MAXW + qb) << 16) : qa | ((MAXW + qb) << 16);
+    }
+#pragma unroll
+    for (int v = 0; v < NodeGroup<T, D, W>::KV; v++) kslot[v] = kernel_slot<T, D, W>(lane, v);
 
     // stage the tile; the common case (axis-0 planes inside the stored half) needs no mirror
     const bool inside = bo.x >= 0 && bo.x + G_::T0 - 1 <= n / 2;
@@ -234,25 +253,25 @@ __global__ void __launch_bounds__(SUB_THREADS) interp_sub_kernel(NodeDesc nd,
         const int mine = j + half;
         const bool act = (G_::NPW == 1) || mine < jb;
         const T Wj = (act && apply_W) ? reinterpret_cast<const T *>(nd.W)[mine] : T(1);
-        warp_kernel_values<T, D, W>(cur, lane, ker);
+        warp_kernel_values<T, D, W>(cur, kslot, ker);
         __syncwarp();
         T accr = T(0), acci = T(0);
         if (act) {
             T k0[L];
 #pragma unroll
             for (int q = 0; q < L; q++) k0[q] = (D == 3) ? kh[q] : T(1);
+            const int obase = origin_index<G_, D>(cur.r0, cur.r1, cur.r2);
 #pragma unroll
             for (int ps = 0; ps < PASSES; ps++) {
-                const int pq = pairs[ps];
-                if (pq >= 0) {
-                    const int qa = pq >> 8, qb = pq & 255;
-                    const T kab = (D == 3) ? kh[MAXW + qa] * kh[2 * MAXW + qb] : kh[qa] * kh[MAXW + qb];
-                    const int idx = col_index<G_, D>(cur.r0, cur.r1, cur.r2, qa, qb);
+                if (coff[ps] >= 0) {
+                    const T kab = kh[kab_off[ps] & 0xffff] * kh[kab_off[ps] >> 16];
+                    const int idx = obase + coff[ps];
+                    const T *pr = tr + idx, *pi = ti + idx;  // the column's run: constant offsets
                     T sr = T(0), si = T(0);
 #pragma unroll
                     for (int q0 = 0; q0 < L; q0++) {
-                        sr += k0[q0] * tr[idx + q0 * PLANE];
-                        si += k0[q0] * ti[idx + q0 * PLANE];
+                        sr += k0[q0] * pr[q0 * PLANE];
+                        si += k0[q0] * pi[q0 * PLANE];
                     }
                     accr += kab * sr;
                     acci += kab * si;
@@ -303,9 +322,17 @@ __global__ void __launch_bounds__(SUB_THREADS) spread_sub_kernel(NodeDesc nd,
     const int4 sb = nd.subs[blockIdx.x];
     const int4 bo = nd.bins[sb.z];
     const int n = nd.n, pad = nd.pad;
-    int pairs[PASSES];
+    // per-lane constants (see the interpolation kernel)
+    int coff[PASSES], kab_off[PASSES], kslot[NodeGroup<T, D, W>::KV];
 #pragma unroll
-    for (int ps = 0; ps < PASSES; ps++) pairs[ps] = nd.pair_order[ps * G_::LPN + lane % G_::LPN];
+    for (int ps = 0; ps < PASSES; ps++) {
+        const int pq = nd.pair_order[ps * G_::LPN + lane % G_::LPN];
+        const int qa = pq >> 8, qb = pq & 255;
+        coff[ps] = pq >= 0 ? column_offset<G_, D>(qa, qb) : -1;
+        kab_off[ps] = (D == 3) ? (MAXW + qa) | ((2 * MAXW + qb) << 16) : qa | ((MAXW + qb) << 16);
+    }
+#pragma unroll
+    for (int v = 0; v < NodeGroup<T, D, W>::KV; v++) kslot[v] = kernel_slot<T, D, W>(lane, v);
 
     // bound B = max(sum |Re c_j|, sum |Im c_j|) over the subproblem, while the tile is cleared
     T bre = T(0), bim = T(0);
@@ -359,25 +386,25 @@ __global__ void __launch_bounds__(SUB_THREADS) spread_sub_kernel(NodeDesc nd,
             cn = (j + G_::NPW + half < jb) ? c_in[j + G_::NPW + half] : czero<T2>();
         }
         const bool act = (G_::NPW == 1) || j + half < jb;
-        warp_kernel_values<T, D, W>(cur, lane, ker);
+        warp_kernel_values<T, D, W>(cur, kslot, ker);
         __syncwarp();
         if (act) {
             T k0[L];
 #pragma unroll
             for (int q = 0; q < L; q++) k0[q] = (D == 3) ? kh[q] : T(1);
             const T csr = c.x * S, csi = c.y * S;
+            const int obase = origin_index<G_, D>(cur.r0, cur.r1, cur.r2);
 #pragma unroll
             for (int ps = 0; ps < PASSES; ps++) {
-                const int pq = pairs[ps];
-                if (pq >= 0) {
-                    const int qa = pq >> 8, qb = pq & 255;
-                    const T kab = (D == 3) ? kh[MAXW + qa] * kh[2 * MAXW + qb] : kh[qa] * kh[MAXW + qb];
+                if (coff[ps] >= 0) {
+                    const T kab = kh[kab_off[ps] & 0xffff] * kh[kab_off[ps] >> 16];
                     const T cr = csr * kab, ci = csi * kab;
-                    const int idx = col_index<G_, D>(cur.r0, cur.r1, cur.r2, qa, qb);
+                    const int idx = obase + coff[ps];
+                    A *pr = tr + idx, *pi = ti + idx;  // the column's run: constant offsets
 #pragma unroll
                     for (int q0 = 0; q0 < L; q0++) {
-                        F::add(tr + idx + q0 * PLANE, F::quant(cr * k0[q0]));
-                        F::add(ti + idx + q0 * PLANE, F::quant(ci * k0[q0]));
+                        F::add(pr + q0 * PLANE, F::quant(cr * k0[q0]));
+                        F::add(pi + q0 * PLANE, F::quant(ci * k0[q0]));
                     }
                 }
             }
