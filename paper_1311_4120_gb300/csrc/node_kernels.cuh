@@ -142,9 +142,12 @@ __device__ __forceinline__ int column_offset(int qa, int qb) {
 }
 
 // Each warp owns a contiguous run of its subproblem's nodes.
-__device__ __forceinline__ void warp_chunk(int4 sb, int wid, int nw, int &ja, int &jb) {
-    ja = sb.x + (int)(((int64_t)sb.y * wid) / nw);
-    jb = sb.x + (int)(((int64_t)sb.y * (wid + 1)) / nw);
+// (32-bit: a subproblem holds at most 2^20 nodes; the warp count is the compile-time
+// SUB_THREADS / 32, so the division is a shift.)
+__device__ __forceinline__ void warp_chunk(int4 sb, int wid, int &ja, int &jb) {
+    constexpr int NW = SUB_THREADS / 32;
+    ja = sb.x + (sb.y * wid) / NW;
+    jb = sb.x + (sb.y * (wid + 1)) / NW;
 }
 
 // Fixed-point accumulation of the spreading tile.  Shared-memory floating-point atomics are
@@ -182,7 +185,8 @@ __global__ void __launch_bounds__(SUB_THREADS) interp_sub_kernel(NodeDesc nd,
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *tr = reinterpret_cast<T *>(smem_raw);
     T *ti = tr + G_::NCELL;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    constexpr int nw = SUB_THREADS / 32;  // the kernels are launched with SUB_THREADS threads
     T *ker = ti + G_::NCELL + wid * 6 * MAXW;
     const int4 sb = nd.subs[blockIdx.x];
     const int4 bo = nd.bins[sb.z];
@@ -242,7 +246,7 @@ __global__ void __launch_bounds__(SUB_THREADS) interp_sub_kernel(NodeDesc nd,
     __syncthreads();
 
     int ja, jb;
-    warp_chunk(sb, wid, nw, ja, jb);
+    warp_chunk(sb, wid, ja, jb);
     const int half = lane / G_::LPN, hl = lane % G_::LPN;  // node of the group, lane in it
     const T *kh = ker + half * 3 * MAXW;  // this lane's node's kernel values
     NodeGroup<T, D, W> cur, nxt;
@@ -317,7 +321,8 @@ __global__ void __launch_bounds__(SUB_THREADS) spread_sub_kernel(NodeDesc nd,
     extern __shared__ __align__(16) unsigned char smem_raw[];
     A *tr = reinterpret_cast<A *>(smem_raw);
     A *ti = tr + G_::NCELL;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    constexpr int nw = SUB_THREADS / 32;  // the kernels are launched with SUB_THREADS threads
     T *ker = reinterpret_cast<T *>(ti + G_::NCELL) + wid * 6 * MAXW;
     const int4 sb = nd.subs[blockIdx.x];
     const int4 bo = nd.bins[sb.z];
@@ -371,7 +376,7 @@ __global__ void __launch_bounds__(SUB_THREADS) spread_sub_kernel(NodeDesc nd,
     __syncthreads();  // every warp has read the bound before the tables are overwritten
 
     int ja, jb;
-    warp_chunk(sb, wid, nw, ja, jb);
+    warp_chunk(sb, wid, ja, jb);
     const int half = lane / G_::LPN;
     const T *kh = ker + half * 3 * MAXW;
     NodeGroup<T, D, W> cur, nxt;
