@@ -39,8 +39,12 @@ __host__ __device__ constexpr int fft_pprod(int n, int s) {  // product of the r
 }
 // Pass modes: 0 column pass; 1 row pass; 2 row pass that reads more than it writes (the fold
 // input of the first inverse pass), which wants more threads per line.
+// Values per thread of the packed real-data column passes (modes 3, 4) for n <= 512, and the
+// resident CTAs their FP32 512-thread launches ask for (tuning constants).
+constexpr int FFT_PACKED_VPT = 8, FFT_PACKED_MINB = 3;
 __host__ __device__ constexpr int fft_vpt(int n, int mode = 0) {
-    return fft_has3(n) ? 24 : (n <= 512 ? (mode == 2 ? 8 : 16) : 32);
+    return fft_has3(n) ? 24
+                       : (n <= 512 ? (mode == 2 ? 8 : ((mode == 3 || mode == 4) ? FFT_PACKED_VPT : 16)) : 32);
 }
 __host__ __device__ constexpr int fft_tpl(int n, int mode = 0) { return n / fft_vpt(n, mode); }  // 2^k
 __host__ __device__ constexpr int fft_row_ld(int n) { return n + n / 16; }  // padded row line
@@ -53,6 +57,11 @@ __host__ __device__ constexpr int fft_col_b_raw(int n, int cs) {  // <= 192 KB o
 }
 __host__ __device__ constexpr int fft_col_b(int n, int cs) {
     return fft_col_b_raw(n, cs) * fft_tpl(n) >= 32 ? fft_col_b_raw(n, cs) : 32 / fft_tpl(n);
+}
+// per mode: packed passes with half the values per thread take half the column pairs per CTA
+__host__ __device__ constexpr int fft_col_b_m(int n, int cs, int mode) {
+    return ((mode == 3 || mode == 4) && fft_vpt(n, mode) * 2 == fft_vpt(n, 0) && fft_col_b(n, cs) >= 2)
+               ? fft_col_b(n, cs) / 2 : fft_col_b(n, cs);
 }
 // Row pass: about 256 threads (mode 1) or 512 threads (mode 2) per CTA.
 __host__ __device__ constexpr int fft_row_thr(int mode) { return mode == 2 ? 512 : 256; }
@@ -99,11 +108,11 @@ struct FftCfg {
     static constexpr int CS = (int)(2 * sizeof(T));
     static constexpr int TPL = fft_tpl(NF, MODE);  // threads per line
     static constexpr int NST = fft_nstages(NF);
-    static constexpr int B = fft_is_row(MODE) ? fft_row_b(NF, CS, MODE) : fft_col_b(NF, CS);  // lines
+    static constexpr int B = fft_is_row(MODE) ? fft_row_b(NF, CS, MODE) : fft_col_b_m(NF, CS, MODE);  // lines
     static constexpr int ROW_LD = fft_row_ld(NF);
     static constexpr int THREADS = B * TPL;
     // packed passes hold two lines' loads in flight: ask for two resident CTAs of 512 threads
-    static constexpr int MIN_BLOCKS = (fft_packed(MODE) && THREADS == 512 && NF <= 512 && sizeof(T) == 4) ? 2
+    static constexpr int MIN_BLOCKS = (fft_packed(MODE) && THREADS == 512 && NF <= 512 && sizeof(T) == 4) ? FFT_PACKED_MINB
                                       : (MODE == 5 && NF <= 512 && sizeof(T) == 4) ? 3 : 0;
 };
 

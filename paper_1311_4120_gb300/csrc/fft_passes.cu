@@ -62,7 +62,7 @@ void config_pass(PassDesc &p, int prec, bool row) {
     const int cs = prec == NLINT_FP32 ? 8 : 16;
     const int mode = pass_mode(p, row);
     p.TPC = fft_tpl(p.n, mode);
-    p.B = row ? fft_row_b(p.n, cs, mode) : fft_col_b(p.n, cs);
+    p.B = row ? fft_row_b(p.n, cs, mode) : fft_col_b_m(p.n, cs, mode);
     p.LD = row ? fft_row_ld(p.n) : p.B;
 }
 
