@@ -39,13 +39,20 @@ __host__ __device__ constexpr int fft_pprod(int n, int s) {  // product of the r
 }
 // Pass modes: 0 column pass; 1 row pass; 2 row pass that reads more than it writes (the fold
 // input of the first inverse pass), which wants more threads per line.
-// Values per thread of the packed real-data column passes (modes 3, 4) for n <= 512, and the
-// resident CTAs their FP32 512-thread launches ask for (tuning constants).
-constexpr int FFT_PACKED_VPT = 8, FFT_PACKED_MINB = 3;
-__host__ __device__ constexpr int fft_vpt(int n, int mode = 0) {
-    return fft_has3(n) ? 24
-                       : (n <= 512 ? (mode == 2 ? 8 : ((mode == 3 || mode == 4) ? FFT_PACKED_VPT : 16)) : 32);
+// Tuning constants for 2^a lines of n <= 512, per pass mode: values per thread, and the
+// resident CTAs that FP32 launches of 512 threads (mode 5: any size) ask for (0: the
+// compiler's choice).  Measured on the 256^3 workload (see the commit history).
+constexpr int FFT_VPT0 = 16, FFT_MINB0 = 0;                 // column passes
+constexpr int FFT_VPT1 = 16, FFT_MINB1 = 0;                 // row passes
+constexpr int FFT_PACKED_VPT = 8, FFT_PACKED_MINB = 3;      // packed real-data column passes
+__host__ __device__ constexpr int fft_vpt_small(int mode) {
+    return mode == 0 ? FFT_VPT0 : mode == 1 ? FFT_VPT1 : mode == 2 ? 8
+         : (mode == 3 || mode == 4) ? FFT_PACKED_VPT : 16;
 }
+__host__ __device__ constexpr int fft_vpt(int n, int mode = 0) {
+    return fft_has3(n) ? 24 : (n <= 512 ? fft_vpt_small(mode) : 32);
+}
+__host__ __device__ constexpr int fft_vpt_ref(int n) { return fft_has3(n) ? 24 : (n <= 512 ? 16 : 32); }
 __host__ __device__ constexpr int fft_tpl(int n, int mode = 0) { return n / fft_vpt(n, mode); }  // 2^k
 __host__ __device__ constexpr int fft_row_ld(int n) { return n + n / 16; }  // padded row line
 // Lines per CTA.  Column pass: 128-byte rows (16 FP32 / 8 FP64 complex), fewer for the
@@ -55,13 +62,13 @@ __host__ __device__ constexpr int fft_pow2_floor(int m) { return m < 2 ? 1 : 2 *
 __host__ __device__ constexpr int fft_col_b_raw(int n, int cs) {  // <= 192 KB of shared memory
     return (128 / cs) < fft_pow2_floor(196608 / (n * cs)) ? 128 / cs : fft_pow2_floor(196608 / (n * cs));
 }
-__host__ __device__ constexpr int fft_col_b(int n, int cs) {
-    return fft_col_b_raw(n, cs) * fft_tpl(n) >= 32 ? fft_col_b_raw(n, cs) : 32 / fft_tpl(n);
+__host__ __device__ constexpr int fft_col_b(int n, int cs) {  // at the reference 16 values
+    return fft_col_b_raw(n, cs) * (n / fft_vpt_ref(n)) >= 32 ? fft_col_b_raw(n, cs) : 32 / (n / fft_vpt_ref(n));
 }
-// per mode: packed passes with half the values per thread take half the column pairs per CTA
+// per mode: column passes with half the values per thread take half the lines per CTA
 __host__ __device__ constexpr int fft_col_b_m(int n, int cs, int mode) {
-    return ((mode == 3 || mode == 4) && fft_vpt(n, mode) * 2 == fft_vpt(n, 0) && fft_col_b(n, cs) >= 2)
-               ? fft_col_b(n, cs) / 2 : fft_col_b(n, cs);
+    return (fft_vpt(n, mode) * 2 == fft_vpt_ref(n) && fft_col_b(n, cs) >= 2) ? fft_col_b(n, cs) / 2
+                                                                             : fft_col_b(n, cs);
 }
 // Row pass: about 256 threads (mode 1) or 512 threads (mode 2) per CTA.
 __host__ __device__ constexpr int fft_row_thr(int mode) { return mode == 2 ? 512 : 256; }
@@ -112,8 +119,11 @@ struct FftCfg {
     static constexpr int ROW_LD = fft_row_ld(NF);
     static constexpr int THREADS = B * TPL;
     // packed passes hold two lines' loads in flight: ask for two resident CTAs of 512 threads
-    static constexpr int MIN_BLOCKS = (fft_packed(MODE) && THREADS == 512 && NF <= 512 && sizeof(T) == 4) ? FFT_PACKED_MINB
-                                      : (MODE == 5 && NF <= 512 && sizeof(T) == 4) ? 3 : 0;
+    static constexpr bool F32_512 = THREADS == 512 && NF <= 512 && sizeof(T) == 4;
+    static constexpr int MIN_BLOCKS = (fft_packed(MODE) && F32_512) ? FFT_PACKED_MINB
+                                    : (MODE == 0 && F32_512) ? FFT_MINB0
+                                    : (MODE == 1 && F32_512) ? FFT_MINB1
+                                    : (MODE == 5 && NF <= 512 && sizeof(T) == 4) ? 3 : 0;
 };
 
 // ------------------------------------------------------------------ butterflies
