@@ -369,6 +369,19 @@ __global__ void __launch_bounds__(SUB_THREADS) spread_sub_kernel(NodeDesc nd,
     // B to within rounding (<= 1024 terms: a relative 1e-4 in FP32); the headroom of 2^E below
     // the integer range (4x) absorbs it
     const T bound = fmax(sre, sim);
+    if (!isfinite(sre) || !isfinite(sim)) {
+        // a non-finite c_j has no fixed-point image: put a NaN into the grid (one cell of the
+        // bin) so that it reaches u as a NaN would without the fixed-point accumulation
+        if (threadIdx.x == 0) {
+            const int np = n / 2 + 1 + 2 * pad;
+            const int pl = min(max(bo.x + pad, 0), np - 1);
+            const int64_t g = (D == 3) ? ((int64_t)pl * n + wrap1(bo.y, n)) * n + wrap1(bo.z, n)
+                                       : (int64_t)pl * n + wrap1(bo.y, n);
+            const T nan = T(NAN);
+            atomic_add_cx(H + g, nan, nan);
+        }
+        return;
+    }
     if (!(bound > T(0))) return;  // every c_j of the subproblem is zero: nothing to add
     int ex = F::E - ilogb(bound) - 1;  // S = 2^ex, S * bound <= 2^E
     if (ex > F::MAXEXP) ex = F::MAXEXP;   // tiny bounds: keep S finite (cells stay < 2^E)
