@@ -102,6 +102,7 @@ typedef struct nlint_info {
     int device;             /* CUDA device ordinal the plan lives on                    */
     int algorithm;          /* 1 or 2; for 2 the node fields describe I_2's nodes       */
     double pu_a, pu_r0, pu_r1, P2; /* Algorithm 2's partition parameters (0 if unused)  */
+    int toeplitz;           /* 1 once nlint_plan_toeplitz has precomputed K_hat          */
 } nlint_info;
 
 /* Fill *p with defaults (d = 3, Coulomb, eps = 1e-6, everything else automatic). */
@@ -204,7 +205,9 @@ int nlint_autotune(const nlint_params *in, double tol, const char *cache_path, n
                    nlint_tune_report *rep);
 
 /* Batched evaluation of independent densities (Algorithm 1 applied to each), e.g. grids of
- * mixed sizes, kernels and precisions.  nlint_batch_create: `count` plans (not owned: they
+ * mixed sizes, kernels and precisions.  A plan whose Toeplitz kernel has been precomputed
+ * (nlint_plan_toeplitz) before the batch graph is captured is evaluated in that form (the same
+ * operator to the NUFFT tolerance, FFT passes only); the others by nlint_eval_energy.  nlint_batch_create: `count` plans (not owned: they
  * must outlive the batch), all on one device; `branches` concurrent streams inside the batch's
  * CUDA graph (0 = min(16, count)); plans are dealt to branches by a cost model.
  * nlint_batch_eval: rho[i], u[i] are plan i's device arrays (its n^d reals, its precision);

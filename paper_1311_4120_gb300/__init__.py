@@ -68,7 +68,8 @@ class nlint_info(ctypes.Structure):
                 ("n_subproblems", ctypes.c_int64), ("n_crowd_bins", ctypes.c_int64),
                 ("bin", ctypes.c_int * 3), ("device", ctypes.c_int),
                 ("algorithm", ctypes.c_int), ("pu_a", ctypes.c_double),
-                ("pu_r0", ctypes.c_double), ("pu_r1", ctypes.c_double), ("P2", ctypes.c_double)]
+                ("pu_r0", ctypes.c_double), ("pu_r1", ctypes.c_double), ("P2", ctypes.c_double),
+                ("toeplitz", ctypes.c_int)]
 
 
 _lib = None

@@ -83,8 +83,10 @@ int nlint_batch_create(int count, const nlint_plan *plans, int branches, nlint_b
         double pts = 1.0;
         for (int a = 0; a < inf.d; a++) pts *= (double)inf.n_fine;
         // cost model: oversampled-grid traffic plus node work (w^d per node), in grid-point units
-        cost[i] = 3.0 * pts + (double)inf.n_half_nodes * std::pow((double)inf.w, inf.d) / 8.0 *
-                                  (inf.precision == NLINT_FP64 ? 16.0 : 1.0);
+        // (a plan with a precomputed Toeplitz kernel runs FFT passes only)
+        cost[i] = 3.0 * pts + (inf.toeplitz ? 0.0
+                                            : (double)inf.n_half_nodes * std::pow((double)inf.w, inf.d) /
+                                                  8.0 * (inf.precision == NLINT_FP64 ? 16.0 : 1.0));
         b->plans.push_back(plans[i]);
     }
     b->device = dev;
@@ -146,8 +148,12 @@ static int batch_capture(nlint_batch_s *b, const void *const *rho, void *const *
         e = cudaStreamWaitEvent(b->branch[k], b->fork, 0);
     for (size_t k = 0; k < b->branch.size() && e == cudaSuccess && rc == NLINT_OK; k++) {
         for (int i : b->deal[k]) {
-            rc = nlint_eval_energy(b->plans[i], rho[i], u[i], lambda, E_dev ? E_dev + i : nullptr,
-                                   (void *)b->branch[k]);
+            nlint_info inf;
+            rc = nlint_plan_info(b->plans[i], &inf);
+            if (rc != NLINT_OK) break;
+            double *Ei = E_dev ? E_dev + i : nullptr;
+            rc = inf.toeplitz ? nlint_eval_toeplitz(b->plans[i], rho[i], u[i], lambda, Ei, (void *)b->branch[k])
+                              : nlint_eval_energy(b->plans[i], rho[i], u[i], lambda, Ei, (void *)b->branch[k]);
             if (rc != NLINT_OK) break;
         }
         if (rc == NLINT_OK) e = cudaEventRecord(b->join[k], b->branch[k]);

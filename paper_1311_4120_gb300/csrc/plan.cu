@@ -1140,6 +1140,7 @@ int nlint_plan_info(nlint_plan p, nlint_info *info) {
     info->pu_r0 = p->pu_r0;
     info->pu_r1 = p->pu_r1;
     info->P2 = p->rad2;
+    info->toeplitz = p->toeplitz ? 1 : 0;
     return NLINT_OK;
 }
 

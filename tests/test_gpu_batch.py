@@ -93,3 +93,31 @@ def test_batch_members_match_oracle(pkg):
 def test_batch_rejects_bad_arguments(pkg):
     with pytest.raises(pkg.NlintError):
         pkg.Batch([])
+
+
+def test_batch_uses_each_plans_form(pkg):
+    """Plans with a precomputed Toeplitz kernel run in that form inside the batch graph, the
+    others by the NUFFT path (and an Algorithm 2 plan by its own path): each member equals
+    the same plan evaluated alone in its form."""
+    members = _members("fp32", count=8)
+    plans, rhos, singles = [], [], []
+    for i, (n, k, a, nd, rho) in enumerate(members):
+        alg = 2 if i == 5 else 1
+        p = pkg.Plan(3, n, 16.0, k, axis=a, nodes=None if alg == 2 else nd, precision="fp32",
+                     eps=1e-6, algorithm=alg, device=0)
+        if i % 2 == 0:
+            p.toeplitz()
+        r = torch.from_numpy(rho).to("cuda:0", torch.float32)
+        u, E = p.eval_toeplitz(r, lam=1.1) if i % 2 == 0 else p.eval_energy(r, lam=1.1)
+        singles.append((u.double().cpu().numpy(), float(E.item())))
+        plans.append(p)
+        rhos.append(r)
+    batch = pkg.Batch(plans, branches=3)
+    us, Es = batch.eval(rhos, lam=1.1)
+    torch.cuda.synchronize()
+    Es = Es.cpu().numpy()
+    for i, (u, E) in enumerate(singles):
+        ub = us[i].double().cpu().numpy()
+        assert np.max(np.abs(ub - u)) <= 1e-5 * np.max(np.abs(u)), i
+        assert abs(Es[i] - E) <= 1e-5 * abs(E), i
+    batch.close()
