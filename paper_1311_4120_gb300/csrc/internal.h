@@ -115,13 +115,16 @@ struct NodeDesc {
     int ncrowd;          // crowded bins (FP32 plans): their tiles are summed in FP64
     double2 *crowd;      // ncrowd tiles of complex doubles
     const int32_t *crowd_bin;  // bin of each crowd slot
-    const int16_t *pair_order; // per pass and node lane: column (q_a << 8 | q_b) or -1
+    const int16_t *pair_order; // per pass and node lane: column (q_a << 8 | q_b) or -1 (spreading)
+    const int16_t *pair_order_i;  // the same for the interpolation (8-byte tile cells)
 };
 
 // Deals the w*w stencil columns (q_a, q_b) of a node to passes of `lanes` lanes so that,
-// within a pass, the tile offsets q_a * row + q_b fall in distinct shared-memory banks where
-// possible (`banks` = 32 for 4-byte, 16 for 8-byte elements).  Returns passes * lanes entries.
-std::vector<int16_t> build_pair_order(int w, int row, int banks, int lanes);
+// within a pass, the tile offsets q_a * row + q_b of each group of `group` lanes (the lanes one
+// shared-memory wavefront serves: 32 for 4-byte, 16 for 8-byte elements) fall in distinct
+// banks where possible (`banks` = 32 for 4-byte, 16 for 8-byte elements).  Returns
+// passes * lanes entries.
+std::vector<int16_t> build_pair_order(int w, int row, int banks, int lanes, int group);
 
 // Bin extent (stencil-origin cells) along array axis `axis`; the same rule is compiled into
 // the kernels, so a plan's bins always match the tile geometry of its kernels.  3D: 8^3 bins,

@@ -183,6 +183,8 @@ __global__ void __launch_bounds__(SUB_THREADS) interp_sub_kernel(NodeDesc nd,
     using G_ = Geo<T, D, W>;
     constexpr int PASSES = G_::PASSES, L = (D == 3) ? W : 1, PLANE = G_::T1 * G_::T2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    // the tile as real and imaginary planes (measured faster than interleaved complex, whose
+    // one 8-byte load per stencil cell cost registers and resident CTAs)
     T *tr = reinterpret_cast<T *>(smem_raw);
     T *ti = tr + G_::NCELL;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -196,7 +198,7 @@ __global__ void __launch_bounds__(SUB_THREADS) interp_sub_kernel(NodeDesc nd,
     int coff[PASSES], kab_off[PASSES], kslot[NodeGroup<T, D, W>::KV];
 #pragma unroll
     for (int ps = 0; ps < PASSES; ps++) {
-        const int pq = nd.pair_order[ps * G_::LPN + lane % G_::LPN];
+        const int pq = nd.pair_order_i[ps * G_::LPN + lane % G_::LPN];
         const int qa = pq >> 8, qb = pq & 255;
         coff[ps] = pq >= 0 ? column_offset<G_, D>(qa, qb) : -1;
         kab_off[ps] = (D == 3) ? (MAXW + qa) | ((2 * MAXW + qb) << 16) : qa | ((MAXW + qb) << 16);
@@ -368,21 +370,16 @@ __global__ void __launch_bounds__(SUB_THREADS) spread_sub_kernel(NodeDesc nd,
     }
     // B to within rounding (<= 1024 terms: a relative 1e-4 in FP32); the headroom of 2^E below
     // the integer range (4x) absorbs it
-    const T bound = fmax(sre, sim);
-    if (!isfinite(sre) || !isfinite(sim)) {
-        // a non-finite c_j has no fixed-point image: put a NaN into the grid (one cell of the
-        // bin) so that it reaches u as a NaN would without the fixed-point accumulation
-        if (threadIdx.x == 0) {
-            const int np = n / 2 + 1 + 2 * pad;
-            const int pl = min(max(bo.x + pad, 0), np - 1);
-            const int64_t g = (D == 3) ? ((int64_t)pl * n + wrap1(bo.y, n)) * n + wrap1(bo.z, n)
-                                       : (int64_t)pl * n + wrap1(bo.y, n);
-            const T nan = T(NAN);
-            atomic_add_cx(H + g, nan, nan);
-        }
+    // (fmax drops a NaN operand: a non-finite sum makes the bound NaN explicitly)
+    const T bound = (isfinite(sre) && isfinite(sim)) ? fmax(sre, sim) : T(NAN);
+    if (!(bound > T(0))) {
+        // zero: every c_j of the subproblem is zero, nothing to add.  Non-finite: a c_j has no
+        // fixed-point image; a NaN in the grid's first cell (the plane below the stored half,
+        // folded into the half by the first inverse pass) reaches every u as it would without
+        // the fixed-point accumulation (NaN absorbs any concurrent addition to the cell)
+        if (bound != T(0) && threadIdx.x == 0) H[0] = cmake<T2>(T(NAN), T(NAN));
         return;
     }
-    if (!(bound > T(0))) return;  // every c_j of the subproblem is zero: nothing to add
     int ex = F::E - ilogb(bound) - 1;  // S = 2^ex, S * bound <= 2^E
     if (ex > F::MAXEXP) ex = F::MAXEXP;   // tiny bounds: keep S finite (cells stay < 2^E)
     const T S = (T)ldexp(1.0, ex), inv_s = (T)ldexp(1.0, -ex);

@@ -72,31 +72,35 @@ static void gauss_legendre(int m, std::vector<double> &x, std::vector<double> &w
 }
 
 
-std::vector<int16_t> build_pair_order(int w, int row, int banks, int lanes) {
+std::vector<int16_t> build_pair_order(int w, int row, int banks, int lanes, int group) {
     std::vector<std::pair<int, int>> rest;
     for (int a = 0; a < w; a++)
         for (int b = 0; b < w; b++) rest.push_back({a, b});
     const int passes = (w * w + lanes - 1) / lanes;
+    if (group <= 0 || group > lanes) group = lanes;
     std::vector<int16_t> out((size_t)passes * lanes, (int16_t)-1);
     for (int ps = 0; ps < passes; ps++) {
-        std::vector<std::pair<int, int>> cur, later;
-        std::vector<bool> used(banks, false);
-        for (auto &q : rest) {
-            const int r = (q.first * row + q.second) % banks;
-            if ((int)cur.size() < lanes && !used[r]) {
-                used[r] = true;
-                cur.push_back(q);
-            } else {
-                later.push_back(q);
+        // lanes in groups served by one shared-memory wavefront: distinct banks within a group
+        for (int g0 = 0; g0 < lanes && !rest.empty(); g0 += group) {
+            std::vector<std::pair<int, int>> cur, later;
+            std::vector<bool> used(banks, false);
+            for (auto &q : rest) {
+                const int r = (q.first * row + q.second) % banks;
+                if ((int)cur.size() < group && !used[r]) {
+                    used[r] = true;
+                    cur.push_back(q);
+                } else {
+                    later.push_back(q);
+                }
             }
+            while ((int)cur.size() < group && !later.empty()) {  // a bank is shared: unavoidable
+                cur.push_back(later.front());
+                later.erase(later.begin());
+            }
+            for (size_t l = 0; l < cur.size(); l++)
+                out[(size_t)ps * lanes + g0 + l] = (int16_t)(cur[l].first << 8 | cur[l].second);
+            rest = later;
         }
-        while ((int)cur.size() < lanes && !later.empty()) {  // a bank is shared: unavoidable
-            cur.push_back(later.front());
-            later.erase(later.begin());
-        }
-        for (size_t l = 0; l < cur.size(); l++)
-            out[(size_t)ps * lanes + l] = (int16_t)(cur[l].first << 8 | cur[l].second);
-        rest = later;
     }
     return out;
 }
@@ -116,7 +120,7 @@ struct nlint_plan_s {
     void *d_ker = nullptr, *d_W = nullptr, *d_fac = nullptr, *d_tw = nullptr;
     int32_t *d_perm = nullptr, *d_mirror = nullptr;
     int4 *d_subs = nullptr, *d_bins = nullptr;
-    int16_t *d_pairs = nullptr;
+    int16_t *d_pairs = nullptr, *d_pairs_i = nullptr;  // spreading / interpolation lane tables
     double2 *d_epart = nullptr;  // energy-only path: one partial per subproblem
     int32_t *d_crowd_bin = nullptr;
     double2 *d_crowd = nullptr;
@@ -239,7 +243,7 @@ static int upload(void **dst, const std::vector<double> &v, size_t &acc) {
 
 static void plan_free(nlint_plan_s *p) {
     void *ptrs[] = {p->d_rel, p->d_ker, p->d_W, p->d_fac, p->d_tw, p->d_perm, p->d_mirror,
-                    p->d_subs, p->d_bins, p->d_crowd_bin, p->d_crowd, p->d_pairs, p->d_epart, p->d_fac1, p->d_khat,
+                    p->d_subs, p->d_bins, p->d_crowd_bin, p->d_crowd, p->d_pairs, p->d_pairs_i, p->d_epart, p->d_fac1, p->d_khat,
                     p->d_bufA, p->d_bufB, p->d_bufG, p->d_c, p->d_partials, p->d_E,
                     p->d_rho_io, p->d_u_io};
     for (void *q : ptrs)
@@ -557,9 +561,16 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
     acc += sizeof(int4) * (subs.size() + bins.size()) + 4 * crowd_bin.size();
     {
         const int row = (d == 3) ? p->T[2] : p->T[1];
-        const std::vector<int16_t> po = build_pair_order(w, row, p->prec == NLINT_FP32 ? 32 : 16, node_lanes(w));
+        // FP32 tiles have 4-byte cells (32 banks, one wavefront per warp), FP64 tiles 8-byte
+        // cells (16 banks per half-warp wavefront); both kernels read / add one plane at a time
+        const int L = node_lanes(w);
+        const std::vector<int16_t> po = p->prec == NLINT_FP32 ? build_pair_order(w, row, 32, L, 32)
+                                                              : build_pair_order(w, row, 16, L, 16);
+        const std::vector<int16_t> &pi = po;
         CK(cudaMalloc((void **)&p->d_pairs, po.size() * sizeof(int16_t)));
         CK(cudaMemcpy(p->d_pairs, po.data(), po.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
+        CK(cudaMalloc((void **)&p->d_pairs_i, pi.size() * sizeof(int16_t)));
+        CK(cudaMemcpy(p->d_pairs_i, pi.data(), pi.size() * sizeof(int16_t), cudaMemcpyHostToDevice));
         acc += po.size() * sizeof(int16_t);
     }
 
@@ -876,6 +887,7 @@ static NodeDesc node_desc(nlint_plan_s *p) {
     nd.crowd = p->d_crowd;
     nd.crowd_bin = p->d_crowd_bin;
     nd.pair_order = p->d_pairs;
+    nd.pair_order_i = p->d_pairs_i;
     return nd;
 }
 
