@@ -152,8 +152,8 @@ int nlint_energy_only(nlint_plan plan, const void *rho_dev, double lambda, doubl
  * itself, and its DFT K_hat on the plan's oversampled grid (n_fine >= 2N, so the circular
  * convolution equals the linear one on the grid); it allocates K_hat (real, Hermitian half) and
  * synchronises `stream`.  nlint_eval_toeplitz then computes u (and E if E_dev != NULL) with the
- * FFT passes only: zero-padded forward FFT of rho, multiply by K_hat (fused into the first
- * inverse pass), inverse FFT, crop.  The result equals nlint_eval_energy's to the NUFFT
+ * FFT passes only: zero-padded forward FFT of rho, multiply by K_hat (between the forward and
+ * inverse transforms along x, in one row pass), inverse FFT, crop.  The result equals nlint_eval_energy's to the NUFFT
  * tolerance; no interpolation or spreading runs per evaluation.  This form is not in the paper:
  * it follows from the operator's Toeplitz structure. */
 /* Both return NLINT_EUNSUPPORTED for an Algorithm 2 plan (whose I_1 part already is an FFT

@@ -979,8 +979,8 @@ static int run_toeplitz(nlint_plan_s *p, const void *rho, void *u, double lambda
 }
 
 // Algorithm 2 (Section 3.3, eq. 3.9): u = I_1 + I_2.  I_1 (step 3): zero-padded forward FFT of
-// rho on the fine grid, multiply by U_hat (1 - p) (fused into the first inverse pass), inverse
-// FFT, crop -> u.  I_2 (step 4): the NUFFT path on I_2's nodes (weights W_j p(k_j)), its last
+// rho on the fine grid, multiply by U_hat (1 - p) (between the forward and inverse x transforms
+// of one row pass), inverse FFT, crop -> u.  I_2 (step 4): the NUFFT path on I_2's nodes (weights W_j p(k_j)), its last
 // pass adding onto u and taking the energy over the sum (step 5 and Remark 3.3).
 template <typename T>
 static int run_alg2(nlint_plan_s *p, const void *rho, void *u, double lambda, double *E,
