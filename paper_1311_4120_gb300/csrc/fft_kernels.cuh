@@ -45,9 +45,10 @@ __host__ __device__ constexpr int fft_pprod(int n, int s) {  // product of the r
 constexpr int FFT_VPT0 = 16, FFT_MINB0 = 0;                 // column passes
 constexpr int FFT_VPT1 = 16, FFT_MINB1 = 0;                 // row passes
 constexpr int FFT_PACKED_VPT = 8, FFT_PACKED_MINB = 3;      // packed real-data column passes
+constexpr int FFT_DUAL_VPT = 16, FFT_DUAL_MINB = 2;         // dual column passes (modes 6, 7)
 __host__ __device__ constexpr int fft_vpt_small(int mode) {
     return mode == 0 ? FFT_VPT0 : mode == 1 ? FFT_VPT1 : mode == 2 ? 8
-         : (mode == 3 || mode == 4) ? FFT_PACKED_VPT : 16;
+         : (mode == 3 || mode == 4) ? FFT_PACKED_VPT : (mode == 6 || mode == 7) ? FFT_DUAL_VPT : 16;
 }
 __host__ __device__ constexpr int fft_vpt(int n, int mode = 0) {
     return fft_has3(n) ? 24 : (n <= 512 ? fft_vpt_small(mode) : 32);
@@ -91,6 +92,12 @@ __host__ __device__ constexpr int fft_row_b(int n, int cs, int mode = 1) {
 // inverse FFT (the multiply of an FFT convolution fused between two transforms of one axis).
 __host__ __device__ constexpr bool fft_is_row(int mode) { return mode == 1 || mode == 2 || mode == 5; }
 __host__ __device__ constexpr bool fft_packed(int mode) { return mode == 3 || mode == 4; }
+// Modes 6 and 7: the dual column passes of Algorithm 2 along z.  6: one real input line carried
+// twice, with the unit factors (I_1) and with the deconvolution factors `fac2` (I_2), as
+// z = x1 + i x2; the half (k <= n/2) of X1 goes to the output, the window (k <= win) of X2 to
+// `out2`.  7: the Hermitian half of I_1 (input) and the window half of I_2 (`in2`) as
+// Z = X1 + i X2; the output is Re z (unit factors) + Im z times the deconvolution (+ energy).
+__host__ __device__ constexpr bool fft_dual(int mode) { return mode == 6 || mode == 7; }
 __host__ __device__ constexpr int fft_pack(int mode) { return fft_packed(mode) ? 2 : 1; }
 
 // Input and output kinds each mode is launched with (compile-time, so a single-kind mode has no
@@ -98,15 +105,15 @@ __host__ __device__ constexpr int fft_pack(int mode) { return fft_packed(mode) ?
 __host__ __device__ constexpr unsigned fft_in_mask(int mode) {
     return mode == 0 ? (1u << IN_CPLX_MODES) | (1u << IN_CPLX_FULL) | (1u << IN_CPLX_WIN)
          : mode == 2 ? (1u << IN_CPLX_FOLD)
-         : mode == 3 ? (1u << IN_REAL_MODES)
-         : mode == 4 ? (1u << IN_CPLX_HERM)
+         : (mode == 3 || mode == 6) ? (1u << IN_REAL_MODES)
+         : (mode == 4 || mode == 7) ? (1u << IN_CPLX_HERM)
                      : (1u << IN_CPLX_MODES);  // 1, 5
 }
 __host__ __device__ constexpr unsigned fft_out_mask(int mode) {
     return mode == 0 ? (1u << OUT_CPLX_FULL) | (1u << OUT_CPLX_MODES) | (1u << OUT_CPLX_WIN)
          : mode == 1 ? (1u << OUT_CPLX_FULL)
-         : mode == 3 ? (1u << OUT_CPLX_HALF)
-         : mode == 4 ? (1u << OUT_REAL_MODES)
+         : (mode == 3 || mode == 6) ? (1u << OUT_CPLX_HALF)
+         : (mode == 4 || mode == 7) ? (1u << OUT_REAL_MODES)
                      : (1u << OUT_CPLX_MODES);  // 2, 5
 }
 
@@ -121,6 +128,7 @@ struct FftCfg {
     // packed passes hold two lines' loads in flight: ask for two resident CTAs of 512 threads
     static constexpr bool F32_512 = THREADS == 512 && NF <= 512 && sizeof(T) == 4;
     static constexpr int MIN_BLOCKS = (fft_packed(MODE) && F32_512) ? FFT_PACKED_MINB
+                                    : (fft_dual(MODE) && F32_512) ? FFT_DUAL_MINB
                                     : (MODE == 0 && F32_512) ? FFT_MINB0
                                     : (MODE == 1 && F32_512) ? FFT_MINB1
                                     : (MODE == 5 && NF <= 512 && sizeof(T) == 4) ? 3 : 0;
@@ -224,7 +232,8 @@ struct LineIO {
 // ------------------------------------------------------------------ the pass kernel
 // MODE 0: column pass, the CTA's B lines are adjacent in memory (128-byte rows);
 // MODE 1, 2: row pass, each line is contiguous (B lines per CTA);
-// MODE 3, 4: column pass with two data columns per FFT line (2B adjacent columns per CTA).
+// MODE 3, 4: column pass with two data columns per FFT line (2B adjacent columns per CTA);
+// MODE 6, 7: column pass with two transforms of one data column per FFT line (B columns).
 template <typename T, int NF, int MODE>
 __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MODE>::MIN_BLOCKS) fft_pass_kernel(
     PassDesc P, const void *__restrict__ vin, void *__restrict__ vout, const cx_t<T> *__restrict__ tw) {
@@ -232,6 +241,8 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MO
     using C = FftCfg<T, NF, MODE>;
     constexpr bool ROW = fft_is_row(MODE);
     constexpr bool PACK = fft_packed(MODE);
+    constexpr bool DUAL = fft_dual(MODE);
+    constexpr bool NATURAL = PACK || DUAL;  // last stage leaves z in natural order for an epilogue
     constexpr int B = C::B;
     constexpr int TPL = C::TPL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -284,6 +295,15 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MO
             io2.out_base = io.out_base + B;
             io2.bfac = io2.valid ? ((P.dim == 3) ? fac[i2 / N] * fac[i2 % N] : fac[i2]) : T(1);
         }
+        if constexpr (DUAL) {  // the same column: I_1 (io, no window) and I_2 (io2: fac2, window)
+            const T *fac2 = reinterpret_cast<const T *>(P.fac2);
+            io.win = 0;
+            io2.fac = fac2;
+            io2.valid = io.valid;
+            io2.in_base = io.in_base;
+            io2.out_base = io.out_base;
+            io2.bfac = io2.valid ? ((P.dim == 3) ? fac2[i / N] * fac2[i % N] : fac2[i]) : T(1);
+        }
     } else {
         const int64_t q = (int64_t)blockIdx.x * B + ll;
         io.valid = q < P.I;
@@ -329,8 +349,11 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MO
 #pragma unroll
             for (int r = 0; r < R; r++) {
                 const int e = t + b * TPL + r * NB;
-                if constexpr (MODE == 3) {  // z = x + i y from two real columns
+                if constexpr (MODE == 3 || MODE == 6) {  // z = x + i y from two real lines
                     v[b][r] = cmake<T2>(io.template load<KM>(e, vin).x, io2.template load<KM>(e, vin).x);
+                } else if constexpr (MODE == 7) {  // Z = X1 + i X2, X2 from the second input
+                    const T2 X = io.template load<KM>(e, vin), Y = io2.template load<KM>(e, P.in2);
+                    v[b][r] = cmake<T2>(X.x - Y.y, X.y + Y.x);
                 } else if constexpr (MODE == 4) {  // Z = X + i Y from two Hermitian columns
                     const T2 X = io.template load<KM>(e, vin), Y = io2.template load<KM>(e, vin);
                     v[b][r] = cmake<T2>(X.x - Y.y, X.y + Y.x);
@@ -382,7 +405,7 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MO
         for (int b = 0; b < MB; b++)
 #pragma unroll
             for (int r = 0; r < R; r++) v[b][r] = buf[sidx(t + b * TPL + r * NB)];
-        if (!LAST || PACK || (MODE == 5 && sgn < 0)) __syncthreads();
+        if (!LAST || NATURAL || (MODE == 5 && sgn < 0)) __syncthreads();
 #pragma unroll
         for (int b = 0; b < MB; b++) {
             const int i = t + b * TPL;
@@ -398,7 +421,7 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MO
                 const int j = (i - k) * R + k;
 #pragma unroll
                 for (int r = 0; r < R; r++) buf[sidx(j + r * PP)] = v[b][r];
-            } else if constexpr (PACK) {  // z in natural order for the epilogue below
+            } else if constexpr (NATURAL) {  // z in natural order for the epilogue below
 #pragma unroll
                 for (int r = 0; r < R; r++) buf[sidx(i + r * PP)] = v[b][r];
             } else if (MODE == 5 && sgn < 0) {  // spectrum times the multiplier row, natural order
@@ -495,6 +518,35 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MO
             }
         }
     }
+    if constexpr (MODE == 7) {  // u = Re z (I_1, unit factors) + Im z times I_2's deconvolution
+        __syncthreads();
+        const T *fac2 = reinterpret_cast<const T *>(P.fac2);
+        const T *rho = reinterpret_cast<const T *>(P.rho);
+#pragma unroll 4
+        for (int a = t; a < N; a += TPL) {
+            const int m = a - h;
+            const T2 z = buf[sidx(m < 0 ? m + NF : m)];
+            if (io.valid) {
+                const int64_t idx = io.out_base + a * io.out_st;
+                const T val = z.x + z.y * fac2[a] * io2.bfac;
+                reinterpret_cast<T *>(vout)[idx] = val;
+                if (rho) eacc.add(val, rho[idx]);
+            }
+        }
+    }
+    if constexpr (MODE == 6) {  // X1 (half) to the output, X2 (window) to out2
+        __syncthreads();
+        for (int k = t; k <= NF / 2; k += TPL) {
+            const T2 zk = buf[sidx(k)], zn = buf[sidx(k == 0 ? 0 : NF - k)];
+            if (io.valid) {
+                reinterpret_cast<T2 *>(vout)[io.out_base + k * io.out_st] =
+                    cmake<T2>(T(0.5) * (zk.x + zn.x), T(0.5) * (zk.y - zn.y));
+                if (k <= P.win)
+                    reinterpret_cast<T2 *>(P.out2)[io.out_base + k * io.out_st] =
+                        cmake<T2>(T(0.5) * (zk.y + zn.y), T(0.5) * (zn.x - zk.x));
+            }
+        }
+    }
     if constexpr (MODE == 3) {  // X(k) = (Z(k) + conj Z(n-k)) / 2, Y(k) = (Z(k) - conj Z(n-k)) / 2i
         __syncthreads();
         const int klim = P.win > 0 ? P.win : NF / 2;  // OUT_CPLX_HALF (within the window)
@@ -509,7 +561,7 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MO
         }
     }
 
-    if (P.out_kind == OUT_REAL_MODES && P.partials) {
+    if (P.out_kind == OUT_REAL_MODES && P.partials) {  // (modes 4, 7 and the column passes)
         __syncthreads();  // the shared buffer becomes the reduction scratch
         const double2 tot = energy_block_sum(eacc, reinterpret_cast<double *>(smem_raw));
         if (threadIdx.x == 0) P.partials[blockIdx.x] = tot;
@@ -521,6 +573,8 @@ template <typename T, int NF, int MODE>
 cudaError_t launch_nf(const PassDesc &p, const void *in, void *out, const void *tw, cudaStream_t s) {
     if (!(fft_in_mask(MODE) & (1u << p.in_kind)) || !(fft_out_mask(MODE) & (1u << p.out_kind)))
         return cudaErrorInvalidValue;  // a pass descriptor this mode was not compiled for
+    if (fft_dual(MODE) && (!p.fac2 || (MODE == 6 ? !p.out2 : !p.in2) || p.win <= 0 || p.win > NF / 2))
+        return cudaErrorInvalidValue;  // a dual pass needs its second factors, buffer and window
     const size_t smem = pass_smem(p, sizeof(T) == 4 ? NLINT_FP32 : NLINT_FP64);
     cudaError_t e = cudaFuncSetAttribute(fft_pass_kernel<T, NF, MODE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -4,7 +4,7 @@
 
 namespace nlint {
 
-// the kernels are instantiated in fft_{f32,f64}_{col,row}.cu
+// the kernels are instantiated in fft_{f32,f64}_{col,row,colp,conv,dual}.cu
 extern template cudaError_t launch_pass_mode<float, 0>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
 extern template cudaError_t launch_pass_mode<float, 1>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
 extern template cudaError_t launch_pass_mode<float, 2>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
@@ -17,9 +17,14 @@ extern template cudaError_t launch_pass_mode<double, 3>(const PassDesc &, const 
 extern template cudaError_t launch_pass_mode<double, 4>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
 extern template cudaError_t launch_pass_mode<float, 5>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
 extern template cudaError_t launch_pass_mode<double, 5>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
+extern template cudaError_t launch_pass_mode<float, 6>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
+extern template cudaError_t launch_pass_mode<float, 7>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
+extern template cudaError_t launch_pass_mode<double, 6>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
+extern template cudaError_t launch_pass_mode<double, 7>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
 
 int pass_mode(const PassDesc &p, bool row) {
     if (!row) {
+        if (p.dual) return p.in_kind == IN_REAL_MODES ? 6 : 7;
         if (p.in_kind == IN_REAL_MODES && p.out_kind == OUT_CPLX_HALF) return 3;
         if (p.in_kind == IN_CPLX_HERM && p.out_kind == OUT_REAL_MODES) return 4;
         return 0;
@@ -88,6 +93,8 @@ cudaError_t launch_colpass(const PassDesc &p, const void *in, void *out, const v
     switch (pass_mode(p, false)) {
         case 3: return launch_pass_mode<T, 3>(p, in, out, tw, s);
         case 4: return launch_pass_mode<T, 4>(p, in, out, tw, s);
+        case 6: return launch_pass_mode<T, 6>(p, in, out, tw, s);
+        case 7: return launch_pass_mode<T, 7>(p, in, out, tw, s);
         default: return launch_pass_mode<T, 0>(p, in, out, tw, s);
     }
 }

@@ -67,6 +67,15 @@ struct PassDesc {
     // row pass that convolves each line (mode 5): forward FFT of the N input modes, times the
     // real n-entry row `mult` + q n, inverse FFT, N output modes
     int conv;
+    // dual column pass (modes 6, 7) of two transforms that share the density and u: I_1 with the
+    // unit factors `fac` and I_2 with the deconvolution factors `fac2` over the window `win`.
+    // Forward (IN_REAL_MODES -> OUT_CPLX_HALF): I_1's half to the output, I_2's window planes
+    // (e <= win, same strides) to `out2`.  Inverse (IN_CPLX_HERM -> OUT_REAL_MODES): I_1's half
+    // from the input, I_2's window planes from `in2`, u = the sum of the two (+ energy).
+    int dual;
+    const void *fac2;
+    const void *in2;
+    void *out2;
 };
 
 void make_radix(int n, PassDesc &p);
@@ -80,7 +89,7 @@ bool pass_fits(const PassDesc &p);
 
 // pass mode 0: column pass; 1: row pass; 2: row pass reading the fold input;
 // 3: column pass real -> Hermitian half, two lines per FFT; 4: Hermitian half -> real, two lines;
-// 5: row pass forward FFT, multiply, inverse FFT
+// 5: row pass forward FFT, multiply, inverse FFT; 6, 7: dual column passes (forward, inverse)
 int pass_mode(const PassDesc &p, bool row);
 template <typename T, int MODE>
 cudaError_t launch_pass_mode(const PassDesc &p, const void *in, void *out, const void *tw,

@@ -150,6 +150,12 @@ struct nlint_plan_s {
     int win = 0;
     size_t bytes_Hwin = 0;  // the planes of the spread grid the window touches
     nlint::PassDesc P1w, P2w, P3w, Q1w, Q2w, Q3w;
+    // dual z passes shared by I_1 and I_2 (the first forward one reads the density once for both,
+    // the last inverse one writes u once); d_win holds I_2's window planes meanwhile
+    bool dual = false;
+    nlint::PassDesc D6, D7;
+    void *d_win = nullptr;
+    size_t bytes_win = 0;
     // host copies for inspection (canonical order)
     std::vector<double> k_canon, W_canon;
     // stage timing
@@ -244,7 +250,7 @@ static int upload(void **dst, const std::vector<double> &v, size_t &acc) {
 static void plan_free(nlint_plan_s *p) {
     void *ptrs[] = {p->d_rel, p->d_ker, p->d_W, p->d_fac, p->d_tw, p->d_perm, p->d_mirror,
                     p->d_subs, p->d_bins, p->d_crowd_bin, p->d_crowd, p->d_pairs, p->d_pairs_i, p->d_epart, p->d_fac1, p->d_khat,
-                    p->d_bufA, p->d_bufB, p->d_bufG, p->d_c, p->d_partials, p->d_E,
+                    p->d_win, p->d_bufA, p->d_bufB, p->d_bufG, p->d_c, p->d_partials, p->d_E,
                     p->d_rho_io, p->d_u_io};
     for (void *q : ptrs)
         if (q) cudaFree(q);
@@ -820,12 +826,29 @@ static void alg2_window(nlint_plan_s *p) {
     config_pass(p->Q3w, p->prec, false);
     if (pass_blocks(p->Q3w, false) > p->n_partials) return;  // (same grid as Q3: never)
     p->win = win;
+    // the dual z passes (I_1 with unit factors, I_2 with the deconvolution) when their grid fits
+    // the energy partials
+    auto dual = [&](PassDesc &dst, const PassDesc &src) {
+        dst = src;
+        dst.dual = 1;
+        dst.fac = p->d_fac1;
+        dst.fac2 = p->d_fac;
+        config_pass(dst, p->prec, false);
+    };
+    dual(p->D6, p->P1w);
+    dual(p->D7, p->Q3w);
+    p->bytes_win = (size_t)(win + 1) * (d == 3 ? N * N : N) * cs;
+    p->dual = pass_fits(p->D6) && pass_fits(p->D7) && pass_blocks(p->D7, false) <= p->n_partials;
 }
 
 static int alg2_setup(nlint_plan_s *p) {
     int rc = upload_ones(p);
     if (rc) return rc;
     alg2_window(p);
+    if (p->win > 0 && p->dual) {
+        CK(cudaMalloc(&p->d_win, p->bytes_win));
+        p->ws_bytes += p->bytes_win;
+    }
     p->ws_bytes += (size_t)std::max<int64_t>(p->N, p->n_fine) * (p->prec == NLINT_FP32 ? 4 : 8);
     rc = p->prec == NLINT_FP32 ? alg2_fill_multiplier<float>(p) : alg2_fill_multiplier<double>(p);
     if (rc) return rc;
@@ -978,6 +1001,67 @@ static int run_toeplitz(nlint_plan_s *p, const void *rho, void *u, double lambda
     return NLINT_OK;
 }
 
+// Algorithm 2 with I_2 on its frequency window and the z passes of both integrals shared: one
+// forward z pass reads rho once and writes I_1's half grid (bufA) and I_2's window planes
+// (d_win); I_2's remaining passes and the NUFFT run on the window, then I_1's y / x-convolution
+// / y passes; one inverse z pass forms u = I_1 + I_2 and the energy products.
+template <typename T>
+static int run_alg2_dual(nlint_plan_s *p, const void *rho, void *u, double lambda, double *E,
+                         cudaStream_t s) {
+    PassDesc d6 = p->D6;
+    d6.out2 = p->d_win;
+    CK(launch_colpass<T>(d6, rho, p->d_bufA, p->d_tw, s));
+    stage_mark(p, s, "dual_fwd_z");
+    if (p->d == 3) {
+        CK(launch_colpass<T>(p->P2w, p->d_win, p->d_bufB, p->d_tw, s));
+        CK(launch_rowpass<T>(p->P3w, p->d_bufB, p->d_bufG, p->d_tw, s));
+    } else {
+        CK(launch_rowpass<T>(p->P3w, p->d_win, p->d_bufG, p->d_tw, s));
+    }
+    stage_mark(p, s, "I2_fwd_fft");
+    CK(launch_interp<T>(node_desc(p), p->d_bufG, p->d_c, 1, s));
+    stage_mark(p, s, "interp");
+    CK(cudaMemsetAsync(p->d_bufG, 0, p->bytes_Hwin, s));
+    if (p->ncrowd) CK(cudaMemsetAsync(p->d_crowd, 0, p->bytes_crowd, s));
+    CK(launch_spread<T>(node_desc(p), p->d_c, p->d_bufG, s));
+    if (p->ncrowd) {
+        CK(launch_crowd_merge<T>(node_desc(p), p->d_bufG, s));
+        p->launches += 1;
+    }
+    stage_mark(p, s, "spread");
+    if (p->d == 3) {
+        CK(launch_rowpass<T>(p->Q1w, p->d_bufG, p->d_bufB, p->d_tw, s));
+        CK(launch_colpass<T>(p->Q2w, p->d_bufB, p->d_win, p->d_tw, s));
+    } else {
+        CK(launch_rowpass<T>(p->Q1w, p->d_bufG, p->d_win, p->d_tw, s));
+    }
+    stage_mark(p, s, "I2_inv_fft");
+    const void *half1;  // I_1's inverse-transformed half grid, before the last z pass
+    if (p->d == 3) {
+        CK(launch_colpass<T>(p->P2, p->d_bufA, p->d_bufB, p->d_tw, s));
+        CK(launch_rowpass<T>(p->X, p->d_bufB, p->d_bufG, p->d_tw, s));  // x: FFT, M, IFFT
+        CK(launch_colpass<T>(p->Q2, p->d_bufG, p->d_bufA, p->d_tw, s));
+        half1 = p->d_bufA;
+    } else {
+        CK(launch_rowpass<T>(p->X, p->d_bufA, p->d_bufG, p->d_tw, s));
+        half1 = p->d_bufG;
+    }
+    stage_mark(p, s, "I1_fft_conv");
+    PassDesc d7 = p->D7;
+    d7.in2 = p->d_win;
+    d7.rho = E ? rho : nullptr;
+    d7.partials = E ? p->d_partials : nullptr;
+    CK(launch_colpass<T>(d7, half1, u, p->d_tw, s));
+    stage_mark(p, s, "dual_inv_z");
+    p->launches += (p->d == 3) ? 11 : 7;
+    if (E) {
+        CK(launch_energy_final(p->d_partials, p->n_partials, 0.5 * lambda * std::pow(p->h, p->d), E, s));
+        p->launches += energy_final_kernels(p->n_partials);
+        stage_mark(p, s, "energy");
+    }
+    return NLINT_OK;
+}
+
 // Algorithm 2 (Section 3.3, eq. 3.9): u = I_1 + I_2.  I_1 (step 3): zero-padded forward FFT of
 // rho on the fine grid, multiply by U_hat (1 - p) (between the forward and inverse x transforms
 // of one row pass), inverse FFT, crop -> u.  I_2 (step 4): the NUFFT path on I_2's nodes (weights W_j p(k_j)), its last
@@ -987,6 +1071,7 @@ static int run_alg2(nlint_plan_s *p, const void *rho, void *u, double lambda, do
                     cudaStream_t s) {
     p->ev_used = 0;
     stage_mark(p, s, "start");
+    if (p->win > 0 && p->dual) return run_alg2_dual<T>(p, rho, u, lambda, E, s);
     CK(launch_colpass<T>(p->T1, rho, p->d_bufA, p->d_tw, s));
     if (p->d == 3) {
         CK(launch_colpass<T>(p->P2, p->d_bufA, p->d_bufB, p->d_tw, s));
