@@ -27,6 +27,10 @@
  *     They must stay valid until the work queued on `stream` has finished.
  *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Work
  *     is queued on it; nothing synchronises the host unless a host output is requested.
+ *     An Algorithm 1 plan clears its spreading grid on an internal stream while the
+ *     interpolation runs: that work is forked from `stream` (after everything queued on it)
+ *     and joined back before the spreading, by events, so the evaluation stays ordered on
+ *     `stream` and can be captured into a CUDA graph.
  *   - Return value: NLINT_OK or a negative status; nlint_last_error() then returns a
  *     message for the calling thread.  No C++ exception crosses this interface.
  *   - A plan is not re-entrant: one evaluation at a time per plan (its workspaces are

@@ -129,6 +129,11 @@ struct nlint_plan_s {
     int ncrowd = 0;
     size_t bytes_crowd = 0;
     void *d_bufA = nullptr, *d_bufB = nullptr, *d_bufG = nullptr, *d_c = nullptr;
+    // Algorithm 1: the spread grid in its own buffer, cleared on a side stream while the
+    // interpolation runs (NULL: the spreading clears d_bufG in stream order)
+    void *d_bufH = nullptr;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_zero = nullptr;
     double2 *d_partials = nullptr;
     double *d_E = nullptr;
     void *d_rho_io = nullptr, *d_u_io = nullptr;  // nlint_eval_host staging
@@ -250,11 +255,14 @@ static int upload(void **dst, const std::vector<double> &v, size_t &acc) {
 static void plan_free(nlint_plan_s *p) {
     void *ptrs[] = {p->d_rel, p->d_ker, p->d_W, p->d_fac, p->d_tw, p->d_perm, p->d_mirror,
                     p->d_subs, p->d_bins, p->d_crowd_bin, p->d_crowd, p->d_pairs, p->d_pairs_i, p->d_epart, p->d_fac1, p->d_khat,
-                    p->d_win, p->d_bufA, p->d_bufB, p->d_bufG, p->d_c, p->d_partials, p->d_E,
+                    p->d_win, p->d_bufA, p->d_bufB, p->d_bufG, p->d_bufH, p->d_c, p->d_partials, p->d_E,
                     p->d_rho_io, p->d_u_io};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    if (p->ev_zero) cudaEventDestroy(p->ev_zero);
+    if (p->side) cudaStreamDestroy(p->side);
 }
 
 static int alg2_setup(nlint_plan_s *p);
@@ -684,6 +692,18 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
     CK(cudaMalloc((void **)&p->d_E, sizeof(double)));
     acc += p->bytes_A + p->bytes_B + std::max(p->bytes_G, p->bytes_Hext) + p->bytes_c +
            sizeof(double2) * (size_t)std::max(p->n_partials, 1024);
+    if (p->algorithm == 1) {
+        // a separate spread grid when memory allows (else the spreading reuses d_bufG)
+        if (cudaMalloc(&p->d_bufH, p->bytes_Hext) == cudaSuccess) {
+            CK(cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking));
+            CK(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&p->ev_zero, cudaEventDisableTiming));
+            acc += p->bytes_Hext;
+        } else {
+            (void)cudaGetLastError();
+            p->d_bufH = nullptr;
+        }
+    }
     p->ws_bytes = acc;
     if (p->algorithm == 2) return alg2_setup(p);
     return NLINT_OK;
@@ -914,25 +934,41 @@ static NodeDesc node_desc(nlint_plan_s *p) {
     return nd;
 }
 
+// Clears the separate spread grid (and the crowd tiles) on the plan's side stream, ordered after
+// everything already on `s` (the previous evaluation's reads of the grid); run_type1 waits for it.
+static int clear_spread_grid(nlint_plan_s *p, cudaStream_t s) {
+    CK(cudaEventRecord(p->ev_fork, s));
+    CK(cudaStreamWaitEvent(p->side, p->ev_fork, 0));
+    CK(cudaMemsetAsync(p->d_bufH, 0, p->bytes_Hext, p->side));
+    if (p->ncrowd) CK(cudaMemsetAsync(p->d_crowd, 0, p->bytes_crowd, p->side));
+    CK(cudaEventRecord(p->ev_zero, p->side));
+    return NLINT_OK;
+}
+
 template <typename T>
 static int run_type1(nlint_plan_s *p, void *u, const void *rho_energy, cudaStream_t s,
                      bool accumulate = false) {
-    CK(cudaMemsetAsync(p->d_bufG, 0, p->bytes_Hext, s));
-    if (p->ncrowd) CK(cudaMemsetAsync(p->d_crowd, 0, p->bytes_crowd, s));
-    CK(launch_spread<T>(node_desc(p), p->d_c, p->d_bufG, s));
+    void *H = p->d_bufH ? p->d_bufH : p->d_bufG;
+    if (p->d_bufH) {
+        CK(cudaStreamWaitEvent(s, p->ev_zero, 0));  // cleared by clear_spread_grid
+    } else {
+        CK(cudaMemsetAsync(H, 0, p->bytes_Hext, s));
+        if (p->ncrowd) CK(cudaMemsetAsync(p->d_crowd, 0, p->bytes_crowd, s));
+    }
+    CK(launch_spread<T>(node_desc(p), p->d_c, H, s));
     if (p->ncrowd) {
-        CK(launch_crowd_merge<T>(node_desc(p), p->d_bufG, s));
+        CK(launch_crowd_merge<T>(node_desc(p), H, s));
         p->launches += 1;
     }
     p->launches += (p->d == 3) ? 4 : 3;
     stage_mark(p, s, "spread");
     if (p->d == 3) {
-        CK(launch_rowpass<T>(p->Q1, p->d_bufG, p->d_bufB, p->d_tw, s));
+        CK(launch_rowpass<T>(p->Q1, H, p->d_bufB, p->d_tw, s));
         stage_mark(p, s, "inv_fft_x");
         CK(launch_colpass<T>(p->Q2, p->d_bufB, p->d_bufA, p->d_tw, s));
         stage_mark(p, s, "inv_fft_y");
     } else {
-        CK(launch_rowpass<T>(p->Q1, p->d_bufG, p->d_bufA, p->d_tw, s));
+        CK(launch_rowpass<T>(p->Q1, H, p->d_bufA, p->d_tw, s));
         stage_mark(p, s, "inv_fft_x");
     }
     PassDesc q3 = p->Q3;
@@ -956,6 +992,7 @@ static int run_eval(nlint_plan_s *p, const void *rho, void *u, double lambda, do
     stage_mark(p, s, "start");
     int rc = run_type2<T>(p, rho, s);
     if (rc) return rc;
+    if (p->d_bufH && (rc = clear_spread_grid(p, s))) return rc;  // overlaps the interpolation
     CK(launch_interp<T>(node_desc(p), p->d_bufG, p->d_c, 1, s));
     p->launches += 1;
     stage_mark(p, s, "interp");
@@ -1501,6 +1538,7 @@ int nlint_type1(nlint_plan p, const void *c, void *u, void *stream) {
     cudaStream_t s = (cudaStream_t)stream;
     p->ev_used = 0;
     p->launches += 1;
+    if (p->d_bufH && (rc = clear_spread_grid(p, s))) return rc;
     if (p->prec == NLINT_FP32) {
         CK(launch_gather_canonical<float>(p->Mh, c, p->d_perm, p->d_mirror, p->d_c, s));
         return run_type1<float>(p, u, nullptr, s);
