@@ -263,6 +263,7 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MO
     io.win = P.win;
     io.bfac = T(1);
     int64_t mbase = 0;
+    int xl = NF;  // ball window (modes 1, 2): |signed x index| <= xl on this row, -1: none
     LineIO<T> io2;  // packed modes: the second data column of this FFT line (set field by field)
     io2.n = P.n;
     io2.h = h;
@@ -332,7 +333,24 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MO
         } else {
             io.in_base = q * P.in_so;
         }
+        if constexpr (MODE == 1 || MODE == 2) {
+            if (P.ball2 > 0) {  // block-uniform branch
+                const int64_t a0 = P.dim == 3 ? q / NF : q, a1 = P.dim == 3 ? q % NF : 0;
+                const int64_t s1 = a1 < NF / 2 ? a1 : a1 - NF;
+                const int64_t r2 = a0 * a0 + s1 * s1;
+                xl = r2 > P.ball2 ? -1 : (int)sqrtf((float)(P.ball2 - r2)) + 1;
+                if (MODE == 1 && xl < 0) io.valid = false;  // nothing to read or write
+                if (!__syncthreads_or(io.valid && xl >= 0)) {  // every row of the CTA outside
+                    if (MODE == 2 && io.valid)
+                        for (int a = t; a < N; a += TPL)
+                            reinterpret_cast<T2 *>(vout)[io.out_base + a] = czero<T2>();
+                    return;
+                }
+            }
+        }
     }
+    // entry e of a row pass inside the ball window
+    auto in_ball = [&](int e) { return (e <= NF / 2 ? e : NF - e) <= xl; };
 
     auto sidx = [&](int e) -> int { return ROW ? ll * C::ROW_LD + e + (e >> 4) : e * B + ll; };
 
@@ -358,7 +376,8 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MO
                     const T2 X = io.template load<KM>(e, vin), Y = io2.template load<KM>(e, vin);
                     v[b][r] = cmake<T2>(X.x - Y.y, X.y + Y.x);
                 } else if constexpr (MODE == 2) {  // fold: the row here, the mirror row below
-                    v[b][r] = io.valid ? reinterpret_cast<const T2 *>(vin)[io.in_base + e] : czero<T2>();
+                    v[b][r] = (io.valid && in_ball(e)) ? reinterpret_cast<const T2 *>(vin)[io.in_base + e]
+                                                       : czero<T2>();
                 } else {
                     v[b][r] = io.template load<KM>(e, vin);
                 }
@@ -372,7 +391,7 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MO
 #pragma unroll
                     for (int r = 0; r < R; r++) {
                         const int e = t + b * TPL + r * NB;
-                        m[b][r] = in[io.mirror_base + (e == 0 ? 0 : NF - e)];
+                        m[b][r] = in_ball(e) ? in[io.mirror_base + (e == 0 ? 0 : NF - e)] : czero<T2>();
                     }
 #pragma unroll
                 for (int b = 0; b < MB; b++)
@@ -440,7 +459,7 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MO
                     constexpr bool OONE = (OM & (OM - 1)) == 0;
                     auto os = [&](int k) { return (OM & (1u << k)) != 0 && (OONE || P.out_kind == k); };
                     if (os(OUT_CPLX_FULL)) {
-                        if (P.win == 0 || e <= P.win || e >= NF - P.win)
+                        if ((P.win == 0 || e <= P.win || e >= NF - P.win) && (MODE != 1 || in_ball(e)))
                             reinterpret_cast<T2 *>(vout)[io.out_base + e * io.out_st] = x;
                     } else if (os(OUT_CPLX_HALF)) {
                         if (e <= (P.win > 0 ? P.win : NF / 2))

@@ -76,6 +76,11 @@ struct PassDesc {
     const void *fac2;
     const void *in2;
     void *out2;
+    // ball window of the full row passes along x (0 = none): every fine cell a node's stencil
+    // touches has s0^2 + s1^2 + s2^2 <= ball2 (signed FFT indices), so the forward row pass
+    // (mode 1) writes, and the fold pass (mode 2) reads, only the entries of each row inside that
+    // ball (rows outside it: nothing written; the fold pass writes their zero transform)
+    int64_t ball2;
 };
 
 void make_radix(int n, PassDesc &p);

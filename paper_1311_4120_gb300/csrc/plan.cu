@@ -153,6 +153,7 @@ struct nlint_plan_s {
     // I_2's frequency window: its nodes' stencils lie within |l_a| <= win fine cells, so its
     // FFT passes transform only the window's lines (0 = the full passes P1..Q3)
     int win = 0;
+    int64_t ball2 = 0;      // ball window of the full x passes (PassDesc::ball2)
     size_t bytes_Hwin = 0;  // the planes of the spread grid the window touches
     nlint::PassDesc P1w, P2w, P3w, Q1w, Q2w, Q3w;
     // dual z passes shared by I_1 and I_2 (the first forward one reads the density once for both,
@@ -416,8 +417,10 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
     std::vector<int32_t> l0((size_t)d * Mh);
     std::vector<double> fr((size_t)d * Mh);
     int32_t lo[3] = {INT32_MAX, INT32_MAX, INT32_MAX}, hi[3] = {INT32_MIN, INT32_MIN, INT32_MIN};
+    int64_t ball2 = 0;  // max over the nodes of the squared norm of their farthest stencil cell
     for (int64_t o = 0; o < Mh; o++) {
         const int64_t j = half[o];
+        int64_t r2 = 0;
         for (int ax = 0; ax < d; ax++) {
             // array axis ax pairs with node component d-1-ax (axis 0 is k_z in 3D, k_y in 2D)
             const double g = p->k_canon[(size_t)j * d + (d - 1 - ax)] * gscale;
@@ -428,8 +431,14 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
                 return fail(NLINT_EINVAL, "internal: node stencil outside the stored half grid");
             lo[ax] = std::min(lo[ax], l);
             hi[ax] = std::max(hi[ax], l);
+            const int64_t far = std::max(std::abs((int64_t)l), std::abs((int64_t)l + w - 1));
+            r2 += far * far;
         }
+        ball2 = std::max(ball2, r2);
     }
+    // (a signed FFT index never exceeds the unwrapped cell index in magnitude, so the bound
+    // holds for the stored grid too); a ball that covers the whole grid is no window
+    p->ball2 = (ball2 < (int64_t)d * (n / 2) * (n / 2)) ? ball2 : 0;
     // bins: boxes of B[ax] stencil-origin cells starting at lo[ax]; tile = B + w - 1
     for (int ax = 0; ax < 3; ax++) {
         p->B[ax] = 1;
@@ -667,6 +676,7 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
         p->bytes_Hext = (size_t)(nh + 2 * p->pad) * n * cs;
     }
     if (p->P1.nrad < 0) return fail(NLINT_EUNSUPPORTED, "fine grid size is not 2^a 3^b");
+    p->P3.ball2 = p->Q1.ball2 = p->ball2;
     config_pass(p->P1, p->prec, false);
     config_pass(p->P3, p->prec, true);
     config_pass(p->Q1, p->prec, true);
