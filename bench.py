@@ -44,14 +44,14 @@ TOL = 1e-5                          # stated relative L-inf tolerance of the FP3
 # was taken on: a changed source reports traffic null until it is captured again.
 # Measured on the 256^3 FP32 workload (profiles/dram_traffic_c4_fp32.md).
 TRAFFIC = {
-    "interp": {"bytes": 734.5e6, "src": "0ad7ff78eca8a0ef"},
-    "spread": {"bytes": 971.5e6, "src": "0ad7ff78eca8a0ef"},
-    "fwd_fft_z": {"bytes": 150.9e6, "src": "ce144836143f685f"},
-    "fwd_fft_y": {"bytes": 342.6e6, "src": "ce144836143f685f"},
-    "fwd_fft_x": {"bytes": 745.5e6, "src": "ce144836143f685f"},
-    "inv_fft_x": {"bytes": 794.6e6, "src": "ce144836143f685f"},
-    "inv_fft_y": {"bytes": 370.0e6, "src": "ce144836143f685f"},
-    "inv_fft_z": {"bytes": 247.7e6, "src": "ce144836143f685f"},
+    "interp": {"bytes": 734.6e6, "src": "0ad7ff78eca8a0ef"},
+    "spread": {"bytes": 971.2e6, "src": "0ad7ff78eca8a0ef"},
+    "fwd_fft_z": {"bytes": 150.7e6, "src": "9a1960e7cd364c8e"},
+    "fwd_fft_y": {"bytes": 342.9e6, "src": "9a1960e7cd364c8e"},
+    "fwd_fft_x": {"bytes": 482.4e6, "src": "9a1960e7cd364c8e"},
+    "inv_fft_x": {"bytes": 530.4e6, "src": "9a1960e7cd364c8e"},
+    "inv_fft_y": {"bytes": 369.8e6, "src": "9a1960e7cd364c8e"},
+    "inv_fft_z": {"bytes": 247.5e6, "src": "9a1960e7cd364c8e"},
 }
 
 
