@@ -424,22 +424,33 @@ def run_ours(args, rank, world, local_rank):
     E32 = float(E.item())
     u32 = u.clone()
 
-    # ---- end to end through the host-buffer entry point (pinned host memory)
-    rho_h = torch.from_numpy(rho_np).pin_memory()
-    u_h = torch.empty(rho_h.shape, dtype=torch.float32).pin_memory()
+    # ---- end to end through the host-buffer entry points (pinned host memory): the streaming
+    # entry point (copies of step k+1's density and step k-1's u overlapped with step k's
+    # evaluation) is the e2e value; one synchronous call per step is reported beside it
+    rho_h = [torch.from_numpy(rho_np).pin_memory() for _ in range(2)]
+    u_h = [torch.empty(rho_h[0].shape, dtype=torch.float32).pin_memory() for _ in range(2)]
+    rhos_k = [rho_h[k % 2] for k in range(args.steps)]
+    us_k = [u_h[k % 2] for k in range(args.steps)]
+    plan.eval_host_many(rhos_k[:2], lam=wl.lam, us_host=us_k[:2])
     for _ in range(2):
-        plan.eval_host(rho_h, lam=wl.lam, u_host=u_h)
+        plan.eval_host(rho_h[0], lam=wl.lam, u_host=u_h[0])
+    barrier()
+    t0 = time.perf_counter()
+    plan.eval_host_many(rhos_k, lam=wl.lam, us_host=us_k)
+    t_e2e = time.perf_counter() - t0
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        plan.eval_host(rho_h, lam=wl.lam, u_host=u_h)
-    t_e2e = time.perf_counter() - t0
+        plan.eval_host(rho_h[0], lam=wl.lam, u_host=u_h[0])
+    t_sync = time.perf_counter() - t0
     if world > 1:
-        tt = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
+        tt = torch.tensor([t_e2e, t_sync], dtype=torch.float64, device=dev)
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_e2e = float(tt.item())
+        t_e2e, t_sync = float(tt[0].item()), float(tt[1].item())
     e2e = {"value": points / t_e2e, "unit": UNIT, "h2d_bytes_per_step": rho_np.nbytes,
-           "d2h_bytes_per_step": rho_np.nbytes + 8}
+           "d2h_bytes_per_step": rho_np.nbytes + 8,
+           "api": "nlint_eval_host_many: K steps in one call, copies overlapped with evaluations",
+           "one_call_per_step": {"api": "nlint_eval_host (synchronous)", "value": points / t_sync}}
 
     # ---- the same operator in its precomputed Toeplitz form (FFT passes only per evaluation)
     toep = None

@@ -172,6 +172,21 @@ int nlint_eval_toeplitz(nlint_plan plan, const void *rho_dev, void *u_dev, doubl
 int nlint_eval_host(nlint_plan plan, const void *rho_host, void *u_host, double lambda,
                     double *E_host, void *stream);
 
+/* Streaming form of nlint_eval_host for many densities: evaluates rho_host[k] -> u_host[k]
+ * and E_host[k] for k < count (each array n^d values of the plan's precision in host memory;
+ * E_host may be NULL: no energies), overlapping the copies with the evaluations.  The copy of
+ * density k+1 to the device and the copy of u_{k-1} back to the host run on two plan-owned
+ * streams while density k is evaluated on `stream`, through two device staging buffers each
+ * way; events order every copy against the evaluations that use its buffer.  The copies are
+ * forked from `stream` after the work already queued on it, and the call returns after every
+ * copy has finished (it synchronises `stream`).  Pinned host memory lets the copies overlap;
+ * pageable memory gives the same results with serialised copies.  Each u_host[k], E_host[k]
+ * equals what nlint_eval_host gives for rho_host[k].  The paper has no counterpart: it is the
+ * serving form of the same evaluation.  Errors: NLINT_EINVAL (count <= 0, NULL arrays or
+ * entries), NLINT_ENOMEM, NLINT_ECUDA. */
+int nlint_eval_host_many(nlint_plan plan, int count, const void *const *rho_host,
+                         void *const *u_host, double lambda, double *E_host, void *stream);
+
 /* Stage entry points.  nlint_type2: rho (n^d reals) -> rho_hat_dev (n_nodes complex, the
  * canonical node order, eq. 3.2).  nlint_type1: c_dev (n_nodes complex, canonical order)
  * -> u_dev = Re sum_j c_j exp(+i k_j . x) (eq. 3.7 with c_j in place of W_j rho_hat_j).

@@ -27,6 +27,7 @@ STATUS = {0: "NLINT_OK", -1: "NLINT_EINVAL", -2: "NLINT_ENOMEM", -3: "NLINT_ECUD
 EXPORTED = [
     "nlint_params_default", "nlint_plan_create", "nlint_plan_create_ex", "nlint_plan_info",
     "nlint_plan_destroy", "nlint_eval", "nlint_eval_energy", "nlint_energy", "nlint_eval_host",
+    "nlint_eval_host_many",
     "nlint_type2", "nlint_type1", "nlint_plan_nodes", "nlint_set_stage_timing",
     "nlint_stage_times", "nlint_launch_count", "nlint_energy_noalloc", "nlint_batch_create",
     "nlint_batch_eval", "nlint_batch_info", "nlint_batch_destroy", "nlint_autotune",
@@ -97,6 +98,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.nlint_eval_energy.argtypes = [vp, vp, vp, dbl, vp, vp]
     lib.nlint_energy.argtypes = [vp, vp, vp, dbl, vp, ctypes.POINTER(dbl), vp]
     lib.nlint_eval_host.argtypes = [vp, vp, vp, dbl, ctypes.POINTER(dbl), vp]
+    lib.nlint_eval_host_many.argtypes = [vp, ci, ctypes.POINTER(vp), ctypes.POINTER(vp), dbl,
+                                         ctypes.POINTER(dbl), vp]
     lib.nlint_type2.argtypes = [vp, vp, vp, vp]
     lib.nlint_type1.argtypes = [vp, vp, vp, vp]
     lib.nlint_plan_nodes.argtypes = [vp, vp, vp]
@@ -329,6 +332,35 @@ class Plan:
         _check(self._lib.nlint_eval_host(self._h, rho_host.data_ptr(), u.data_ptr(), float(lam),
                                          ctypes.byref(Eh), _stream_ptr(stream)))
         return u, Eh.value
+
+    def _host(self, a, name):
+        torch = _torch()
+        if isinstance(a, np.ndarray):
+            a = torch.from_numpy(np.ascontiguousarray(a))
+        if a.is_cuda or a.dtype != self.dtype or tuple(a.shape) != self.grid_shape or not a.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous CPU array of the plan's dtype and grid shape")
+        return a
+
+    def eval_host_many(self, rhos_host, lam: float = 1.0, us_host=None, energies: bool = True,
+                       stream=None):
+        """Many densities from host buffers, copies overlapped with the evaluations (pinned host
+        memory is best).  Returns (list of u host tensors, list of E or None)."""
+        torch = _torch()
+        rhos = [self._host(r, "rho_host") for r in rhos_host]
+        if not rhos:
+            raise ValueError("rhos_host is empty")
+        us = (list(us_host) if us_host is not None
+              else [torch.empty(self.grid_shape, dtype=self.dtype) for _ in rhos])
+        if len(us) != len(rhos):
+            raise ValueError("us_host must have one array per density")
+        us = [self._host(u, "u_host") for u in us]
+        vp = ctypes.c_void_p
+        rp = (vp * len(rhos))(*[r.data_ptr() for r in rhos])
+        up = (vp * len(us))(*[u.data_ptr() for u in us])
+        E = (ctypes.c_double * len(rhos))() if energies else None
+        _check(self._lib.nlint_eval_host_many(self._h, len(rhos), rp, up, float(lam),
+                                              E if energies else None, _stream_ptr(stream)))
+        return us, (list(E) if energies else None)
 
     def type2(self, rho, out=None, stream=None):
         torch = _torch()

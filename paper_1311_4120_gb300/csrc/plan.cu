@@ -137,6 +137,13 @@ struct nlint_plan_s {
     double2 *d_partials = nullptr;
     double *d_E = nullptr;
     void *d_rho_io = nullptr, *d_u_io = nullptr;  // nlint_eval_host staging
+    // nlint_eval_host_many: two staging buffers each way, a copy-in and a copy-out stream, the
+    // events that order them against the evaluations, and the energies on the device
+    void *d_rho_st[2] = {nullptr, nullptr}, *d_u_st[2] = {nullptr, nullptr};
+    double *d_Em = nullptr;
+    int64_t nEm = 0;
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    cudaEvent_t ev_io[7] = {};  // in[2], comp[2], out[2], fork/join
     int n_partials = 0;
     size_t bytes_A = 0, bytes_B = 0, bytes_G = 0, bytes_Hext = 0, bytes_c = 0;
     size_t ws_bytes = 0;
@@ -257,13 +264,18 @@ static void plan_free(nlint_plan_s *p) {
     void *ptrs[] = {p->d_rel, p->d_ker, p->d_W, p->d_fac, p->d_tw, p->d_perm, p->d_mirror,
                     p->d_subs, p->d_bins, p->d_crowd_bin, p->d_crowd, p->d_pairs, p->d_pairs_i, p->d_epart, p->d_fac1, p->d_khat,
                     p->d_win, p->d_bufA, p->d_bufB, p->d_bufG, p->d_bufH, p->d_c, p->d_partials, p->d_E,
-                    p->d_rho_io, p->d_u_io};
+                    p->d_rho_io, p->d_u_io, p->d_rho_st[0], p->d_rho_st[1], p->d_u_st[0],
+                    p->d_u_st[1], p->d_Em};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
     if (p->ev_fork) cudaEventDestroy(p->ev_fork);
     if (p->ev_zero) cudaEventDestroy(p->ev_zero);
     if (p->side) cudaStreamDestroy(p->side);
+    for (cudaEvent_t e : p->ev_io)
+        if (e) cudaEventDestroy(e);
+    if (p->s_in) cudaStreamDestroy(p->s_in);
+    if (p->s_out) cudaStreamDestroy(p->s_out);
 }
 
 static int alg2_setup(nlint_plan_s *p);
@@ -1516,6 +1528,66 @@ int nlint_eval_host(nlint_plan p, const void *rho_host, void *u_host, double lam
     if (rc) return rc;
     CK(cudaMemcpyAsync(u_host, p->d_u_io, bytes, cudaMemcpyDeviceToHost, s));
     if (E_host) CK(cudaMemcpyAsync(E_host, p->d_E, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return NLINT_OK;
+}
+
+int nlint_eval_host_many(nlint_plan p, int count, const void *const *rho_host, void *const *u_host,
+                         double lambda, double *E_host, void *stream) {
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (count <= 0 || !rho_host || !u_host)
+        return fail(NLINT_EINVAL, "count must be positive and rho_host, u_host non-NULL");
+    for (int k = 0; k < count; k++)
+        if (!rho_host[k] || !u_host[k]) return fail(NLINT_EINVAL, "NULL rho_host[k] or u_host[k]");
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t cells = 1;
+    for (int a = 0; a < p->d; a++) cells *= p->N;
+    const size_t bytes = (size_t)cells * (p->prec == NLINT_FP32 ? 4 : 8);
+    if (!p->s_in) {
+        CK(cudaStreamCreateWithFlags(&p->s_in, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&p->s_out, cudaStreamNonBlocking));
+        for (cudaEvent_t &e : p->ev_io) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    for (int b = 0; b < 2; b++) {
+        if (!p->d_rho_st[b]) CK(cudaMalloc(&p->d_rho_st[b], bytes));
+        if (!p->d_u_st[b]) CK(cudaMalloc(&p->d_u_st[b], bytes));
+    }
+    if (E_host && p->nEm < count) {
+        if (p->d_Em) CK(cudaFree(p->d_Em));
+        p->d_Em = nullptr;
+        p->nEm = 0;
+        CK(cudaMalloc((void **)&p->d_Em, sizeof(double) * (size_t)count));
+        p->nEm = count;
+    }
+    cudaEvent_t *ev_in = p->ev_io, *ev_comp = p->ev_io + 2, *ev_out = p->ev_io + 4, ev_fj = p->ev_io[6];
+    CK(cudaEventRecord(ev_fj, s));  // the copies follow the work already queued on `stream`
+    CK(cudaStreamWaitEvent(p->s_in, ev_fj, 0));
+    CK(cudaStreamWaitEvent(p->s_out, ev_fj, 0));
+    for (int k = 0; k < count; k++) {
+        const int b = k & 1;
+        // density k into staging buffer b, once evaluation k-2 (the last reader of b) is done
+        CK(cudaStreamWaitEvent(p->s_in, ev_comp[b], 0));
+        CK(cudaMemcpyAsync(p->d_rho_st[b], rho_host[k], bytes, cudaMemcpyHostToDevice, p->s_in));
+        CK(cudaEventRecord(ev_in[b], p->s_in));
+        // evaluation k, once its density has arrived and u_{k-2} has left staging buffer b
+        CK(cudaStreamWaitEvent(s, ev_in[b], 0));
+        CK(cudaStreamWaitEvent(s, ev_out[b], 0));
+        double *E = E_host ? p->d_Em + k : nullptr;
+        rc = p->prec == NLINT_FP32 ? run_eval<float>(p, p->d_rho_st[b], p->d_u_st[b], lambda, E, s)
+                                   : run_eval<double>(p, p->d_rho_st[b], p->d_u_st[b], lambda, E, s);
+        if (rc) return rc;
+        CK(cudaEventRecord(ev_comp[b], s));
+        // u_k back to the host while evaluation k+1 runs
+        CK(cudaStreamWaitEvent(p->s_out, ev_comp[b], 0));
+        CK(cudaMemcpyAsync(u_host[k], p->d_u_st[b], bytes, cudaMemcpyDeviceToHost, p->s_out));
+        CK(cudaEventRecord(ev_out[b], p->s_out));
+    }
+    CK(cudaEventRecord(ev_fj, p->s_out));  // join both copy streams back into `stream`
+    CK(cudaStreamWaitEvent(s, ev_fj, 0));
+    CK(cudaEventRecord(ev_fj, p->s_in));
+    CK(cudaStreamWaitEvent(s, ev_fj, 0));
+    if (E_host) CK(cudaMemcpyAsync(E_host, p->d_Em, sizeof(double) * (size_t)count, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     return NLINT_OK;
 }

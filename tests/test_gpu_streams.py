@@ -2,7 +2,11 @@
 internal stream forked from the caller's stream (before the interpolation) and joined back
 before the spreading.  Each result must equal a fresh plan's result for the same input, whatever
 ran on the plan before, on the current stream, on another torch stream, and when the evaluation
-is captured into a CUDA graph and replayed with new data."""
+is captured into a CUDA graph and replayed with new data.  The streaming host entry point
+(copies on two plan-owned streams, overlapped with the evaluations) must give each density
+what the device entry point gives it."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -96,3 +100,32 @@ def test_evaluation_captured_in_a_cuda_graph(pkg):
         torch.cuda.synchronize()
         assert _rel(u, u_ref) <= TOL
         assert abs(E.item() - E_ref.item()) <= TOL * abs(E_ref.item())
+
+
+@pytest.mark.parametrize("count", [1, 2, 5])
+def test_streaming_host_entry_point_matches_device_evaluations(pkg, count):
+    rhos = _densities(48, count)
+    ref = _plan(pkg)
+    refs = [ref.eval_energy(r) for r in rhos]
+    plan = _plan(pkg)
+    rh = [r.cpu().pin_memory() for r in rhos]
+    uh = [torch.empty_like(r).pin_memory() for r in rh]
+    for _ in range(2):  # the second call reuses the staging buffers and events
+        us, Es = plan.eval_host_many(rh, us_host=uh)
+    torch.cuda.synchronize()
+    for u, E, (u_ref, E_ref) in zip(us, Es, refs):
+        assert _rel(u, u_ref.cpu()) <= TOL
+        assert abs(E - E_ref.item()) <= TOL * abs(E_ref.item())
+    us2, none = plan.eval_host_many([r.cpu() for r in rhos], energies=False)  # pageable memory
+    assert none is None
+    for u, (u_ref, _) in zip(us2, refs):
+        assert _rel(u, u_ref.cpu()) <= TOL
+
+
+def test_streaming_host_entry_point_rejects_bad_arguments(pkg):
+    plan = _plan(pkg)
+    with pytest.raises(ValueError):
+        plan.eval_host_many([])
+    assert plan._lib.nlint_eval_host_many(plan._h, 0, None, None, 1.0, None, None) == -1
+    null2 = (ctypes.c_void_p * 2)(None, None)
+    assert plan._lib.nlint_eval_host_many(plan._h, 2, null2, null2, 1.0, None, None) == -1
