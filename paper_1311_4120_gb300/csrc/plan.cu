@@ -463,8 +463,8 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
     }
     int64_t nbin[3] = {1, 1, 1};
     for (int ax = 0; ax < d; ax++) nbin[ax] = (Mh ? (hi[ax] - lo[ax]) / p->B[ax] + 1 : 1);
-    // sort by bin, then by stencil origin inside the bin (nodes sharing an origin become
-    // adjacent, which the kernels exploit), then canonical order
+    // sort by bin, then by stencil origin inside the bin (a warp's consecutive nodes then touch
+    // overlapping tile cells), then canonical order
     std::vector<int64_t> key(Mh), okey(Mh);
     for (int64_t o = 0; o < Mh; o++) {
         int64_t kk = 0, oo = 0;
