@@ -211,6 +211,53 @@ def run_alg2(pkg, torch, dev, wl, rho32, flush, stream, args, ms_step, ms64=None
     return out
 
 
+FP64_TFLOPS = 1.25   # nominal dense FP64 rate of a GB300 (FP64 vector units)
+FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz
+
+
+def node_flops(info: dict) -> float:
+    """Algorithmic flops of one interpolation plus one spreading over the half node set: per
+    stencil cell a complex-by-real multiply-add in each (8 w^d flops per node)."""
+    return 8.0 * info["w"] ** info["d"] * info["n_half_nodes"]
+
+
+def run_configs(pkg, torch, dev, flush, stream, reps=5):
+    """The other single-density configurations (3D Coulomb 32^3, 2.5D Coulomb 512^2, 3D dipole
+    128^3) in FP32 and FP64: time per evaluation (L2 flushed), throughput, and the FP32 result's
+    error against the FP64 GPU result (u: relative L-inf; E: relative to the FP64 energy's
+    magnitude)."""
+    out = {}
+    for name in ("c1", "c2", "c3"):
+        wl = synth.CONFIGS[name]()
+        rho64 = torch.from_numpy(wl.rho()).to(dev)
+        res, us, Es = {}, {}, {}
+        for prec in ("fp32", "fp64"):
+            plan = pkg.Plan(wl.d, wl.n, wl.L, wl.kernel, axis=wl.axis, nodes=wl.nodes, precision=prec,
+                            eps=1e-6 if prec == "fp32" else 1e-12, device=dev.index)
+            r = rho64 if prec == "fp64" else rho64.float()
+            u = torch.empty_like(r)
+            E = torch.empty((), dtype=torch.float64, device=dev)
+            for _ in range(3):
+                plan.eval_energy(r, lam=wl.lam, out=u, E_out=E)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * reps)]
+            for k in range(reps):
+                flush.fill_(float(k))
+                ev[2 * k].record(stream)
+                plan.eval_energy(r, lam=wl.lam, out=u, E_out=E)
+                ev[2 * k + 1].record(stream)
+            torch.cuda.synchronize()
+            ms = statistics.median(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(reps))
+            res[prec] = {"ms_per_step": ms, "value": wl.n_points / (ms / 1e3), "w": plan.info["w"]}
+            us[prec], Es[prec] = u.double(), float(E.item())
+            plan.close()
+        out[name] = {"workload": wl.desc, "unit": UNIT, "fp32": res["fp32"], "fp64": res["fp64"],
+                     "speedup_fp32_vs_fp64_gpu": res["fp64"]["ms_per_step"] / res["fp32"]["ms_per_step"],
+                     "rel_linf_fp32_vs_fp64": float((us["fp32"] - us["fp64"]).abs().max()
+                                                    / us["fp64"].abs().max()),
+                     "rel_energy_fp32_vs_fp64": abs(Es["fp32"] - Es["fp64"]) / abs(Es["fp64"])}
+    return out
+
+
 def path_bytes(info: dict) -> float:
     """Whole-path algorithmic bytes per evaluation: s (51.4 N^3 + 2 N_f) in 3D."""
     s = 4.0 if info["precision"] == 0 else 8.0
@@ -495,10 +542,24 @@ def run_ours(args, rank, world, local_rank):
             ev[2 * k + 1].record(stream)
         torch.cuda.synchronize()
         ms64 = statistics.median(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(k64))
+        # FP64 ALU roofline of the node kernels: one more evaluation with the stage events
+        plan64.set_stage_timing(True)
+        plan64.eval_energy(rho64, lam=wl.lam, out=u64, E_out=E64)
+        torch.cuda.synchronize()
+        st64 = dict(plan64.stage_times())
+        plan64.set_stage_timing(False)
+        i64 = plan64.info
+        fl = node_flops(i64)
+        t_nodes = (st64["interp"] + st64["spread"]) / 1e3
         fp64 = {"value": wl.n_points / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
-                "w": plan64.info["w"], "energy": float(E64.item()),
+                "w": i64["w"], "energy": float(E64.item()),
                 "rel_linf_fp32_vs_fp64": float((u32.double() - u64).abs().max() / u64.abs().max()),
-                "rel_energy_fp32_vs_fp64": abs(E32 - float(E64.item())) / abs(float(E64.item()))}
+                "rel_energy_fp32_vs_fp64": abs(E32 - float(E64.item())) / abs(float(E64.item())),
+                "stages_ms": {k: round(v, 3) for k, v in st64.items()},
+                "roofline": {"bound": "alu", "kernel": "interp+spread", "unit": "TFLOP/s",
+                             "algorithmic_flops": fl, "achieved": fl / t_nodes / 1e12,
+                             "peak": FP64_TFLOPS, "peak_kind": "nominal FP64 (no measured figure)",
+                             "frac": fl / t_nodes / 1e12 / FP64_TFLOPS}}
         plan64.close()
         del rho64
 
@@ -525,6 +586,13 @@ def run_ours(args, rank, world, local_rank):
                  "unit": "GB/s", "frac": ach / peak, "traffic": traffic,
                  "algorithmic_bytes": stage_bytes(info, dom),
                  "mean_ms": mean_stage[dom]})
+    # the node kernels against the FP32 ALU rate as well (they are issue-bound, not flop-bound)
+    t_nodes32 = (mean_stage.get("interp", 0.0) + mean_stage.get("spread", 0.0)) / 1e3
+    if t_nodes32 > 0:
+        roof["alu_view"] = {"kernel": "interp+spread", "unit": "TFLOP/s",
+                            "achieved": node_flops(info) / t_nodes32 / 1e12,
+                            "peak": FP32_TFLOPS, "peak_kind": "nominal FP32 (SM count x lanes x clock)",
+                            "frac": node_flops(info) / t_nodes32 / 1e12 / FP32_TFLOPS}
     ms_step = 1e3 * t_max / args.steps
     path_gbs = path_bytes(info) / (ms_step / 1e3) / 1e9
 
@@ -536,6 +604,7 @@ def run_ours(args, rank, world, local_rank):
                                "half Coulomb, half dipole, one CUDA graph",
                    "fp32": b32, "fp64": b64,
                    "speedup_fp32_vs_fp64_gpu": b64["ms_per_step"] / b32["ms_per_step"]}
+    configs = None if args.no_configs else run_configs(pkg, torch, dev, flush, stream)
     cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline_obj()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -554,6 +623,7 @@ def run_ours(args, rank, world, local_rank):
         "batched": batched,
         "toeplitz_form": toep,
         "algorithm2": alg2,
+        "other_configs": configs,
         "stages_ms": {k: round(v, 4) for k, v in mean_stage.items()},
         "path_bytes_per_step": path_bytes(info),
         "path_frac_of_hbm": path_gbs / peak,
@@ -579,6 +649,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison leg")
     ap.add_argument("--no-toeplitz", action="store_true", help="skip the precomputed-kernel form")
     ap.add_argument("--no-alg2", action="store_true", help="skip the Algorithm 2 leg")
+    ap.add_argument("--no-configs", action="store_true", help="skip the other single-density configs")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
