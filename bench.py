@@ -61,6 +61,23 @@ def _src_hash(stage: str) -> str:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
+def max_over_ranks(values, device):
+    """Element-wise maximum of per-rank times over all ranks of the default process group (the
+    values themselves when there is no process group): the whole job finishes with its
+    slowest rank."""
+    import torch
+    if not (torch.distributed.is_available() and torch.distributed.is_initialized()):
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def job_rate(units_per_rank, world, t_max):
+    """Whole-job throughput of replicas: every rank's units over the slowest rank's time."""
+    return units_per_rank * world / t_max
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -461,13 +478,9 @@ def run_ours(args, rank, world, local_rank):
     plan.set_stage_timing(False)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     t_dev = sum(step_ms) / 1e3
-    t_max = t_dev
-    if world > 1:
-        tt = torch.tensor([t_dev], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(tt.item())
+    (t_max,) = max_over_ranks([t_dev], dev)
     points = wl.n_points * args.steps * world
-    value = points / t_max
+    value = job_rate(wl.n_points * args.steps, world, t_max)
     E32 = float(E.item())
     u32 = u.clone()
 
@@ -490,10 +503,7 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(args.steps):
         plan.eval_host(rho_h[0], lam=wl.lam, u_host=u_h[0])
     t_sync = time.perf_counter() - t0
-    if world > 1:
-        tt = torch.tensor([t_e2e, t_sync], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_e2e, t_sync = float(tt[0].item()), float(tt[1].item())
+    t_e2e, t_sync = max_over_ranks([t_e2e, t_sync], dev)
     e2e = {"value": points / t_e2e, "unit": UNIT, "h2d_bytes_per_step": rho_np.nbytes,
            "d2h_bytes_per_step": rho_np.nbytes + 8,
            "api": "nlint_eval_host_many: K steps in one call, copies overlapped with evaluations",
