@@ -154,20 +154,27 @@ __device__ __forceinline__ void warp_chunk(int4 sb, int wid, int &ja, int &jb) {
 // several times slower than integer ones on this GPU, so each CTA adds integer multiples of
 // 1/S: S = 2^(E - ceil(log2 B)) with B >= max(sum_j |Re c_j|, sum_j |Im c_j|) over the
 // subproblem (every cell sum and every contribution is at most B, since phi <= 1), E = 29 for
-// FP32 (int32 cells) and 61 for FP64 (int64 cells), so no cell can overflow.  Each contribution is rounded to 1/S <= 2^-E B
-// (FP32: 2^-29 B, finer than FP32 rounding of the largest cells); the integer sums are exact,
-// so a tile does not depend on the order of its additions.
+// FP32 (int32 cells) and 50 for FP64 (int64 cells), so no cell can overflow.  Each
+// contribution a * b is rounded to 1/S <= 2^-E B (FP32: 2^-29 B, finer than FP32 rounding of the
+// largest cells; FP64: 2^-50 B); the integer sums are exact, so a tile does not depend on the
+// order of its additions.  FP64 rounds with one fused multiply-add: a * b + 1.5 * 2^52 lies in
+// [2^52, 2^53) for |a * b| < 2^51, where the spacing of doubles is 1, so its low mantissa bits
+// are a * b rounded to the nearest integer (the classic magic-number conversion) -- one
+// operation on the FP64 units, which bound the FP64 path, instead of a multiply and a convert.
 template <typename T> struct FixAcc;
 template <> struct FixAcc<float> {
     using A = int;
     static constexpr int E = 29, MAXEXP = 126;
-    __device__ __forceinline__ static A quant(float v) { return __float2int_rn(v); }
+    __device__ __forceinline__ static A mulq(float a, float b) { return __float2int_rn(a * b); }
     __device__ __forceinline__ static void add(A *p, A v) { atomicAdd(p, v); }
 };
 template <> struct FixAcc<double> {
     using A = long long;
-    static constexpr int E = 61, MAXEXP = 1000;
-    __device__ __forceinline__ static A quant(double v) { return __double2ll_rn(v); }
+    static constexpr int E = 50, MAXEXP = 1000;
+    __device__ __forceinline__ static A mulq(double a, double b) {
+        constexpr double MAGIC = 6755399441055744.0;  // 1.5 * 2^52
+        return __double_as_longlong(fma(a, b, MAGIC)) - __double_as_longlong(MAGIC);
+    }
     __device__ __forceinline__ static void add(A *p, A v) {
         atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)v);
     }
@@ -418,8 +425,8 @@ __global__ void __launch_bounds__(SUB_THREADS) spread_sub_kernel(NodeDesc nd,
                     A *pr = tr + idx, *pi = ti + idx;  // the column's run: constant offsets
 #pragma unroll
                     for (int q0 = 0; q0 < L; q0++) {
-                        F::add(pr + q0 * PLANE, F::quant(cr * k0[q0]));
-                        F::add(pi + q0 * PLANE, F::quant(ci * k0[q0]));
+                        F::add(pr + q0 * PLANE, F::mulq(cr, k0[q0]));
+                        F::add(pi + q0 * PLANE, F::mulq(ci, k0[q0]));
                     }
                 }
             }
