@@ -375,8 +375,9 @@ __global__ void __launch_bounds__(SUB_THREADS) spread_sub_kernel(NodeDesc nd,
         sre += kq[0];
         sim += kq[1];
     }
-    // B to within rounding (<= 1024 terms: a relative 1e-4 in FP32); the headroom of 2^E below
-    // the integer range (4x) absorbs it
+    // B to within rounding (<= 1024 terms: a relative 1e-4 in FP32, 1e-13 in FP64); the room
+    // above 2^E absorbs it (FP32: int32 cells, 4x; FP64: contributions below 2^51 for the
+    // rounding by fused multiply-add, 2x)
     // (fmax drops a NaN operand: a non-finite sum makes the bound NaN explicitly)
     const T bound = (isfinite(sre) && isfinite(sim)) ? fmax(sre, sim) : T(NAN);
     if (!(bound > T(0))) {
