@@ -183,7 +183,8 @@ int nlint_eval_host(nlint_plan plan, const void *rho_host, void *u_host, double 
  * pageable memory gives the same results with serialised copies.  Each u_host[k], E_host[k]
  * equals what nlint_eval_host gives for rho_host[k].  The paper has no counterpart: it is the
  * serving form of the same evaluation.  Errors: NLINT_EINVAL (count <= 0, NULL arrays or
- * entries), NLINT_ENOMEM, NLINT_ECUDA. */
+ * entries), NLINT_ECUDA (including a failed allocation of the staging buffers, which are
+ * allocated on the first call and kept by the plan). */
 int nlint_eval_host_many(nlint_plan plan, int count, const void *const *rho_host,
                          void *const *u_host, double lambda, double *E_host, void *stream);
 
