@@ -2,7 +2,11 @@
 //
 // The plan follows Algorithm 1 (Section 3.2): steps 1-3 (grid, nodes and weights of
 // eq. 3.7) run once on the host in FP64; steps 4-5 (type-2 NUFFT, multiply, type-1 NUFFT)
-// and the energy of Remark 3.3 run on the device for every evaluation.
+// and the energy of Remark 3.3 run on the device for every evaluation.  Besides that path:
+// Algorithm 2 (Section 3.3, run_alg2), the same operator with its Toeplitz kernel precomputed
+// (nlint_plan_toeplitz), the stage entry points, and the host-buffer forms (nlint_eval_host,
+// and nlint_eval_host_many with its copies overlapped with the evaluations).  An Algorithm 1
+// plan clears its spread grid on a side stream while the interpolation runs.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
