@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MO
         } else {
             io.in_base = q * P.in_so;
         }
-        if constexpr (MODE == 1 || MODE == 2) {
+        if constexpr (MODE == 1 || MODE == 2 || MODE == 5) {
             if (P.ball2 > 0) {  // block-uniform branch
                 const int64_t a0 = P.dim == 3 ? q / NF : q, a1 = P.dim == 3 ? q % NF : 0;
                 const int64_t s1 = a1 < NF / 2 ? a1 : a1 - NF;
@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MO
                 xl = r2 > P.ball2 ? -1 : (int)sqrtf((float)(P.ball2 - r2)) + 1;
                 if (MODE == 1 && xl < 0) io.valid = false;  // nothing to read or write
                 if (!__syncthreads_or(io.valid && xl >= 0)) {  // every row of the CTA outside
-                    if (MODE == 2 && io.valid)
+                    if ((MODE == 2 || MODE == 5) && io.valid)  // their transforms are zero
                         for (int a = t; a < N; a += TPL)
                             reinterpret_cast<T2 *>(vout)[io.out_base + a] = czero<T2>();
                     return;

@@ -79,7 +79,9 @@ struct PassDesc {
     // ball window of the full row passes along x (0 = none): every fine cell a node's stencil
     // touches has s0^2 + s1^2 + s2^2 <= ball2 (signed FFT indices), so the forward row pass
     // (mode 1) writes, and the fold pass (mode 2) reads, only the entries of each row inside that
-    // ball (rows outside it: nothing written; the fold pass writes their zero transform)
+    // ball (rows outside it: nothing written; the fold pass writes their zero transform).  For
+    // the convolution pass (mode 5) every multiplier row with s0^2 + s1^2 > ball2 is zero, so
+    // those rows write zeros without transforming
     int64_t ball2;
 };
 

@@ -165,6 +165,7 @@ struct nlint_plan_s {
     // FFT passes transform only the window's lines (0 = the full passes P1..Q3)
     int win = 0;
     int64_t ball2 = 0;      // ball window of the full x passes (PassDesc::ball2)
+    int64_t conv_ball2 = 0; // Algorithm 2: rows of I_1's convolution pass beyond it are zero
     size_t bytes_Hwin = 0;  // the planes of the spread grid the window touches
     nlint::PassDesc P1w, P2w, P3w, Q1w, Q2w, Q3w;
     // dual z passes shared by I_1 and I_2 (the first forward one reads the density once for both,
@@ -781,6 +782,7 @@ static int alg2_fill_multiplier(nlint_plan_s *p) {
     const double dk = 2.0 * M_PI / ((double)n * p->h);
     const double inv = 1.0 / std::pow((double)n, d);
     std::vector<T> m((size_t)(rows * n));
+    std::vector<int64_t> row_r2(rows, -1);  // s0^2 + s1^2 of each row with a nonzero entry
     auto sgn = [n](int64_t g) { return (double)(g < n / 2 ? g : g - n); };
     auto work = [&](int64_t r0, int64_t r1) {
         for (int64_t r = r0; r < r1; r++) {
@@ -796,6 +798,10 @@ static int alg2_fill_multiplier(nlint_plan_s *p) {
                     k[0] = dk * sgn(c);
                 }
                 m[(size_t)(r * n + c)] = (T)(alg2_multiplier(p, k) * inv);
+                if (m[(size_t)(r * n + c)] != T(0)) {
+                    const int64_t s0 = (d == 3) ? (int64_t)sgn(g0) : g0, s1 = (d == 3) ? (int64_t)sgn(g1) : 0;
+                    row_r2[r] = s0 * s0 + s1 * s1;
+                }
             }
         }
     };
@@ -803,6 +809,11 @@ static int alg2_fill_multiplier(nlint_plan_s *p) {
     std::vector<std::thread> th;
     for (int t = 0; t < nt; t++) th.emplace_back(work, rows * t / nt, rows * (t + 1) / nt);
     for (auto &t : th) t.join();
+    // the convolution pass skips the rows beyond every nonzero multiplier row (PassDesc::ball2)
+    int64_t r2max = 0;
+    for (int64_t v : row_r2) r2max = std::max(r2max, v);
+    const int64_t full = (d == 3) ? 2 * (int64_t)(n / 2) * (n / 2) : (int64_t)(n / 2) * (n / 2);
+    p->conv_ball2 = r2max < full ? std::max<int64_t>(r2max, 1) : 0;
     CK(cudaMalloc(&p->d_khat, m.size() * sizeof(T)));
     CK(cudaMemcpy(p->d_khat, m.data(), m.size() * sizeof(T), cudaMemcpyHostToDevice));
     p->ws_bytes += m.size() * sizeof(T);
@@ -899,6 +910,7 @@ static int alg2_setup(nlint_plan_s *p) {
     rc = p->prec == NLINT_FP32 ? alg2_fill_multiplier<float>(p) : alg2_fill_multiplier<double>(p);
     if (rc) return rc;
     conv_passes(p);
+    p->X.ball2 = p->conv_ball2;
     return NLINT_OK;
 }
 
