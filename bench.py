@@ -45,13 +45,13 @@ TOL = 1e-5                          # stated relative L-inf tolerance of the FP3
 # Measured on the 256^3 FP32 workload (profiles/dram_traffic_c4_fp32.md).
 TRAFFIC = {
     "interp": {"bytes": 734.5e6, "src": "aab02eb942c297d4"},
-    "spread": {"bytes": 971.4e6, "src": "aab02eb942c297d4"},
-    "fwd_fft_z": {"bytes": 150.7e6, "src": "9a1960e7cd364c8e"},
-    "fwd_fft_y": {"bytes": 342.7e6, "src": "9a1960e7cd364c8e"},
-    "fwd_fft_x": {"bytes": 482.4e6, "src": "9a1960e7cd364c8e"},
-    "inv_fft_x": {"bytes": 530.2e6, "src": "9a1960e7cd364c8e"},
-    "inv_fft_y": {"bytes": 369.5e6, "src": "9a1960e7cd364c8e"},
-    "inv_fft_z": {"bytes": 247.5e6, "src": "9a1960e7cd364c8e"},
+    "spread": {"bytes": 971.5e6, "src": "aab02eb942c297d4"},
+    "fwd_fft_z": {"bytes": 150.6e6, "src": "2cc1764e7d09412c"},
+    "fwd_fft_y": {"bytes": 342.4e6, "src": "2cc1764e7d09412c"},
+    "fwd_fft_x": {"bytes": 482.4e6, "src": "2cc1764e7d09412c"},
+    "inv_fft_x": {"bytes": 530.3e6, "src": "2cc1764e7d09412c"},
+    "inv_fft_y": {"bytes": 369.6e6, "src": "2cc1764e7d09412c"},
+    "inv_fft_z": {"bytes": 247.5e6, "src": "2cc1764e7d09412c"},
 }
 
 
