@@ -275,6 +275,39 @@ def run_configs(pkg, torch, dev, flush, stream, reps=5):
     return out
 
 
+def fft_yardstick(torch, dev, wl, n_fine, flush, stream, stages, reps=5):
+    """cuFFT (torch.fft) on the same oversampled grid, as a timing yardstick only (never on the
+    path): the full real-to-complex transform of the zero-padded n_fine^3 density and the
+    complex-to-real transform back, against the path's three forward and three inverse passes
+    (which also deconvolve, prune to the stored modes and window, and fold)."""
+    x = torch.zeros((n_fine,) * 3, dtype=torch.float32, device=dev)
+    x[: wl.n, : wl.n, : wl.n] = torch.from_numpy(wl.rho()).to(dev, torch.float32)
+    X = torch.fft.rfftn(x)
+    y = torch.fft.irfftn(X, s=x.shape)
+    ms = {"rfftn": [], "irfftn": []}
+    for k in range(reps + 1):
+        for name in ms:
+            flush.fill_(float(k))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            if name == "rfftn":
+                X = torch.fft.rfftn(x)
+            else:
+                y = torch.fft.irfftn(X, s=x.shape)
+            b.record(stream)
+            torch.cuda.synchronize()
+            if k > 0:
+                ms[name].append(a.elapsed_time(b))
+    del x, X, y
+    ours_f = sum(stages.get(k, 0.0) for k in ("fwd_fft_z", "fwd_fft_y", "fwd_fft_x"))
+    ours_i = sum(stages.get(k, 0.0) for k in ("inv_fft_x", "inv_fft_y", "inv_fft_z"))
+    return {"what": f"cuFFT via torch.fft on the {n_fine}^3 FP32 zero-padded grid (yardstick, not "
+                    "on the path) vs the path's pruned passes with their fused deconvolution",
+            "cufft_rfftn_ms": statistics.median(ms["rfftn"]),
+            "cufft_irfftn_ms": statistics.median(ms["irfftn"]),
+            "ours_forward_passes_ms": ours_f, "ours_inverse_passes_ms": ours_i}
+
+
 def path_bytes(info: dict) -> float:
     """Whole-path algorithmic bytes per evaluation: s (51.4 N^3 + 2 N_f) in 3D."""
     s = 4.0 if info["precision"] == 0 else 8.0
@@ -615,6 +648,8 @@ def run_ours(args, rank, world, local_rank):
                    "fp32": b32, "fp64": b64,
                    "speedup_fp32_vs_fp64_gpu": b64["ms_per_step"] / b32["ms_per_step"]}
     configs = None if args.no_configs else run_configs(pkg, torch, dev, flush, stream)
+    yard = None if args.no_yardstick else fft_yardstick(torch, dev, wl, info["n_fine"], flush,
+                                                         stream, mean_stage)
     cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline_obj()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -634,6 +669,7 @@ def run_ours(args, rank, world, local_rank):
         "toeplitz_form": toep,
         "algorithm2": alg2,
         "other_configs": configs,
+        "fft_yardstick": yard,
         "stages_ms": {k: round(v, 4) for k, v in mean_stage.items()},
         "path_bytes_per_step": path_bytes(info),
         "path_frac_of_hbm": path_gbs / peak,
@@ -660,6 +696,7 @@ def main():
     ap.add_argument("--no-toeplitz", action="store_true", help="skip the precomputed-kernel form")
     ap.add_argument("--no-alg2", action="store_true", help="skip the Algorithm 2 leg")
     ap.add_argument("--no-configs", action="store_true", help="skip the other single-density configs")
+    ap.add_argument("--no-yardstick", action="store_true", help="skip the cuFFT timing yardstick")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
