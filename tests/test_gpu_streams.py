@@ -122,6 +122,23 @@ def test_streaming_host_entry_point_matches_device_evaluations(pkg, count):
         assert _rel(u, u_ref.cpu()) <= TOL
 
 
+@pytest.mark.parametrize("d,prec,alg", [(2, "fp64", 1), (3, "fp64", 1), (3, "fp32", 2)])
+def test_streaming_host_entry_point_other_plans(pkg, d, prec, alg):
+    n, L = (64, 16.0) if d == 2 else (32, 12.0)
+    plan = pkg.Plan(d, n, L, "coulomb", precision=prec, eps=1e-6 if prec == "fp32" else 1e-12,
+                    algorithm=alg, device=0)
+    dt = torch.float32 if prec == "fp32" else torch.float64
+    rng = np.random.default_rng(5 + d)
+    rh = [torch.from_numpy(rng.standard_normal((n,) * d)).to(dt).pin_memory() for _ in range(3)]
+    us, Es = plan.eval_host_many(rh)
+    tol = 1e-6 if prec == "fp32" else 1e-12
+    for r, u, E in zip(rh, us, Es):
+        u_ref, E_ref = plan.eval_energy(r.to("cuda:0"))
+        torch.cuda.synchronize()
+        assert _rel(u, u_ref.cpu()) <= tol
+        assert abs(E - E_ref.item()) <= tol * abs(E_ref.item())
+
+
 def test_streaming_host_entry_point_rejects_bad_arguments(pkg):
     plan = _plan(pkg)
     with pytest.raises(ValueError):
