@@ -1,0 +1,35 @@
+"""The bench's algorithmic models at the 256^3 workload (FP32, w = 7; FP64, w = 13) equal the
+figures the measurement documentation divides by: the whole-path bytes s (51.4 N^3 + 2 N_f),
+the spreading kernel's bytes (the fine-grid ball plus the node stream) and the node kernels'
+8 w^d flops per half node."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+C4 = {"precision": 0, "n": 256, "n_fine": 512, "n_nodes": 160 * 160 * 320,
+      "n_half_nodes": 160 * 160 * 320 // 2, "w": 7, "d": 3}
+
+
+def test_path_bytes():
+    assert bench.path_bytes(C4) == pytest.approx(4 * (51.4 * 256 ** 3 + 2 * 8192000))
+    assert bench.path_bytes(C4) == pytest.approx(3.515e9, rel=1e-3)
+    assert bench.path_bytes(dict(C4, precision=1)) == pytest.approx(2 * bench.path_bytes(C4))
+
+
+def test_spread_and_interp_bytes():
+    assert bench.stage_bytes(C4, "spread") == pytest.approx(412.2e6, rel=1e-3)
+    assert bench.stage_bytes(C4, "interp") == pytest.approx(428.6e6, rel=1e-3)
+
+
+def test_node_flops():
+    assert bench.node_flops(C4) == 8 * 7 ** 3 * 4096000
+    assert bench.node_flops(dict(C4, w=13)) == pytest.approx(7.2e10, rel=1e-2)
+
+
+def test_job_rate_of_replicas():
+    assert bench.job_rate(16777216 * 10, 4, 0.0307) == pytest.approx(4 * 16777216 * 10 / 0.0307)
