@@ -8,8 +8,9 @@ TEST INFRASTRUCTURE ONLY.  Parameter settings:
   * "fine"    sigma = 2, w = 24, tau = (w pi / sigma) / (2 N^2 sqrt(sigma (sigma - 1))), which
                 balances aliasing against truncation (about 1e-11 in 3D, limited by rounding
                 amplified by exp(3 N^2 tau / 4) at the corner modes);
-  * "fp32ref" sigma = 2, w = 16, tau balanced as for "fine" (about 2e-8): a reference for
-                FP32 results at a third of the cost of "fine";
+  * "fp32ref" sigma = 2, w = 16, tau balanced as for "fine" (0.6-1.0e-8 against the direct
+                sums on 12^3, 16^3 and 32^2 grids, pinned below 3e-8): a reference for FP32
+                results at a third of the cost of "fine";
   * "paper12" the paper's 12-digit setting: Mr = 2N, tau = 12 / N^2, 24 points;
   * "paper6"  the paper's 6-digit setting:  Mr = 2N, tau = 6 / N^2, 12 points.
 The balanced tau is this project's reading (the paper states only the two settings above);

@@ -141,3 +141,26 @@ def test_pins_catch_mutation(monkeypatch, mutation):
         monkeypatch.setattr(pipeline, "type2", offset_type2)
         err = mix_err()
     assert err > 5e-2, f"{mutation} not detected (err={err:.2e})"
+
+
+def test_fp32ref_pin_catches_narrow_stencil(monkeypatch):
+    # The FP32 reference setting run with half its stencil (w = 8 instead of 16, tau balanced
+    # for w = 8) must fail the 3e-8 pin against the direct sums (Section 2 with eqs. 3.2/3.7).
+    from oracle import nufft
+    orig = nufft.params
+
+    def narrow(N, setting="parity"):
+        if setting == "fp32ref":
+            tau = (8 * np.pi / 2) / (2.0 * N ** 2 * np.sqrt(2.0))
+            return 2 * N, 8, tau
+        return orig(N, setting)
+
+    d, n, nodes, L = 3, 12, (8, 8, 16), 8.0
+    rho = synth.gauss_iso(d, n, L) + 0.1 * np.random.default_rng(n + d).standard_normal((n,) * d)
+    k, W = quadrature.nodes_weights(d, n, L, nodes)
+    rd = direct.type2(rho, L, k)
+    ok = np.max(np.abs(pipeline.type2(rho, L, k, "nufft", "fp32ref") - rd)) / np.max(np.abs(rd))
+    assert ok < 3e-8
+    monkeypatch.setattr(nufft, "params", narrow)
+    bad = np.max(np.abs(pipeline.type2(rho, L, k, "nufft", "fp32ref") - rd)) / np.max(np.abs(rd))
+    assert bad > 3e-8, f"narrow fp32ref stencil not detected (err={bad:.2e})"

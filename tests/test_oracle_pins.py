@@ -127,7 +127,9 @@ def test_grid_energy_equals_dual_energy():
 
 
 # --------------------------------------------------------------------------- O2 vs O1
-@pytest.mark.parametrize("setting,tol", [("parity", 3e-14), ("fine", 3e-11),
+# fp32ref is the reference of every FP32 parity test: measured 0.6-1.0e-8 on these cases,
+# pinned at 3e-8 (three orders below the FP32 path's 1e-5 tolerance)
+@pytest.mark.parametrize("setting,tol", [("parity", 3e-14), ("fine", 3e-11), ("fp32ref", 3e-8),
                                          ("paper12", 5e-11), ("paper6", 1e-5)])
 @pytest.mark.parametrize("d,n,nodes", [(3, 12, (8, 8, 16)), (3, 16, (10, 10, 20)), (2, 32, (16, 32))])
 def test_nufft_matches_direct_sums(setting, tol, d, n, nodes):
