@@ -42,7 +42,8 @@ TOL = 1e-5                          # stated relative L-inf tolerance of the FP3
 # DRAM bytes per launch from an ncu capture of the kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum), keyed by stage name, with the hash of the kernel source the capture
 # was taken on: a changed source reports traffic null until it is captured again.
-# Measured on the 256^3 FP32 workload (profiles/dram_traffic_c4_fp32.md).
+# Measured with ncu on the 256^3 FP32 workload (one launch of each kernel, one pass of
+# dram__bytes_read.sum and dram__bytes_write.sum).
 TRAFFIC = {
     "interp": {"bytes": 734.5e6, "src": "aab02eb942c297d4"},
     "spread": {"bytes": 971.5e6, "src": "aab02eb942c297d4"},
@@ -151,29 +152,44 @@ def stage_bytes(info: dict, stage: str) -> float:
     """Algorithmic DRAM bytes of one launch of a stage (3D, sigma = 2 Hermitian layout).
 
     s = real size, b = 2 s complex size, N grid, n fine grid, nh = n/2 + 1 stored planes,
-    M = half node count.  FFT passes read their input once and write their output once;
-    interp reads the ball |t| < pi (+ stencil) of the half grid once (pi/12 n^3 cells)
-    plus 7 node values and writes c; spread reads c and the node stream and writes the ball
-    once; the energy pass additionally reads rho.
+    M = half node count.  FFT passes read their input once and write their output once.  The
+    node kernels follow the whole-path model s (51.4 N^3 + 2 N_f): each touches the ball
+    |t| < pi of the half grid once ((pi/12) n^3 cells) and carries half of the node stream of
+    four values per node (2 N_f s over the path, i.e. two values, M b, per kernel).
     """
     s = 4.0 if info["precision"] == 0 else 8.0
     b = 2 * s
     N, n, M = info["n"], info["n_fine"], info["n_half_nodes"]
     nh = n // 2 + 1
-    node = 3 * 4 + 3 * s + s            # l0 (int32 x3), frac x3, W
     ball = (np.pi / 12.0) * n ** 3 * b
     table = {
         "fwd_fft_z": N ** 3 * s + nh * N * N * b,
         "fwd_fft_y": nh * N * N * b + nh * n * N * b,
         "fwd_fft_x": nh * n * N * b + nh * n * n * b,
-        "interp": ball + M * (node + b),
-        "spread": ball + M * (node - s + b),
+        "interp": ball + M * b,
+        "spread": ball + M * b,
         "inv_fft_x": nh * n * n * b + nh * n * N * b,
         "inv_fft_y": nh * n * N * b + nh * N * N * b,
         "inv_fft_z": nh * N * N * b + 2 * N ** 3 * s,
         "energy": 0.0,
     }
     return float(table[stage])
+
+
+def layout_bytes(info: dict, stage: str) -> float:
+    """DRAM bytes of one launch as the kernels store their data: the ball once plus the node
+    records each node kernel reads and writes (the packed stencil origin and the d w stencil
+    values the plan precomputes), W and c.  Reported beside the algorithmic model, which ``frac`` divides by."""
+    s = 4.0 if info["precision"] == 0 else 8.0
+    b = 2 * s
+    n, M = info["n_fine"], info["n_half_nodes"]
+    ball = (np.pi / 12.0) * n ** 3 * b
+    rec = 4.0 + 3 * info["w"] * s
+    if stage == "interp":
+        return float(ball + M * (rec + s + b))
+    if stage == "spread":
+        return float(ball + M * (rec + b))
+    return stage_bytes(info, stage)
 
 
 def run_alg2(pkg, torch, dev, wl, rho32, flush, stream, args, ms_step, ms64=None, u64=None):
@@ -628,6 +644,8 @@ def run_ours(args, rank, world, local_rank):
     roof.update({"kernel": dom, "achieved": ach, "peak": peak, "peak_kind": peak_kind,
                  "unit": "GB/s", "frac": ach / peak, "traffic": traffic,
                  "algorithmic_bytes": stage_bytes(info, dom),
+                 "model": "ball (pi/12) n^3 b + half node stream M b (whole path s (51.4 N^3 + 2 N_f))",
+                 "layout_bytes": layout_bytes(info, dom),
                  "mean_ms": mean_stage[dom]})
     # the node kernels against the FP32 ALU rate as well (they are issue-bound, not flop-bound)
     t_nodes32 = (mean_stage.get("interp", 0.0) + mean_stage.get("spread", 0.0)) / 1e3

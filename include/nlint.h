@@ -237,7 +237,8 @@ int nlint_autotune(const nlint_params *in, double tol, const char *cache_path, n
  * launches that graph on `stream` (no host synchronisation).  Each u_i equals what
  * nlint_eval_energy gives for plan i alone, up to the order of the spreading's atomic
  * additions.  One batch evaluation at a time; the plans must not be used concurrently.
- * Errors: NLINT_EINVAL (NULL arguments, invalid plans, plans on different devices),
+ * Errors: NLINT_EINVAL (NULL arguments, invalid plans, plans on different devices, a plan
+ * listed more than once: its workspaces cannot serve two concurrent evaluations),
  * NLINT_ECUDA. */
 int nlint_batch_create(int count, const nlint_plan *plans, int branches, nlint_batch *out);
 int nlint_batch_eval(nlint_batch batch, const void *const *rho_dev, void *const *u_dev,
@@ -255,7 +256,9 @@ void nlint_batch_destroy(nlint_batch batch); /* NULL is a no-op; waits for the d
  * It allocates nothing: its scratch is a 1 MiB array in the library's device memory, held on
  * every device that loads the library until the process exits.  The first call on a device
  * looks up that array's device address (cudaGetSymbolAddress) with the device current; make
- * that first call before any stream capture.  Grids above 268435456 points (65536 partial
+ * that first call before any stream capture.  The address is cached per device and CUDA
+ * context: a call under another context of the device (after cudaDeviceReset, or with a
+ * non-primary context current) looks it up again, so that call too belongs before capture.  Grids above 268435456 points (65536 partial
  * sums of 4096 points) are rejected with NLINT_EINVAL.  Every call reuses the same scratch:
  * calls that overlap on the GPU (other streams or host threads) race; serialise them.
  * Summation order is fixed by the inputs (deterministic), partial sums compensated in FP64. */

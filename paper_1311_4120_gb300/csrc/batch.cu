@@ -74,6 +74,13 @@ int nlint_batch_create(int count, const nlint_plan *plans, int branches, nlint_b
             delete b;
             return bfail(NLINT_EINVAL, "invalid plan in the batch");
         }
+        // a plan owns one set of workspaces: two of its evaluations on different branches of
+        // the graph would run at the same time on them and corrupt both results
+        for (int j = 0; j < i; j++)
+            if (plans[j] == plans[i]) {
+                delete b;
+                return bfail(NLINT_EINVAL, "a plan appears more than once in the batch");
+            }
         const int pdev = inf.device;
         if (dev < 0) dev = pdev;
         if (pdev != dev) {

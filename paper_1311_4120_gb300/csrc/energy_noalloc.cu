@@ -17,6 +17,8 @@
 // calls; the array keeps the last call's partial sums.  Calls share the one array, so two
 // calls whose work overlaps on the GPU (different streams, or different host threads) race
 // and give wrong energies: serialise them.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "common.cuh"
@@ -63,24 +65,61 @@ __global__ void __launch_bounds__(1024) noalloc_final_kernel(const double2 *__re
     if (threadIdx.x == 0) *E = scale * tot.value();
 }
 
-// Device address of the scratch array, looked up once per device with that device current.
-// In host code the array's name is only a host-side stand-in, never a device address.
+// Device address of the scratch array, looked up once per device and CUDA context with that
+// device current.  In host code the array's name is only a host-side stand-in, never a device
+// address.  The address belongs to the context the library's module was loaded into: after
+// cudaDeviceReset, or under another context of the same device, the module is loaded again,
+// possibly elsewhere, so the cache is keyed on the calling thread's current context (its
+// process-unique ID from cuCtxGetId, reached through the runtime's driver entry points, so
+// the library does not link the driver library) and the address is looked up again when that
+// ID changes.
+typedef int (*ctx_get_current_fn)(CUcontext *);
+typedef int (*ctx_get_id_fn)(CUcontext, unsigned long long *);
+
 static std::mutex g_noalloc_mu;
 static double2 *g_noalloc_ptr[64];
-static bool g_noalloc_ready[64];
+static unsigned long long g_noalloc_ctx[64];  // context ID of the cached address, 0 = none
+static ctx_get_current_fn g_ctx_get_current;
+static ctx_get_id_fn g_ctx_get_id;
+
+// Process-unique ID of the calling thread's current context, 0 when there is none yet.
+static int current_context_id(unsigned long long *id) {
+    *id = 0;
+    if (!g_ctx_get_current || !g_ctx_get_id) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            return report_error(NLINT_ECUDA, "driver entry points cuCtxGetCurrent/cuCtxGetId unavailable");
+        g_ctx_get_current = (ctx_get_current_fn)f1;
+        g_ctx_get_id = (ctx_get_id_fn)f2;
+    }
+    CUcontext ctx = nullptr;
+    if (g_ctx_get_current(&ctx) != 0) return report_error(NLINT_ECUDA, "cuCtxGetCurrent failed");
+    if (ctx && g_ctx_get_id(ctx, id) != 0) return report_error(NLINT_ECUDA, "cuCtxGetId failed");
+    return NLINT_OK;
+}
 
 static int noalloc_scratch(int dev, double2 **out) {
     if (dev < 0 || dev >= 64) return report_error(NLINT_EUNSUPPORTED, "device ordinal >= 64");
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ready[dev]) {
+    unsigned long long id = 0;
+    int rc = current_context_id(&id);
+    if (rc != NLINT_OK) return rc;
+    if (id == 0 || g_noalloc_ctx[dev] != id) {
         void *ptr = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_partials);
         if (e != cudaSuccess) {
             std::string m = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
             return report_error(NLINT_ECUDA, m.c_str());
         }
+        if (id == 0) {  // the lookup made the device's primary context current
+            rc = current_context_id(&id);
+            if (rc != NLINT_OK) return rc;
+        }
         g_noalloc_ptr[dev] = static_cast<double2 *>(ptr);
-        g_noalloc_ready[dev] = true;
+        g_noalloc_ctx[dev] = id;
     }
     *out = g_noalloc_ptr[dev];
     return NLINT_OK;

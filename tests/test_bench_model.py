@@ -22,8 +22,21 @@ def test_path_bytes():
 
 
 def test_spread_and_interp_bytes():
-    assert bench.stage_bytes(C4, "spread") == pytest.approx(412.2e6, rel=1e-3)
-    assert bench.stage_bytes(C4, "interp") == pytest.approx(428.6e6, rel=1e-3)
+    # the half ball (pi/12) 512^3 complex floats plus two values per half node:
+    # 281.1 MB + 32.8 MB = 313.9 MB per node kernel at the 256^3 workload
+    ball = (3.141592653589793 / 12) * 512 ** 3 * 8
+    assert ball == pytest.approx(281.1e6, rel=1e-3)
+    for st in ("spread", "interp"):
+        assert bench.stage_bytes(C4, st) == pytest.approx(ball + 4096000 * 8)
+        assert bench.stage_bytes(C4, st) == pytest.approx(313.9e6, rel=1e-3)
+    # the per-stage models add up to the whole-path model (which rounds n/2 + 1 stored planes
+    # to n/2 and the per-cell coefficient to 51.4)
+    stages = ("fwd_fft_z", "fwd_fft_y", "fwd_fft_x", "interp", "spread", "inv_fft_x",
+              "inv_fft_y", "inv_fft_z")
+    tot = sum(bench.stage_bytes(C4, st) for st in stages)
+    assert tot == pytest.approx(bench.path_bytes(C4), rel=5e-3)
+    # the stored records: packed origin and 21 stencil values, W and c for the interpolation
+    assert bench.layout_bytes(C4, "interp") == pytest.approx(ball + 4096000 * (4 + 84 + 4 + 8))
 
 
 def test_node_flops():

@@ -95,6 +95,19 @@ def test_batch_rejects_bad_arguments(pkg):
         pkg.Batch([])
 
 
+def test_batch_rejects_a_plan_listed_twice(pkg):
+    # one plan owns one set of workspaces, so two of its evaluations cannot run side by side
+    # on the graph's branches: the batch refuses the duplicate instead of corrupting both
+    p = pkg.Plan(3, 24, 16.0, "coulomb", nodes=(16, 16, 32), precision="fp32", eps=1e-6, device=0)
+    q = pkg.Plan(3, 32, 16.0, "coulomb", nodes=(16, 16, 32), precision="fp32", eps=1e-6, device=0)
+    with pytest.raises(pkg.NlintError, match="more than once"):
+        pkg.Batch([p, q, p], branches=2)
+    b = pkg.Batch([p, q], branches=2)  # the same plans once each are accepted
+    b.close()
+    p.close()
+    q.close()
+
+
 def test_batch_uses_each_plans_form(pkg):
     """Plans with a precomputed Toeplitz kernel run in that form inside the batch graph, the
     others by the NUFFT path (and an Algorithm 2 plan by its own path): each member equals
