@@ -90,6 +90,12 @@ typedef struct nlint_params {
     double pu_a;         /* 3D: a of p_3; 0 = (11.8 / L)^2                                    */
     double pu_r0, pu_r1; /* 2D: R0 < R1 of p_2; 0 = 12 / L and 160 / L                        */
     double P2;           /* radius of I_2's nodes; 0 = min(P, 6.1 sqrt(a)) (3D), min(P, R1) (2D) */
+    /* Bins of stencil-origin cells that one interpolation / spreading CTA covers with a
+     * shared-memory tile of bin + w - 1 cells per axis.  0 = automatic; 3D: 1 = 8x8x8,
+     * 2 = 4x8x8 (FP64 only), 3 = 8x16x16 (FP32 only), 4 = 16x16x16 (FP32 only); 2D: 1 =
+     * 16x16.  A shape whose tile does not fit in shared memory at the plan's width is
+     * NLINT_EUNSUPPORTED (automatic: the smallest shape is taken instead).                  */
+    int bin_shape;
 } nlint_params;
 
 /* Read-only description of a plan. */
@@ -107,6 +113,7 @@ typedef struct nlint_info {
     int algorithm;          /* 1 or 2; for 2 the node fields describe I_2's nodes       */
     double pu_a, pu_r0, pu_r1, P2; /* Algorithm 2's partition parameters (0 if unused)  */
     int toeplitz;           /* 1 once nlint_plan_toeplitz has precomputed K_hat          */
+    int bin_shape;          /* the bin shape in use (see nlint_params.bin_shape)         */
 } nlint_info;
 
 /* Fill *p with defaults (d = 3, Coulomb, eps = 1e-6, everything else automatic). */

@@ -121,12 +121,24 @@ struct NodeDesc {
     int w;               // stencil width
     int pad;             // extended planes below/above the half grid (slowest axis)
     double beta;         // ES kernel shape parameter
+    int bin_shape;       // bin shape (see bin_dim); the kernels are compiled per shape
+    // FP32 plans: one 16-byte record per node, {r0 | r1 << 8 | r2 << 16, u_0, u_1, u_2}: the
+    // first stencil cell per axis relative to the bin origin and, as float bits, the offset
+    // u_a = frac_a - (w/2 - 1) in (0, 1] of the node from that cell (frac_a = g_a - first
+    // cell); the kernels evaluate the stencil values from u_a.  FP64 plans: rel and ker.
+    const int4 *pos;
     const int32_t *rel;  // M: first stencil cell relative to the bin origin, r0 | r1 << 8 | r2 << 16
     const void *ker;     // M x (d w): kernel values phi((q - frac_a)/(w/2)), row per node
     const void *W;       // M, h^d W_j (plan precision), may be NULL (type-2 only)
     int B[3], T[3];      // bin and tile extents per array axis
     int64_t nsub;        // number of subproblems
     const int4 *subs;    // per subproblem {first node, node count, bin, 0}
+    // FP32 3D plans: the nodes of each bin are ordered in groups of at most 32 whose stencil
+    // origins share no shared-memory bank unless they are equal (see build_node_groups); the
+    // interpolation gives each node of a group a lane of its own
+    int64_t ngsub;       // interpolation subproblems (runs of groups of one bin)
+    const int4 *gsubs;   // per interpolation subproblem {first group, group count, bin, 0}
+    const int32_t *grp;  // group g holds nodes grp[g] .. grp[g + 1] - 1
     const int4 *bins;    // per bin {origin axis 0, axis 1, axis 2, crowd slot or -1}
     int ncrowd;          // crowded bins (FP32 plans): their tiles are summed in FP64
     double2 *crowd;      // ncrowd tiles of complex doubles
@@ -142,12 +154,34 @@ struct NodeDesc {
 // passes * lanes entries.
 std::vector<int16_t> build_pair_order(int w, int row, int banks, int lanes, int group);
 
-// Bin extent (stencil-origin cells) along array axis `axis`; the same rule is compiled into
-// the kernels, so a plan's bins always match the tile geometry of its kernels.  3D: 8^3 bins,
-// except 4 x 8 x 8 for FP64 stencils of width >= 10 (tile <= 100 KB of shared memory);
-// 2D: 16 x 16 bins.
-__host__ __device__ constexpr int bin_extent(bool fp64, int d, int w, int axis) {
-    return d == 3 ? ((axis == 0 && fp64 && w >= 10) ? 4 : 8) : (axis < 2 ? 16 : 1);
+// Splits one bin's nodes (indices first .. first + count - 1, sorted by stencil origin; org[i]
+// is node i's origin as a tile offset) into groups of at most 32 nodes in which two nodes have
+// either the same origin or origins in different shared-memory banks (offsets that differ mod
+// 32).  A lane per node then reads the node's stencil (the same offsets from every origin)
+// without bank conflicts.  Greedy: origins with the most remaining nodes first, each group
+// taking as many nodes of one origin as fit.  Appends the bin's new node order to `order` and
+// each group's size to `sizes`.
+void build_node_groups(const int32_t *org, int64_t first, int64_t count, std::vector<int64_t> &order,
+                       std::vector<int> &sizes);
+
+// Bin shapes (stencil-origin cells per array axis).  3D: 1 = 8 x 8 x 8, 2 = 4 x 8 x 8,
+// 3 = 8 x 16 x 16, 4 = 16 x 16 x 16; 2D: 16 x 16 for every shape.  The kernels are compiled
+// per shape (FP32 3D: shapes 1, 3, 4; FP64 3D: 1, 2; 2D: 1), so a plan's bins always match the
+// tile geometry of its kernels.  A tile is bin + w - 1 cells per axis.
+static constexpr int NBIN_SHAPES = 4;
+__host__ __device__ constexpr int bin_dim(int d, int bs, int axis) {
+    return d == 2 ? (axis < 2 ? 16 : 1)
+                  : (bs == 2 ? (axis == 0 ? 4 : 8)
+                             : bs == 3 ? (axis == 0 ? 8 : 16) : bs == 4 ? 16 : 8);
+}
+// Whether kernels are compiled for a (precision, dimension, shape).
+__host__ __device__ constexpr bool bin_shape_built(bool fp64, int d, int bs) {
+    return d == 2 ? bs == 1 : (fp64 ? (bs == 1 || bs == 2) : (bs == 1 || bs == 3 || bs == 4));
+}
+// The shape a plan takes when none is requested: FP64 3D 4 x 8 x 8 for w >= 10 (tile within
+// 100 KB of shared memory), else 8 x 8 x 8; FP32 3D 8 x 16 x 16.
+__host__ __device__ constexpr int default_bin_shape(bool fp64, int d, int w) {
+    return d == 2 ? 1 : (fp64 ? (w >= 10 ? 2 : 1) : 3);
 }
 
 static constexpr int NODE_MAXW = 16;     // widest stencil
@@ -158,8 +192,38 @@ __host__ __device__ constexpr int node_lanes(int w) {
 }
 static constexpr int NODE_THREADS = 256;  // threads per interpolation / spreading CTA
 
+// Shared-memory row pitch of a 3D FP32 tile (cells between consecutive axis-1 rows; at least
+// the tile extent bin + w - 1 along axis 2).  A node's lanes read (or add to) its w*w stencil
+// columns, at offsets pitch * q_a + q_b, in passes of node_lanes(w) lanes; the smallest pitch
+// whose offsets fall at most `passes` times in any of the 32 banks lets every pass hit distinct
+// banks (an 8 x 16 x 16 bin at w = 7 has rows of 22 cells, whose offsets miss three banks and
+// doubled a third of all shared wavefronts; a pitch of 23 removes that).  FP64 and 2D tiles
+// keep the extent.
+__host__ __device__ constexpr int tile_pitch(bool fp64, int d, int w, int bs) {
+    const int t2 = (d == 3 ? bin_dim(d, bs, 2) : bin_dim(d, bs, 1)) + w - 1;
+    if (fp64 || d != 3) return t2;
+    const int lanes = node_lanes(w), passes = (w * w + lanes - 1) / lanes;
+    for (int p = t2; p < t2 + 9; p++) {
+        int cnt[32] = {};
+        int mx = 0;
+        for (int a = 0; a < w; a++)
+            for (int b = 0; b < w; b++) {
+                const int r = (p * a + b) % 32;
+                cnt[r]++;
+                mx = cnt[r] > mx ? cnt[r] : mx;
+            }
+        if (mx <= passes) return p;
+    }
+    return t2;
+}
+
 int tile_cells(const NodeDesc &nd);
 size_t node_smem(const NodeDesc &nd, int prec);
+// Dynamic shared memory of the node kernels for a plan geometry (tile planes, plus the FP64
+// kernels' per-warp stencil-value tables); must not exceed NODE_SMEM_MAX.
+size_t node_smem_for(int prec, int d, int w, int bs);
+// (the opt-in limit per CTA, 227 KB, less 1 KB for the kernels' static shared arrays)
+static constexpr size_t NODE_SMEM_MAX = 227 * 1024 - 1024;
 
 // c_out[j] = (apply_W ? W_j : 1) rho_hat_j / h^d; with epart != NULL nothing is written to
 // c_out and each CTA writes sum_j W_j |rho_hat_j / h^d|^2 over its nodes to epart[cta]
@@ -170,12 +234,13 @@ template <typename T>
 cudaError_t launch_spread(const NodeDesc &nd, const void *c_in, void *Hext, cudaStream_t s);
 template <typename T>
 cudaError_t launch_crowd_merge(const NodeDesc &nd, void *Hext, cudaStream_t s);
-// per (precision, dimension) launchers, one translation unit each (width dispatch inside)
-template <typename T, int D>
-cudaError_t launch_interp_d(const NodeDesc &nd, const void *G, void *c_out, int apply_W,
-                            double2 *epart, cudaStream_t s);
-template <typename T, int D>
-cudaError_t launch_spread_d(const NodeDesc &nd, const void *c_in, void *Hext, cudaStream_t s);
+// per (precision, dimension, bin shape) launchers, one translation unit each (width dispatch
+// inside); only the combinations bin_shape_built() names exist
+template <typename T, int D, int BS>
+cudaError_t launch_interp_bs(const NodeDesc &nd, const void *G, void *c_out, int apply_W,
+                             double2 *epart, cudaStream_t s);
+template <typename T, int D, int BS>
+cudaError_t launch_spread_bs(const NodeDesc &nd, const void *c_in, void *Hext, cudaStream_t s);
 template <typename T, int D>
 cudaError_t launch_crowd_merge_d(const NodeDesc &nd, void *Hext, cudaStream_t s);
 

@@ -1,11 +1,15 @@
 // Type-2 interpolation with the multiply by W_j, and type-1 spreading (steps a3, a4 and a5 of
-// the path; Algorithm 1, eq. 3.2 and eq. 3.7), templated on the stencil width so that every
-// loop over the stencil is unrolled and every tile index is a compile-time product.
+// the path; Algorithm 1, eq. 3.2 and eq. 3.7), templated on the stencil width and the bin
+// shape so that every loop over the stencil is unrolled and every tile index is a
+// compile-time product.
 //
 // Spreading function: the "exponential of semicircle" of Barnett, Magland and af Klinteberg
 // (SIAM J. Sci. Comput. 2019), phi(z) = exp(beta (sqrt(1 - z^2) - 1)) on |z| <= 1, with
-// z = (l - g) / (w/2) for fine cell l and node position g in fine-cell units.  The nodes are
-// fixed per plan, so the plan evaluates phi for every node and axis once, in FP64.
+// z = (l - g) / (w/2) for fine cell l and node position g in fine-cell units.  FP64 plans
+// evaluate phi for every node and axis once on the host, in FP64, and the kernels read those
+// values; FP32 kernels evaluate phi from each node's fractional offsets in registers (a
+// 16-byte record per node instead of d w stored values) and hand the values to the lanes
+// that need them by warp shuffles.
 //
 // Only the half node set (k on the non-negative side of array axis 0) is processed:
 // rho_hat(-k) = conj(rho_hat(k)) for a real density, and the mirrored nodes' spreading is
@@ -35,13 +39,17 @@ namespace nlint {
 static constexpr int MAXW = NODE_MAXW;
 static constexpr int SUB_THREADS = NODE_THREADS;
 
-template <typename T, int D, int W>
+template <typename T, int D, int W, int BS>
 struct Geo {
     static constexpr bool F64 = sizeof(T) == 8;
-    static constexpr int B0 = bin_extent(F64, D, W, 0), B1 = bin_extent(F64, D, W, 1);
-    static constexpr int B2 = (D == 3) ? bin_extent(F64, D, W, 2) : 1;
+    static constexpr int B0 = bin_dim(D, BS, 0), B1 = bin_dim(D, BS, 1);
+    static constexpr int B2 = (D == 3) ? bin_dim(D, BS, 2) : 1;
     static constexpr int T0 = B0 + W - 1, T1 = B1 + W - 1, T2 = (D == 3) ? B2 + W - 1 : 1;
-    static constexpr int NCELL = T0 * T1 * T2;
+    // shared layout: axis-2 rows of P2 >= T2 cells (padded against bank conflicts), planes of
+    // T1 rows; cells with axis-2 offset >= T2 are padding that no stencil touches
+    static constexpr int P2 = (D == 3) ? tile_pitch(F64, D, W, BS) : 1;
+    static constexpr int PLANE = (D == 3) ? T1 * P2 : T1;
+    static constexpr int NCELL = T0 * PLANE;
     static constexpr int PAIRS = W * W;  // stencil columns per node
     // lanes per node: 16 (two nodes per warp) when that wastes fewer lane slots, else 32
     static constexpr int LPN = node_lanes(W);
@@ -72,6 +80,226 @@ __device__ __forceinline__ cx_t<T> fetch_half(const cx_t<T> *__restrict__ G, int
     return cconj(G[(int64_t)mz * n + wrapn(-l1, n)]);
 }
 
+// ---------------------------------------------------------------- shared by both precisions
+
+// Decompose a tile cell into its per-axis offsets.
+template <typename G_>
+__device__ __forceinline__ void cell_coords(int cell, int &a0, int &a1, int &a2) {
+    a0 = cell / G_::PLANE;
+    const int rem = cell - a0 * G_::PLANE;
+    a1 = rem / G_::P2;
+    a2 = rem - a1 * G_::P2;
+}
+
+// Tile offset of stencil column (qa, qb) for the origin (r0, r1, r2), axis-0 run start:
+// origin_index(r0, r1, r2) + column_offset(qa, qb).
+template <typename G_, int D>
+__device__ __forceinline__ int origin_index(int r0, int r1, int r2) {
+    return (D == 3) ? (r0 * G_::T1 + r1) * G_::P2 + r2 : r0 * G_::T1 + r1;
+}
+template <typename G_, int D>
+__device__ __forceinline__ int column_offset(int qa, int qb) {
+    return (D == 3) ? qa * G_::P2 + qb : qa * G_::T1 + qb;
+}
+
+// Each warp owns a contiguous run of its subproblem's nodes.
+// (32-bit: a subproblem holds at most 2^20 nodes; the warp count is the compile-time
+// SUB_THREADS / 32, so the division is a shift.)
+__device__ __forceinline__ void warp_chunk(int4 sb, int wid, int &ja, int &jb) {
+    constexpr int NW = SUB_THREADS / 32;
+    ja = sb.x + (sb.y * wid) / NW;
+    jb = sb.x + (sb.y * (wid + 1)) / NW;
+}
+
+
+// Stages the bin's tile of G (T0 x T1 (x T2) cells from the bin origin) in shared memory as
+// real and imaginary planes.  The common case (axis-0 planes inside the stored half) goes by
+// (axis-1, axis-2) column: its wrapped offsets and base index once, then the T0 planes at a
+// constant stride; tiles that reach outside the stored half read the mirror by conjugation.
+template <typename T, typename G_, int D>
+__device__ __forceinline__ void stage_tile(const cx_t<T> *__restrict__ G, int4 bo, int n, T *tr, T *ti) {
+    using T2 = cx_t<T>;
+    constexpr int PLANE = G_::PLANE;
+    const bool inside = bo.x >= 0 && bo.x + G_::T0 - 1 <= n / 2;
+    if (D == 3 && inside) {
+        const int64_t nn = (int64_t)n * n;
+        for (int col = threadIdx.x; col < PLANE; col += blockDim.x) {
+            const int a1 = col / G_::P2, a2 = col - a1 * G_::P2;
+            if (a2 >= G_::T2) continue;  // row padding
+            const T2 *g = G + ((int64_t)bo.x * n + wrap1(bo.y + a1, n)) * n + wrap1(bo.z + a2, n);
+            constexpr int GRP = 4;  // planes in flight per thread (bounds the registers)
+#pragma unroll 1
+            for (int a0b = 0; a0b < G_::T0; a0b += GRP) {
+                T2 v[GRP];
+#pragma unroll
+                for (int k = 0; k < GRP; k++)
+                    if (a0b + k < G_::T0) v[k] = g[(a0b + k) * nn];
+#pragma unroll
+                for (int k = 0; k < GRP; k++)
+                    if (a0b + k < G_::T0) {
+                        tr[(a0b + k) * PLANE + col] = v[k].x;
+                        ti[(a0b + k) * PLANE + col] = v[k].y;
+                    }
+            }
+        }
+    } else {
+        for (int cell = threadIdx.x; cell < G_::NCELL; cell += blockDim.x) {
+            int a0, a1, a2;
+            cell_coords<G_>(cell, a0, a1, a2);
+            if (D == 3 && a2 >= G_::T2) continue;  // row padding
+            T2 v;
+            if (inside) {
+                const int l0 = bo.x + a0, l1 = wrap1(bo.y + a1, n);
+                v = (D == 3) ? G[((int64_t)l0 * n + l1) * n + wrap1(bo.z + a2, n)] : G[(int64_t)l0 * n + l1];
+            } else {
+                v = fetch_half<T, D>(G, n, bo.x + a0, bo.y + a1, bo.z + a2);
+            }
+            tr[cell] = v.x;
+            ti[cell] = v.y;
+        }
+    }
+}
+
+__device__ __forceinline__ void atomic_add_cx(float2 *p, float re, float im) {
+    atomicAdd(p, make_float2(re, im));
+}
+__device__ __forceinline__ void atomic_add_cx(double2 *p, double re, double im) {
+    atomicAdd(&p->x, re);
+    atomicAdd(&p->y, im);
+}
+
+// Adds a spreading tile of fixed-point sums (multiples of 2^-ex) into the extended spread grid
+// H+ (planes -pad .. n/2 + pad of axis 0) with global atomics, or, for a crowded bin (bo.w is
+// its crowd slot), exactly into its FP64 tile.  Zero cells are skipped.
+template <typename T, typename G_, int D, typename A>
+__device__ __forceinline__ void flush_tile(const A *tr, const A *ti, int4 bo, const NodeDesc &nd, int ex,
+                                           cx_t<T> *__restrict__ H) {
+    constexpr int PLANE = G_::PLANE;
+    const int n = nd.n, pad = nd.pad, slot = bo.w;
+    const int nplanes = n / 2 + 1 + 2 * pad;
+    const T inv_s = (T)ldexp(1.0, -ex);
+    if (D == 3 && slot < 0) {
+        // by (axis-1, axis-2) column, as the tile load: wrapped offsets once, then the planes of
+        // the extended grid at a constant stride
+        const int64_t nn = (int64_t)n * n;
+        for (int col = threadIdx.x; col < PLANE; col += blockDim.x) {
+            const int a1 = col / G_::P2, a2 = col - a1 * G_::P2;
+            if (a2 >= G_::T2) continue;  // row padding (never added to)
+            const int64_t gb = (int64_t)wrap1(bo.y + a1, n) * n + wrap1(bo.z + a2, n);
+#pragma unroll 4
+            for (int a0 = 0; a0 < G_::T0; a0++) {
+                const A qr = tr[a0 * PLANE + col], qi = ti[a0 * PLANE + col];
+                const int pl = bo.x + a0 + pad;
+                if ((qr == 0 && qi == 0) || pl < 0 || pl >= nplanes) continue;
+                atomic_add_cx(H + pl * nn + gb, (T)qr * inv_s, (T)qi * inv_s);
+            }
+        }
+        return;
+    }
+    constexpr int TCELL = G_::T0 * G_::T1 * G_::T2;  // unpadded cells: the crowd tile's layout
+    for (int cell = threadIdx.x; cell < G_::NCELL; cell += blockDim.x) {
+        const A qr = tr[cell], qi = ti[cell];
+        if (qr == 0 && qi == 0) continue;  // (row padding is never added to: always zero)
+        int a0, a1, a2;
+        cell_coords<G_>(cell, a0, a1, a2);
+        if (slot >= 0) {  // crowded bin: FP64 sum across its subproblems (exact: q / 2^ex)
+            const double is = ldexp(1.0, -ex);
+            const int tc = (a0 * G_::T1 + a1) * G_::T2 + a2;
+            atomic_add_cx(nd.crowd + (int64_t)slot * TCELL + tc, (double)qr * is, (double)qi * is);
+            continue;
+        }
+        const int pl = bo.x + a0 + pad;
+        if (pl < 0 || pl >= nplanes) continue;  // outside every stencil: the cell is zero
+        const int64_t g = (D == 3)
+            ? ((int64_t)pl * n + wrap1(bo.y + a1, n)) * n + wrap1(bo.z + a2, n)
+            : (int64_t)pl * n + wrap1(bo.y + a1, n);
+        atomic_add_cx(H + g, (T)qr * inv_s, (T)qi * inv_s);
+    }
+}
+
+// Fixed-point accumulation of the spreading tile.  Shared-memory floating-point atomics are
+// several times slower than integer ones on this GPU, so each CTA adds integer multiples of
+// 1/S: S = 2^(E - ceil(log2 B)) with B >= max(sum_j |Re c_j|, sum_j |Im c_j|) over the
+// subproblem (every cell sum and every contribution is at most B, since phi <= 1), E = 29 for
+// FP32 (int32 cells) and 50 for FP64 (int64 cells), so no cell can overflow.  Each
+// contribution is rounded to 1/S <= 2^-E B (FP32: 2^-29 B, finer than FP32 rounding of the
+// largest cells; FP64: 2^-50 B); the integer sums are exact, so a tile does not depend on the
+// order of its additions.  FP64 rounds with one fused multiply-add: a * b + 1.5 * 2^52 lies in
+// [2^52, 2^53) for |a * b| < 2^51, where the spacing of doubles is 1, so its low mantissa bits
+// are a * b rounded to the nearest integer (the classic magic-number conversion) -- one
+// operation on the FP64 units, which bound the FP64 path, instead of a multiply and a convert.
+// FP32 3D forms the product in integers instead (see mulq31).
+template <typename T> struct FixAcc;
+template <> struct FixAcc<float> {
+    using A = int;
+    static constexpr int E = 29, MAXEXP = 126;
+    __device__ __forceinline__ static void add(A *p, A v) { atomicAdd(p, v); }
+};
+template <> struct FixAcc<double> {
+    using A = long long;
+    static constexpr int E = 50, MAXEXP = 1000;
+    __device__ __forceinline__ static A mulq(double a, double b) {
+        constexpr double MAGIC = 6755399441055744.0;  // 1.5 * 2^52
+        return __double_as_longlong(fma(a, b, MAGIC)) - __double_as_longlong(MAGIC);
+    }
+    __device__ __forceinline__ static void add(A *p, A v) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)v);
+    }
+};
+
+// Scale exponent of a spreading CTA: reads the subproblem's c values, sums |Re| and |Im| over
+// the CTA (the bound B above), clears the tile and returns ex with S = 2^ex (S B <= 2^E), or
+// INT_MIN when the subproblem adds nothing (all c zero) or a c is not finite (then the first
+// cell of H+ is set to NaN, which the first inverse pass folds into every output, as a
+// floating-point accumulation would).  `red` is 2 * (SUB_THREADS / 32) entries of shared
+// scratch.
+template <typename T, typename A, int NCELL, int E, int MAXEXP>
+__device__ __forceinline__ int spread_scale(const cx_t<T> *__restrict__ c_in, int4 sb, A *tr, A *ti,
+                                            T *red, cx_t<T> *__restrict__ H) {
+    using T2 = cx_t<T>;
+    constexpr int nw = SUB_THREADS / 32;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    T bre = T(0), bim = T(0);
+    for (int i = threadIdx.x; i < sb.y; i += blockDim.x) {
+        const T2 v = c_in[sb.x + i];
+        bre += fabs(v.x);
+        bim += fabs(v.y);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        bre += __shfl_xor_sync(0xffffffffu, bre, off);
+        bim += __shfl_xor_sync(0xffffffffu, bim, off);
+    }
+    for (int cell = threadIdx.x; cell < NCELL; cell += blockDim.x) {
+        tr[cell] = 0;
+        ti[cell] = 0;
+    }
+    if (lane == 0) {
+        red[2 * wid] = bre;
+        red[2 * wid + 1] = bim;
+    }
+    __syncthreads();
+    T sre = T(0), sim = T(0);
+    for (int q = 0; q < nw; q++) {
+        sre += red[2 * q];
+        sim += red[2 * q + 1];
+    }
+    // B to within rounding (<= 1024 terms: a relative 1e-4 in FP32, 1e-13 in FP64); the room
+    // above 2^E absorbs it (FP32: int32 cells, 4x; FP64: contributions below 2^51 for the
+    // rounding by fused multiply-add, 2x)
+    // (fmax drops a NaN operand: a non-finite sum makes the bound NaN explicitly)
+    const T bound = (isfinite(sre) && isfinite(sim)) ? fmax(sre, sim) : T(NAN);
+    if (!(bound > T(0))) {
+        if (bound != T(0) && threadIdx.x == 0) H[0] = cmake<T2>(T(NAN), T(NAN));
+        return INT_MIN;
+    }
+    int ex = E - ilogb(bound) - 1;  // S = 2^ex, S * bound <= 2^E
+    if (ex > MAXEXP) ex = MAXEXP;    // tiny bounds: keep S finite (cells stay < 2^E)
+    return ex;
+}
+
+// ------------------------------------------------- FP64: stencil values precomputed per node
+
 // A warp works on NPW = 32 / LPN nodes at a time (one per LPN-lane group): per node its lanes
 // share the w*w stencil columns, and the nodes share the warp's per-node work (loads, shuffle
 // reductions).  NodeGroup holds this lane's view: the stencil origin of its group's node
@@ -79,7 +307,7 @@ __device__ __forceinline__ cx_t<T> fetch_half(const cx_t<T> *__restrict__ G, int
 // computed once (the nodes are fixed).
 template <typename T, int D, int W>
 struct NodeGroup {
-    static constexpr int LPN = Geo<T, D, W>::LPN, NPW = Geo<T, D, W>::NPW;
+    static constexpr int LPN = Geo<T, D, W, 1>::LPN, NPW = Geo<T, D, W, 1>::NPW;
     static constexpr int NKV = NPW * D * W;        // kernel values of the group
     static constexpr int KV = (NKV + 31) / 32;     // ... per lane
     int r0, r1, r2;
@@ -121,85 +349,24 @@ __device__ __forceinline__ void warp_kernel_values(const NodeGroup<T, D, W> &np,
         if (slot[v] >= 0) ker[slot[v]] = np.kv[v];
 }
 
-// Decompose a tile cell into its per-axis offsets.
-template <typename G_>
-__device__ __forceinline__ void cell_coords(int cell, int &a0, int &a1, int &a2) {
-    a0 = cell / (G_::T1 * G_::T2);
-    const int rem = cell - a0 * (G_::T1 * G_::T2);
-    a1 = rem / G_::T2;
-    a2 = rem - a1 * G_::T2;
-}
-
-// Tile offset of stencil column (qa, qb) for the origin (r0, r1, r2), axis-0 run start:
-// origin_index(r0, r1, r2) + column_offset(qa, qb).
-template <typename G_, int D>
-__device__ __forceinline__ int origin_index(int r0, int r1, int r2) {
-    return (D == 3) ? (r0 * G_::T1 + r1) * G_::T2 + r2 : r0 * G_::T1 + r1;
-}
-template <typename G_, int D>
-__device__ __forceinline__ int column_offset(int qa, int qb) {
-    return (D == 3) ? qa * G_::T2 + qb : qa * G_::T1 + qb;
-}
-
-// Each warp owns a contiguous run of its subproblem's nodes.
-// (32-bit: a subproblem holds at most 2^20 nodes; the warp count is the compile-time
-// SUB_THREADS / 32, so the division is a shift.)
-__device__ __forceinline__ void warp_chunk(int4 sb, int wid, int &ja, int &jb) {
-    constexpr int NW = SUB_THREADS / 32;
-    ja = sb.x + (sb.y * wid) / NW;
-    jb = sb.x + (sb.y * (wid + 1)) / NW;
-}
-
-// Fixed-point accumulation of the spreading tile.  Shared-memory floating-point atomics are
-// several times slower than integer ones on this GPU, so each CTA adds integer multiples of
-// 1/S: S = 2^(E - ceil(log2 B)) with B >= max(sum_j |Re c_j|, sum_j |Im c_j|) over the
-// subproblem (every cell sum and every contribution is at most B, since phi <= 1), E = 29 for
-// FP32 (int32 cells) and 50 for FP64 (int64 cells), so no cell can overflow.  Each
-// contribution a * b is rounded to 1/S <= 2^-E B (FP32: 2^-29 B, finer than FP32 rounding of the
-// largest cells; FP64: 2^-50 B); the integer sums are exact, so a tile does not depend on the
-// order of its additions.  FP64 rounds with one fused multiply-add: a * b + 1.5 * 2^52 lies in
-// [2^52, 2^53) for |a * b| < 2^51, where the spacing of doubles is 1, so its low mantissa bits
-// are a * b rounded to the nearest integer (the classic magic-number conversion) -- one
-// operation on the FP64 units, which bound the FP64 path, instead of a multiply and a convert.
-template <typename T> struct FixAcc;
-template <> struct FixAcc<float> {
-    using A = int;
-    static constexpr int E = 29, MAXEXP = 126;
-    __device__ __forceinline__ static A mulq(float a, float b) { return __float2int_rn(a * b); }
-    __device__ __forceinline__ static void add(A *p, A v) { atomicAdd(p, v); }
-};
-template <> struct FixAcc<double> {
-    using A = long long;
-    static constexpr int E = 50, MAXEXP = 1000;
-    __device__ __forceinline__ static A mulq(double a, double b) {
-        constexpr double MAGIC = 6755399441055744.0;  // 1.5 * 2^52
-        return __double_as_longlong(fma(a, b, MAGIC)) - __double_as_longlong(MAGIC);
-    }
-    __device__ __forceinline__ static void add(A *p, A v) {
-        atomicAdd(reinterpret_cast<unsigned long long *>(p), (unsigned long long)v);
-    }
-};
-
-template <typename T, int D, int W, bool EN>
+template <typename T, int D, int W, int BS, bool EN>
 __global__ void __launch_bounds__(SUB_THREADS) interp_sub_kernel(NodeDesc nd,
                                                                 const cx_t<T> *__restrict__ G,
                                                                 cx_t<T> *__restrict__ c_out,
                                                                 int apply_W,
                                                                 double2 *__restrict__ epart) {
     using T2 = cx_t<T>;
-    using G_ = Geo<T, D, W>;
-    constexpr int PASSES = G_::PASSES, L = (D == 3) ? W : 1, PLANE = G_::T1 * G_::T2;
+    using G_ = Geo<T, D, W, BS>;
+    constexpr int PASSES = G_::PASSES, L = (D == 3) ? W : 1, PLANE = G_::PLANE;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // the tile as real and imaginary planes (measured faster than interleaved complex, whose
     // one 8-byte load per stencil cell cost registers and resident CTAs)
     T *tr = reinterpret_cast<T *>(smem_raw);
     T *ti = tr + G_::NCELL;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    constexpr int nw = SUB_THREADS / 32;  // the kernels are launched with SUB_THREADS threads
     T *ker = ti + G_::NCELL + wid * 6 * MAXW;
     const int4 sb = nd.subs[blockIdx.x];
     const int4 bo = nd.bins[sb.z];
-    const int n = nd.n;
     // this lane's stencil columns, one per pass (-1: idle), as tile offsets and kernel-table
     // offsets of the two column axes; its slots in the warp's kernel table
     int coff[PASSES], kab_off[PASSES], kslot[NodeGroup<T, D, W>::KV];
@@ -213,45 +380,7 @@ __global__ void __launch_bounds__(SUB_THREADS) interp_sub_kernel(NodeDesc nd,
 #pragma unroll
     for (int v = 0; v < NodeGroup<T, D, W>::KV; v++) kslot[v] = kernel_slot<T, D, W>(lane, v);
 
-    // stage the tile; the common case (axis-0 planes inside the stored half) needs no mirror
-    const bool inside = bo.x >= 0 && bo.x + G_::T0 - 1 <= n / 2;
-    if (D == 3 && inside) {
-        // by (axis-1, axis-2) column: its wrapped offsets and base index once, then the T0
-        // planes at a constant stride (no per-cell index decomposition)
-        const int64_t nn = (int64_t)n * n;
-        for (int col = threadIdx.x; col < PLANE; col += blockDim.x) {
-            const int a1 = col / G_::T2, a2 = col - a1 * G_::T2;
-            const T2 *g = G + ((int64_t)bo.x * n + wrap1(bo.y + a1, n)) * n + wrap1(bo.z + a2, n);
-            constexpr int GRP = 4;  // planes in flight per thread (bounds the registers)
-#pragma unroll 1
-            for (int a0b = 0; a0b < G_::T0; a0b += GRP) {
-                T2 v[GRP];
-#pragma unroll
-                for (int k = 0; k < GRP; k++)
-                    if (a0b + k < G_::T0) v[k] = g[(a0b + k) * nn];
-#pragma unroll
-                for (int k = 0; k < GRP; k++)
-                    if (a0b + k < G_::T0) {
-                        tr[(a0b + k) * PLANE + col] = v[k].x;
-                        ti[(a0b + k) * PLANE + col] = v[k].y;
-                    }
-            }
-        }
-    } else {
-        for (int cell = threadIdx.x; cell < G_::NCELL; cell += blockDim.x) {
-            int a0, a1, a2;
-            cell_coords<G_>(cell, a0, a1, a2);
-            T2 v;
-            if (inside) {
-                const int l0 = bo.x + a0, l1 = wrap1(bo.y + a1, n);
-                v = (D == 3) ? G[((int64_t)l0 * n + l1) * n + wrap1(bo.z + a2, n)] : G[(int64_t)l0 * n + l1];
-            } else {
-                v = fetch_half<T, D>(G, n, bo.x + a0, bo.y + a1, bo.z + a2);
-            }
-            tr[cell] = v.x;
-            ti[cell] = v.y;
-        }
-    }
+    stage_tile<T, G_, D>(G, bo, nd.n, tr, ti);
     __syncthreads();
 
     int ja, jb;
@@ -310,32 +439,23 @@ __global__ void __launch_bounds__(SUB_THREADS) interp_sub_kernel(NodeDesc nd,
     }
 }
 
-__device__ __forceinline__ void atomic_add_cx(float2 *p, float re, float im) {
-    atomicAdd(p, make_float2(re, im));
-}
-__device__ __forceinline__ void atomic_add_cx(double2 *p, double re, double im) {
-    atomicAdd(&p->x, re);
-    atomicAdd(&p->y, im);
-}
-
-template <typename T, int D, int W>
+template <typename T, int D, int W, int BS>
 __global__ void __launch_bounds__(SUB_THREADS) spread_sub_kernel(NodeDesc nd,
                                                                 const cx_t<T> *__restrict__ c_in,
                                                                 cx_t<T> *__restrict__ H) {
     using T2 = cx_t<T>;
-    using G_ = Geo<T, D, W>;
+    using G_ = Geo<T, D, W, BS>;
     using F = FixAcc<T>;
     using A = typename F::A;
-    constexpr int PASSES = G_::PASSES, L = (D == 3) ? W : 1, PLANE = G_::T1 * G_::T2;
+    constexpr int PASSES = G_::PASSES, L = (D == 3) ? W : 1, PLANE = G_::PLANE;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     A *tr = reinterpret_cast<A *>(smem_raw);
     A *ti = tr + G_::NCELL;
+    __shared__ T red[2 * (SUB_THREADS / 32)];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    constexpr int nw = SUB_THREADS / 32;  // the kernels are launched with SUB_THREADS threads
     T *ker = reinterpret_cast<T *>(ti + G_::NCELL) + wid * 6 * MAXW;
     const int4 sb = nd.subs[blockIdx.x];
     const int4 bo = nd.bins[sb.z];
-    const int n = nd.n, pad = nd.pad;
     // per-lane constants (see the interpolation kernel)
     int coff[PASSES], kab_off[PASSES], kslot[NodeGroup<T, D, W>::KV];
 #pragma unroll
@@ -348,50 +468,9 @@ __global__ void __launch_bounds__(SUB_THREADS) spread_sub_kernel(NodeDesc nd,
 #pragma unroll
     for (int v = 0; v < NodeGroup<T, D, W>::KV; v++) kslot[v] = kernel_slot<T, D, W>(lane, v);
 
-    // bound B = max(sum |Re c_j|, sum |Im c_j|) over the subproblem, while the tile is cleared
-    T bre = T(0), bim = T(0);
-    for (int i = threadIdx.x; i < sb.y; i += blockDim.x) {
-        const T2 v = c_in[sb.x + i];
-        bre += fabs(v.x);
-        bim += fabs(v.y);
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        bre += __shfl_xor_sync(0xffffffffu, bre, off);
-        bim += __shfl_xor_sync(0xffffffffu, bim, off);
-    }
-    for (int cell = threadIdx.x; cell < G_::NCELL; cell += blockDim.x) {
-        tr[cell] = 0;
-        ti[cell] = 0;
-    }
-    if (lane == 0) {
-        ker[0] = bre;  // the warp's kernel table is free until the node loop
-        ker[1] = bim;
-    }
-    __syncthreads();
-    T sre = T(0), sim = T(0);
-    for (int q = 0; q < nw; q++) {
-        const T *kq = reinterpret_cast<T *>(ti + G_::NCELL) + q * 6 * MAXW;
-        sre += kq[0];
-        sim += kq[1];
-    }
-    // B to within rounding (<= 1024 terms: a relative 1e-4 in FP32, 1e-13 in FP64); the room
-    // above 2^E absorbs it (FP32: int32 cells, 4x; FP64: contributions below 2^51 for the
-    // rounding by fused multiply-add, 2x)
-    // (fmax drops a NaN operand: a non-finite sum makes the bound NaN explicitly)
-    const T bound = (isfinite(sre) && isfinite(sim)) ? fmax(sre, sim) : T(NAN);
-    if (!(bound > T(0))) {
-        // zero: every c_j of the subproblem is zero, nothing to add.  Non-finite: a c_j has no
-        // fixed-point image; a NaN in the grid's first cell (the plane below the stored half,
-        // folded into the half by the first inverse pass) reaches every u as it would without
-        // the fixed-point accumulation (NaN absorbs any concurrent addition to the cell)
-        if (bound != T(0) && threadIdx.x == 0) H[0] = cmake<T2>(T(NAN), T(NAN));
-        return;
-    }
-    int ex = F::E - ilogb(bound) - 1;  // S = 2^ex, S * bound <= 2^E
-    if (ex > F::MAXEXP) ex = F::MAXEXP;   // tiny bounds: keep S finite (cells stay < 2^E)
-    const T S = (T)ldexp(1.0, ex), inv_s = (T)ldexp(1.0, -ex);
-    __syncthreads();  // every warp has read the bound before the tables are overwritten
+    const int ex = spread_scale<T, A, G_::NCELL, F::E, F::MAXEXP>(c_in, sb, tr, ti, red, H);
+    if (ex == INT_MIN) return;
+    const T S = (T)ldexp(1.0, ex);
 
     int ja, jb;
     warp_chunk(sb, wid, ja, jb);
@@ -437,72 +516,628 @@ __global__ void __launch_bounds__(SUB_THREADS) spread_sub_kernel(NodeDesc nd,
         c = cn;
     }
     __syncthreads();
+    flush_tile<T, G_, D, A>(tr, ti, bo, nd, ex, H);
+}
 
-    const int slot = bo.w;
-    const int nplanes = n / 2 + 1 + 2 * pad;
-    if (D == 3 && slot < 0) {
-        // by (axis-1, axis-2) column, as the interpolation's tile load: wrapped offsets once,
-        // then the planes of the extended grid at a constant stride
-        const int64_t nn = (int64_t)n * n;
-        for (int col = threadIdx.x; col < PLANE; col += blockDim.x) {
-            const int a1 = col / G_::T2, a2 = col - a1 * G_::T2;
-            const int64_t gb = (int64_t)wrap1(bo.y + a1, n) * n + wrap1(bo.z + a2, n);
+// ------------------------------------------ FP32: stencil values evaluated from the offsets
+
+// phi(z) = exp(beta (sqrt(1 - z^2) - 1)) for |z| <= 1, written as exp(-beta z^2 / (1 +
+// sqrt(1 - z^2))): the second form has no cancellation next to z = 0, where phi is largest, so
+// its FP32 rounding stays a few ulps relative for the values that matter.  1 - z^2 is clamped
+// at 0, so a z that rounds onto +-1 gives exp(-beta), the limit from inside.  The truncated
+// function jumps from exp(-beta) to 0 at |z| = 1 (1e-4 at w = 4, 1e-7 at w = 7): which cells
+// take the jump is decided exactly, from the offsets (see F32Lane::values), never by rounding.
+__device__ __forceinline__ float es_phi_f32(float z, float beta) {
+    const float z2 = z * z;
+    const float t = fmaxf(1.0f - z2, 0.0f);
+    const float s = t * rsqrtf(fmaxf(t, 1e-30f));
+    return __expf(__fdividef(-beta * z2, 1.0f + s));
+}
+
+// Value slot t of the warp's group (slot t lives in register t / 32 of lane t % 32).
+template <int KV, typename V>
+__device__ __forceinline__ V shfl_slot(const V (&v)[KV], int t) {
+    V r = __shfl_sync(0xffffffffu, v[0], t & 31);
 #pragma unroll
-            for (int a0 = 0; a0 < G_::T0; a0++) {
-                const A qr = tr[a0 * PLANE + col], qi = ti[a0 * PLANE + col];
-                const int pl = bo.x + a0 + pad;
-                if ((qr == 0 && qi == 0) || pl < 0 || pl >= nplanes) continue;
-                atomic_add_cx(H + pl * nn + gb, (T)qr * inv_s, (T)qi * inv_s);
+    for (int k = 1; k < KV; k++) {
+        const V x = __shfl_sync(0xffffffffu, v[k], t & 31);
+        if ((t >> 5) == k) r = x;
+    }
+    return r;
+}
+
+// round(a b / 2^32) for |a| < 2^31 and 0 <= b < 2^31, as the high word of one 32 x 32 -> 64-bit
+// integer multiply-add (no float-to-integer conversion per stencil cell)
+__device__ __forceinline__ int mulq31(int a, int b) {
+    return (int)(((long long)a * (long long)b + 0x80000000LL) >> 32);
+}
+
+// Sums four per-lane values over the warp with five shuffles (a transposed butterfly: the
+// first two steps exchange halves of the value set, the last three sum one value): afterwards
+// lanes 0-7 hold the total of v0, 8-15 of v1, 16-23 of v2, 24-31 of v3.
+__device__ __forceinline__ float warp_sum4(float v0, float v1, float v2, float v3, int lane) {
+    const bool h16 = lane & 16, h8 = lane & 8;
+    float k0 = h16 ? v2 : v0, k1 = h16 ? v3 : v1;
+    k0 += __shfl_xor_sync(0xffffffffu, h16 ? v0 : v2, 16);
+    k1 += __shfl_xor_sync(0xffffffffu, h16 ? v1 : v3, 16);
+    float k = h8 ? k1 : k0;
+    k += __shfl_xor_sync(0xffffffffu, h8 ? k0 : k1, 8);
+    k += __shfl_xor_sync(0xffffffffu, k, 4);
+    k += __shfl_xor_sync(0xffffffffu, k, 2);
+    k += __shfl_xor_sync(0xffffffffu, k, 1);
+    return k;
+}
+
+// FP32 per-lane constants: this lane's value slots (node of the group, axis, and the cell's
+// part of z), and its columns' tile offsets and value slots.
+template <int D, int W, int BS>
+struct F32Lane {
+    using G_ = Geo<float, D, W, BS>;
+    static constexpr int LPN = G_::LPN, NPW = G_::NPW, DW = D * W, PASSES = G_::PASSES;
+    static constexpr int NKV = NPW * DW, KV = (NKV + 31) / 32;
+    int vnode[KV], vax[KV];
+    float vc[KV];                // (q + 1 - w/2) (2 / w) of the slot's cell q
+    bool vfirst[KV];             // the slot's cell is the first of its axis (q = 0)
+    int coff[PASSES], sa[PASSES], sb[PASSES];
+    __device__ __forceinline__ void init(const int16_t *__restrict__ pair_order, int lane) {
+        const int half = lane / LPN, hl = lane % LPN;
+#pragma unroll
+        for (int v = 0; v < KV; v++) {
+            const int t = lane + 32 * v;
+            if (t < NKV) {
+                const int h = t / DW, rem = t - h * DW, a = rem / W, q = rem - a * W;
+                vnode[v] = h;
+                vax[v] = a;
+                vc[v] = ((float)q + 1.0f - 0.5f * (float)W) * (2.0f / (float)W);
+                vfirst[v] = q == 0;
+            } else {
+                vnode[v] = -1;
+                vax[v] = 0;
+                vc[v] = 0.0f;
+                vfirst[v] = false;
             }
         }
-        return;
-    }
-    for (int cell = threadIdx.x; cell < G_::NCELL; cell += blockDim.x) {
-        const A qr = tr[cell], qi = ti[cell];
-        if (qr == 0 && qi == 0) continue;
-        if (slot >= 0) {  // crowded bin: FP64 sum across its subproblems (exact: q / 2^ex)
-            const double is = ldexp(1.0, -ex);
-            atomic_add_cx(nd.crowd + (int64_t)slot * G_::NCELL + cell, (double)qr * is, (double)qi * is);
-            continue;
+#pragma unroll
+        for (int ps = 0; ps < PASSES; ps++) {
+            const int pq = pair_order[ps * LPN + hl];
+            const int qa = pq >= 0 ? (pq >> 8) : 0, qb = pq >= 0 ? (pq & 255) : 0;
+            coff[ps] = pq >= 0 ? column_offset<G_, D>(qa, qb) : -1;
+            sa[ps] = half * DW + (D == 3 ? W : 0) + qa;
+            sb[ps] = half * DW + (D == 3 ? 2 * W : W) + qb;
         }
-        int a0, a1, a2;
-        cell_coords<G_>(cell, a0, a1, a2);
-        const int pl = bo.x + a0 + pad;
-        if (pl < 0 || pl >= nplanes) continue;  // outside every stencil: the cell is zero
-        const int64_t g = (D == 3)
-            ? ((int64_t)pl * n + wrap1(bo.y + a1, n)) * n + wrap1(bo.z + a2, n)
-            : (int64_t)pl * n + wrap1(bo.y + a1, n);
-        atomic_add_cx(H + g, (T)qr * inv_s, (T)qi * inv_s);
+    }
+    // this lane's stencil values of nodes j .. j + NPW - 1 (those below jb); `me` is the record
+    // of node j + lane / LPN, which serves every slot when NPW = 1.  With u in (0, 1], only the
+    // first cell can reach |z| = 1, exactly when u = 1; the plan stores u = 1 only for nodes
+    // whose FP64 offset is exactly w/2 (the FP64 plans' values are then 0 too) and rounds every
+    // other u below 1, so both precisions zero the same cells
+    __device__ __forceinline__ void values(const int4 *__restrict__ pos, int j, int jb, int4 me,
+                                           float beta, float (&phv)[KV]) const {
+#pragma unroll
+        for (int v = 0; v < KV; v++) {
+            float val = 0.0f;
+            const int nn = j + vnode[v];
+            if (vnode[v] >= 0 && nn < jb) {
+                const int4 r = (NPW == 1) ? me : pos[nn];
+                const float u = __int_as_float(vax[v] == 0 ? r.y : (vax[v] == 1 ? r.z : r.w));
+                if (!(vfirst[v] && u >= 1.0f)) val = es_phi_f32(fmaf(-u, 2.0f / (float)W, vc[v]), beta);
+            }
+            phv[v] = val;
+        }
+    }
+};
+
+template <int D, int W, int BS, bool EN>
+__global__ void __launch_bounds__(SUB_THREADS) interp_f32_kernel(NodeDesc nd, const float2 *__restrict__ G,
+                                                                float2 *__restrict__ c_out, int apply_W,
+                                                                double2 *__restrict__ epart) {
+    using G_ = Geo<float, D, W, BS>;
+    using LN = F32Lane<D, W, BS>;
+    constexpr int PASSES = G_::PASSES, L = (D == 3) ? W : 1, PLANE = G_::PLANE;
+    constexpr int LPN = G_::LPN, NPW = G_::NPW, KV = LN::KV, DW = D * W;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *tr = reinterpret_cast<float *>(smem_raw);
+    float *ti = tr + G_::NCELL;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int4 sb = nd.subs[blockIdx.x];
+    const int4 bo = nd.bins[sb.z];
+    LN ln;
+    ln.init(nd.pair_order_i, lane);
+    stage_tile<float, G_, D>(G, bo, nd.n, tr, ti);
+    __syncthreads();
+
+    int ja, jb;
+    warp_chunk(sb, wid, ja, jb);
+    const int half = lane / LPN, hl = lane % LPN;
+    const int4 *__restrict__ pos = nd.pos;
+    const float *__restrict__ Wv = reinterpret_cast<const float *>(nd.W);
+    const float beta = (float)nd.beta;
+    EAcc<float> eacc;
+    if constexpr (LPN == 32 && D == 3) {
+        // Two nodes per iteration (A = j, B = j + 1): both nodes' stencil values come from one
+        // evaluation pass over the lanes, their four sums are reduced together (warp_sum4), and
+        // when they share a stencil origin (about half of the pairs after the plan's sort by
+        // origin) each tile value is loaded once for both.
+        int4 rA_n = make_int4(0, 0, 0, 0), rB_n = make_int4(0, 0, 0, 0);
+        float WA_n = 1.0f, WB_n = 1.0f;
+        if (ja < jb) {
+            rA_n = pos[ja];
+            if (apply_W) WA_n = Wv[ja];
+        }
+        if (ja + 1 < jb) {
+            rB_n = pos[ja + 1];
+            if (apply_W) WB_n = Wv[ja + 1];
+        }
+        for (int j = ja; j < jb; j += 2) {
+            const bool hasB = j + 1 < jb;
+            const int4 rA = rA_n, rB = rB_n;
+            const float WA = WA_n, WB = WB_n;
+            if (j + 2 < jb) {
+                rA_n = pos[j + 2];
+                if (apply_W) WA_n = Wv[j + 2];
+            }
+            if (j + 3 < jb) {
+                rB_n = pos[j + 3];
+                if (apply_W) WB_n = Wv[j + 3];
+            }
+            float phA[KV], phB[KV];
+            ln.values(pos, j, jb, rA, beta, phA);
+            ln.values(pos, j + 1, jb, rB, beta, phB);
+            float kA[L], kB[L];
+#pragma unroll
+            for (int q = 0; q < L; q++) {
+                kA[q] = shfl_slot<KV>(phA, q);
+                kB[q] = shfl_slot<KV>(phB, q);
+            }
+            const int oA = origin_index<G_, D>(rA.x & 255, (rA.x >> 8) & 255, (rA.x >> 16) & 255);
+            const int oB = origin_index<G_, D>(rB.x & 255, (rB.x >> 8) & 255, (rB.x >> 16) & 255);
+            const bool same = hasB && rA.x == rB.x;  // the same for every lane
+            float aAr = 0.0f, aAi = 0.0f, aBr = 0.0f, aBi = 0.0f;
+#pragma unroll
+            for (int ps = 0; ps < PASSES; ps++) {
+                const float kabA = shfl_slot<KV>(phA, ln.sa[ps]) * shfl_slot<KV>(phA, ln.sb[ps]);
+                const float kabB = shfl_slot<KV>(phB, ln.sa[ps]) * shfl_slot<KV>(phB, ln.sb[ps]);
+                if (ln.coff[ps] >= 0) {
+                    const float *prA = tr + oA + ln.coff[ps], *piA = ti + oA + ln.coff[ps];
+                    float sAr = 0.0f, sAi = 0.0f, sBr = 0.0f, sBi = 0.0f;
+                    if (same) {
+#pragma unroll
+                        for (int q0 = 0; q0 < L; q0++) {
+                            const float gr = prA[q0 * PLANE], gi = piA[q0 * PLANE];
+                            sAr = fmaf(kA[q0], gr, sAr);
+                            sAi = fmaf(kA[q0], gi, sAi);
+                            sBr = fmaf(kB[q0], gr, sBr);
+                            sBi = fmaf(kB[q0], gi, sBi);
+                        }
+                    } else {
+                        const float *prB = tr + oB + ln.coff[ps], *piB = ti + oB + ln.coff[ps];
+#pragma unroll
+                        for (int q0 = 0; q0 < L; q0++) {
+                            sAr = fmaf(kA[q0], prA[q0 * PLANE], sAr);
+                            sAi = fmaf(kA[q0], piA[q0 * PLANE], sAi);
+                        }
+                        if (hasB) {
+#pragma unroll
+                            for (int q0 = 0; q0 < L; q0++) {
+                                sBr = fmaf(kB[q0], prB[q0 * PLANE], sBr);
+                                sBi = fmaf(kB[q0], piB[q0 * PLANE], sBi);
+                            }
+                        }
+                    }
+                    aAr = fmaf(kabA, sAr, aAr);
+                    aAi = fmaf(kabA, sAi, aAi);
+                    aBr = fmaf(kabB, sBr, aBr);
+                    aBi = fmaf(kabB, sBi, aBi);
+                }
+            }
+            // lane 0: Re A, lane 8: Im A, lane 16: Re B, lane 24: Im B
+            const float tot = warp_sum4(aAr, aAi, aBr, aBi, lane);
+            const bool isB = lane & 16;
+            const int node = j + (isB ? 1 : 0);
+            const float Wn = isB ? WB : WA;
+            if constexpr (EN) {
+                const float im = __shfl_xor_sync(0xffffffffu, tot, 8);
+                if ((lane & 15) == 0 && (!isB || hasB)) eacc.add(Wn * (tot * tot + im * im), 1.0f);
+            } else {
+                if ((lane & 7) == 0 && (!isB || hasB))
+                    reinterpret_cast<float *>(c_out + node)[(lane >> 3) & 1] = tot * Wn;
+            }
+        }
+    } else {
+    // software pipeline: a node's stencil values are evaluated one iteration before its tile
+    // work (so the exp / rsqrt latency overlaps the previous node's loads), from a record
+    // loaded two iterations before
+    int4 me = make_int4(0, 0, 0, 0), me_n = make_int4(0, 0, 0, 0);
+    float Wj = 1.0f, W_n = 1.0f;
+    float phv[KV];
+    if (ja + half < jb) {
+        me = pos[ja + half];
+        if (apply_W) Wj = Wv[ja + half];
+    }
+    ln.values(pos, ja, jb, me, beta, phv);
+    if (ja + NPW + half < jb) {
+        me_n = pos[ja + NPW + half];
+        if (apply_W) W_n = Wv[ja + NPW + half];
+    }
+    for (int j = ja; j < jb; j += NPW) {
+        const int mine = j + half;
+        const bool act = (NPW == 1) || mine < jb;
+        float phn[KV];
+        ln.values(pos, j + NPW, jb, me_n, beta, phn);
+        int4 me_nn = make_int4(0, 0, 0, 0);
+        float W_nn = 1.0f;
+        if (j + 2 * NPW + half < jb) {
+            me_nn = pos[j + 2 * NPW + half];
+            if (apply_W) W_nn = Wv[j + 2 * NPW + half];
+        }
+        float k0[L];
+#pragma unroll
+        for (int q = 0; q < L; q++) k0[q] = (D == 3) ? shfl_slot<KV>(phv, half * DW + q) : 1.0f;
+        const int obase = origin_index<G_, D>(me.x & 255, (me.x >> 8) & 255, (me.x >> 16) & 255);
+        float accr = 0.0f, acci = 0.0f;
+#pragma unroll
+        for (int ps = 0; ps < PASSES; ps++) {
+            const float kab = shfl_slot<KV>(phv, ln.sa[ps]) * shfl_slot<KV>(phv, ln.sb[ps]);
+            if (act && ln.coff[ps] >= 0) {
+                const float *pr = tr + obase + ln.coff[ps], *pi = ti + obase + ln.coff[ps];
+                float sr = 0.0f, si = 0.0f;
+#pragma unroll
+                for (int q0 = 0; q0 < L; q0++) {
+                    sr = fmaf(k0[q0], pr[q0 * PLANE], sr);
+                    si = fmaf(k0[q0], pi[q0 * PLANE], si);
+                }
+                accr = fmaf(kab, sr, accr);
+                acci = fmaf(kab, si, acci);
+            }
+        }
+#pragma unroll
+        for (int off = LPN / 2; off > 0; off >>= 1) {  // within each node's lanes
+            accr += __shfl_xor_sync(0xffffffffu, accr, off);
+            acci += __shfl_xor_sync(0xffffffffu, acci, off);
+        }
+        if (hl == 0 && act) {
+            if constexpr (EN) eacc.add(Wj * (accr * accr + acci * acci), 1.0f);  // W_j |rho_hat_j|^2
+            else c_out[mine] = make_float2(accr * Wj, acci * Wj);
+        }
+        me = me_n;
+        me_n = me_nn;
+        Wj = W_n;
+        W_n = W_nn;
+#pragma unroll
+        for (int v = 0; v < KV; v++) phv[v] = phn[v];
+    }
+    }
+    if constexpr (EN) {  // energy-only mode: one compensated partial per CTA
+        __syncthreads();
+        const double2 tot = energy_block_sum(eacc, reinterpret_cast<double *>(smem_raw));
+        if (threadIdx.x == 0) epart[blockIdx.x] = tot;
     }
 }
 
-template <typename T, int D, int W>
+// FP32 3D interpolation with a lane per node.  The plan orders each bin's nodes in groups of
+// at most 32 whose stencil origins are equal or fall in different shared-memory banks, so a
+// warp reading the same stencil offset from each lane's origin is served by one wavefront
+// (equal origins are broadcasts).  Each lane evaluates its node's 3w stencil values itself and
+// sums its w^3 cells in registers: no value exchange between lanes and no reduction, so the
+// shared reads and their multiply-adds are nearly the whole instruction stream.  Lanes past a
+// group's size idle.
+template <int W>
+__device__ __forceinline__ void es_phi_axis(float u, float beta, float (&f)[W]) {
+#pragma unroll
+    for (int q = 0; q < W; q++) {
+        const float vc = ((float)q + 1.0f - 0.5f * (float)W) * (2.0f / (float)W);
+        // the first cell reaches |z| = 1 exactly when u = 1 (see F32Lane::values)
+        f[q] = (q == 0 && u >= 1.0f) ? 0.0f : es_phi_f32(fmaf(-u, 2.0f / (float)W, vc), beta);
+    }
+}
+
+template <int W, int BS, bool EN>
+__global__ void __launch_bounds__(SUB_THREADS) interp_grp_kernel(NodeDesc nd, const float2 *__restrict__ G,
+                                                                float2 *__restrict__ c_out, int apply_W,
+                                                                double2 *__restrict__ epart) {
+    using G_ = Geo<float, 3, W, BS>;
+    constexpr int PLANE = G_::PLANE, P2 = G_::P2, NW = SUB_THREADS / 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *tr = reinterpret_cast<float *>(smem_raw);
+    float *ti = tr + G_::NCELL;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int4 gs = nd.gsubs[blockIdx.x];
+    const int4 bo = nd.bins[gs.z];
+    stage_tile<float, G_, 3>(G, bo, nd.n, tr, ti);
+    __syncthreads();
+
+    const float beta = (float)nd.beta;
+    const float *__restrict__ Wv = reinterpret_cast<const float *>(nd.W);
+    EAcc<float> eacc;
+    for (int g = gs.x + wid; g < gs.x + gs.y; g += NW) {
+        const int first = nd.grp[g], cnt = nd.grp[g + 1] - first;
+        if (lane < cnt) {
+            const int node = first + lane;
+            const int4 r = nd.pos[node];
+            const float Wj = apply_W ? Wv[node] : 1.0f;
+            float fz[W], fy[W], fx[W];
+            es_phi_axis<W>(__int_as_float(r.y), beta, fz);
+            es_phi_axis<W>(__int_as_float(r.z), beta, fy);
+            es_phi_axis<W>(__int_as_float(r.w), beta, fx);
+            const int o = origin_index<G_, 3>(r.x & 255, (r.x >> 8) & 255, (r.x >> 16) & 255);
+            const float *pr = tr + o, *pi = ti + o;
+            float ar = 0.0f, ai = 0.0f;
+#pragma unroll(W <= 8 ? W : 1)
+            for (int qa = 0; qa < W; qa++) {
+                float br = 0.0f, bi = 0.0f;
+#pragma unroll
+                for (int qb = 0; qb < W; qb++) {
+                    float sr = 0.0f, si = 0.0f;
+#pragma unroll
+                    for (int q0 = 0; q0 < W; q0++) {
+                        const int off = q0 * PLANE + qa * P2 + qb;
+                        sr = fmaf(fz[q0], pr[off], sr);
+                        si = fmaf(fz[q0], pi[off], si);
+                    }
+                    br = fmaf(fx[qb], sr, br);
+                    bi = fmaf(fx[qb], si, bi);
+                }
+                ar = fmaf(fy[qa], br, ar);
+                ai = fmaf(fy[qa], bi, ai);
+            }
+            if constexpr (EN) eacc.add(Wj * (ar * ar + ai * ai), 1.0f);  // W_j |rho_hat_j|^2
+            else c_out[node] = make_float2(ar * Wj, ai * Wj);
+        }
+    }
+    if constexpr (EN) {  // energy-only mode: one compensated partial per CTA
+        __syncthreads();
+        const double2 tot = energy_block_sum(eacc, reinterpret_cast<double *>(smem_raw));
+        if (threadIdx.x == 0) epart[blockIdx.x] = tot;
+    }
+}
+
+// FP32 spreading.  In 3D each lane converts its column's weight c_j phi_1 phi_2 (times 2S) to
+// an integer once per pass, and each axis-0 value phi_0(q) to Q31 once per node; a cell's
+// contribution round(c_j phi_0 phi_1 phi_2 S) is then the high word of one integer
+// multiply-add (mulq31): about 0.75 of a fixed-point unit of rounding, as the FP32 product
+// rounded once, with no float-to-integer conversion per cell.
+template <int D, int W, int BS>
+__global__ void __launch_bounds__(SUB_THREADS) spread_f32_kernel(NodeDesc nd, const float2 *__restrict__ c_in,
+                                                                float2 *__restrict__ H) {
+    using G_ = Geo<float, D, W, BS>;
+    using LN = F32Lane<D, W, BS>;
+    using F = FixAcc<float>;
+    constexpr int PASSES = G_::PASSES, L = (D == 3) ? W : 1, PLANE = G_::PLANE;
+    constexpr int LPN = G_::LPN, NPW = G_::NPW, KV = LN::KV, DW = D * W;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int *tr = reinterpret_cast<int *>(smem_raw);
+    int *ti = tr + G_::NCELL;
+    __shared__ float red[2 * (SUB_THREADS / 32)];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int4 sb = nd.subs[blockIdx.x];
+    const int4 bo = nd.bins[sb.z];
+    LN ln;
+    ln.init(nd.pair_order, lane);
+
+    const int ex = spread_scale<float, int, G_::NCELL, F::E, F::MAXEXP>(c_in, sb, tr, ti, red, H);
+    if (ex == INT_MIN) return;
+    // 3D: weights carry 2S, so that mulq31 (a product over 2^32) lands on units of 1/S
+    const float S = ldexpf(1.0f, ex + (D == 3 ? 1 : 0));
+
+    int ja, jb;
+    warp_chunk(sb, wid, ja, jb);
+    const int half = lane / LPN;
+    const int4 *__restrict__ pos = nd.pos;
+    const float beta = (float)nd.beta;
+    if constexpr (LPN == 32 && D == 3) {
+        // Two nodes per iteration, as in the interpolation; when they share a stencil origin
+        // their two contributions to a cell are added (exactly, in integers) before one shared
+        // atomic, so that pair costs the atomics of one node.
+        int4 rA_n = make_int4(0, 0, 0, 0), rB_n = make_int4(0, 0, 0, 0);
+        float2 cA_n = make_float2(0.0f, 0.0f), cB_n = make_float2(0.0f, 0.0f);
+        if (ja < jb) {
+            rA_n = pos[ja];
+            cA_n = c_in[ja];
+        }
+        if (ja + 1 < jb) {
+            rB_n = pos[ja + 1];
+            cB_n = c_in[ja + 1];
+        }
+        for (int j = ja; j < jb; j += 2) {
+            const bool hasB = j + 1 < jb;
+            const int4 rA = rA_n, rB = rB_n;
+            const float2 cA = cA_n, cB = cB_n;
+            if (j + 2 < jb) {
+                rA_n = pos[j + 2];
+                cA_n = c_in[j + 2];
+            }
+            if (j + 3 < jb) {
+                rB_n = pos[j + 3];
+                cB_n = c_in[j + 3];
+            }
+            float phA[KV], phB[KV];
+            ln.values(pos, j, jb, rA, beta, phA);
+            ln.values(pos, j + 1, jb, rB, beta, phB);
+            int qA[KV], qB[KV];
+#pragma unroll
+            for (int v = 0; v < KV; v++) {
+                qA[v] = __float2int_rn(phA[v] * 2147483648.0f);  // Q31 (saturates at 1)
+                qB[v] = __float2int_rn(phB[v] * 2147483648.0f);
+            }
+            int kA[L], kB[L];
+#pragma unroll
+            for (int q = 0; q < L; q++) {
+                kA[q] = shfl_slot<KV>(qA, q);
+                kB[q] = shfl_slot<KV>(qB, q);
+            }
+            const int oA = origin_index<G_, D>(rA.x & 255, (rA.x >> 8) & 255, (rA.x >> 16) & 255);
+            const int oB = origin_index<G_, D>(rB.x & 255, (rB.x >> 8) & 255, (rB.x >> 16) & 255);
+            const bool same = hasB && rA.x == rB.x;  // the same for every lane
+            const float sAr = cA.x * S, sAi = cA.y * S, sBr = cB.x * S, sBi = cB.y * S;
+#pragma unroll
+            for (int ps = 0; ps < PASSES; ps++) {
+                const float kabA = shfl_slot<KV>(phA, ln.sa[ps]) * shfl_slot<KV>(phA, ln.sb[ps]);
+                const float kabB = shfl_slot<KV>(phB, ln.sa[ps]) * shfl_slot<KV>(phB, ln.sb[ps]);
+                if (ln.coff[ps] >= 0) {
+                    const int wAr = __float2int_rn(sAr * kabA), wAi = __float2int_rn(sAi * kabA);
+                    const int wBr = __float2int_rn(sBr * kabB), wBi = __float2int_rn(sBi * kabB);
+                    int *prA = tr + oA + ln.coff[ps], *piA = ti + oA + ln.coff[ps];
+                    if (same) {
+                        // |A + B| < 2^30: each contribution is below 2^29 (S B <= 2^29)
+#pragma unroll
+                        for (int q0 = 0; q0 < L; q0++) {
+                            F::add(prA + q0 * PLANE, mulq31(wAr, kA[q0]) + mulq31(wBr, kB[q0]));
+                            F::add(piA + q0 * PLANE, mulq31(wAi, kA[q0]) + mulq31(wBi, kB[q0]));
+                        }
+                    } else {
+#pragma unroll
+                        for (int q0 = 0; q0 < L; q0++) {
+                            F::add(prA + q0 * PLANE, mulq31(wAr, kA[q0]));
+                            F::add(piA + q0 * PLANE, mulq31(wAi, kA[q0]));
+                        }
+                        if (hasB) {
+                            int *prB = tr + oB + ln.coff[ps], *piB = ti + oB + ln.coff[ps];
+#pragma unroll
+                            for (int q0 = 0; q0 < L; q0++) {
+                                F::add(prB + q0 * PLANE, mulq31(wBr, kB[q0]));
+                                F::add(piB + q0 * PLANE, mulq31(wBi, kB[q0]));
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        flush_tile<float, G_, D, int>(tr, ti, bo, nd, ex, H);
+        return;
+    }
+    // software pipeline as in the interpolation: stencil values one iteration ahead, records
+    // and c two iterations ahead
+    int4 me = make_int4(0, 0, 0, 0), me_n = make_int4(0, 0, 0, 0);
+    float2 c = make_float2(0.0f, 0.0f), c_n = make_float2(0.0f, 0.0f);
+    float phv[KV];
+    if (ja + half < jb) {
+        me = pos[ja + half];
+        c = c_in[ja + half];
+    }
+    ln.values(pos, ja, jb, me, beta, phv);
+    if (ja + NPW + half < jb) {
+        me_n = pos[ja + NPW + half];
+        c_n = c_in[ja + NPW + half];
+    }
+    for (int j = ja; j < jb; j += NPW) {
+        const bool act = (NPW == 1) || j + half < jb;
+        float phn[KV];
+        ln.values(pos, j + NPW, jb, me_n, beta, phn);
+        int4 me_nn = make_int4(0, 0, 0, 0);
+        float2 c_nn = make_float2(0.0f, 0.0f);
+        if (j + 2 * NPW + half < jb) {
+            me_nn = pos[j + 2 * NPW + half];
+            c_nn = c_in[j + 2 * NPW + half];
+        }
+        int k0i[L];
+        if constexpr (D == 3) {
+            int phq[KV];
+#pragma unroll
+            for (int v = 0; v < KV; v++) phq[v] = __float2int_rn(phv[v] * 2147483648.0f);  // saturates at 1
+#pragma unroll
+            for (int q = 0; q < L; q++) k0i[q] = shfl_slot<KV>(phq, half * DW + q);
+        }
+        const float csr = c.x * S, csi = c.y * S;
+        const int obase = origin_index<G_, D>(me.x & 255, (me.x >> 8) & 255, (me.x >> 16) & 255);
+#pragma unroll
+        for (int ps = 0; ps < PASSES; ps++) {
+            const float kab = shfl_slot<KV>(phv, ln.sa[ps]) * shfl_slot<KV>(phv, ln.sb[ps]);
+            if (act && ln.coff[ps] >= 0) {
+                const int cwr = __float2int_rn(csr * kab), cwi = __float2int_rn(csi * kab);
+                int *pr = tr + obase + ln.coff[ps], *pi = ti + obase + ln.coff[ps];
+                if constexpr (D == 3) {
+#pragma unroll
+                    for (int q0 = 0; q0 < L; q0++) {
+                        F::add(pr + q0 * PLANE, mulq31(cwr, k0i[q0]));
+                        F::add(pi + q0 * PLANE, mulq31(cwi, k0i[q0]));
+                    }
+                } else {
+                    F::add(pr, cwr);
+                    F::add(pi, cwi);
+                }
+            }
+        }
+        me = me_n;
+        me_n = me_nn;
+        c = c_n;
+        c_n = c_nn;
+#pragma unroll
+        for (int v = 0; v < KV; v++) phv[v] = phn[v];
+    }
+    __syncthreads();
+    flush_tile<float, G_, D, int>(tr, ti, bo, nd, ex, H);
+}
+
+template <typename T, int D, int W, int BS>
 static cudaError_t launch_interp_w(const NodeDesc &nd, const void *G, void *c_out, int apply_W,
                                    double2 *epart, size_t smem, cudaStream_t s) {
-    if (epart) {
-        cudaError_t e = cudaFuncSetAttribute(interp_sub_kernel<T, D, W, true>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        interp_sub_kernel<T, D, W, true><<<(unsigned)nd.nsub, SUB_THREADS, smem, s>>>(
-            nd, (const cx_t<T> *)G, (cx_t<T> *)c_out, apply_W, epart);
+    const unsigned grid = (unsigned)nd.nsub;
+    if constexpr (sizeof(T) == 4 && D == 3) {  // lane per node over the plan's node groups
+        if (!nd.grp) return cudaErrorInvalidValue;
+        const unsigned ggrid = (unsigned)nd.ngsub;
+        if (ggrid == 0) return cudaSuccess;
+        if (epart) {
+            cudaError_t e = cudaFuncSetAttribute(interp_grp_kernel<W, BS, true>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            interp_grp_kernel<W, BS, true><<<ggrid, SUB_THREADS, smem, s>>>(
+                nd, (const float2 *)G, (float2 *)c_out, apply_W, epart);
+        } else {
+            cudaError_t e = cudaFuncSetAttribute(interp_grp_kernel<W, BS, false>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            interp_grp_kernel<W, BS, false><<<ggrid, SUB_THREADS, smem, s>>>(
+                nd, (const float2 *)G, (float2 *)c_out, apply_W, nullptr);
+        }
+    } else if constexpr (sizeof(T) == 4) {
+        if (epart) {
+            cudaError_t e = cudaFuncSetAttribute(interp_f32_kernel<D, W, BS, true>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            interp_f32_kernel<D, W, BS, true><<<grid, SUB_THREADS, smem, s>>>(
+                nd, (const float2 *)G, (float2 *)c_out, apply_W, epart);
+        } else {
+            cudaError_t e = cudaFuncSetAttribute(interp_f32_kernel<D, W, BS, false>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            interp_f32_kernel<D, W, BS, false><<<grid, SUB_THREADS, smem, s>>>(
+                nd, (const float2 *)G, (float2 *)c_out, apply_W, nullptr);
+        }
     } else {
-        cudaError_t e = cudaFuncSetAttribute(interp_sub_kernel<T, D, W, false>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        interp_sub_kernel<T, D, W, false><<<(unsigned)nd.nsub, SUB_THREADS, smem, s>>>(
-            nd, (const cx_t<T> *)G, (cx_t<T> *)c_out, apply_W, nullptr);
+        if (epart) {
+            cudaError_t e = cudaFuncSetAttribute(interp_sub_kernel<T, D, W, BS, true>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            interp_sub_kernel<T, D, W, BS, true><<<grid, SUB_THREADS, smem, s>>>(
+                nd, (const cx_t<T> *)G, (cx_t<T> *)c_out, apply_W, epart);
+        } else {
+            cudaError_t e = cudaFuncSetAttribute(interp_sub_kernel<T, D, W, BS, false>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            interp_sub_kernel<T, D, W, BS, false><<<grid, SUB_THREADS, smem, s>>>(
+                nd, (const cx_t<T> *)G, (cx_t<T> *)c_out, apply_W, nullptr);
+        }
     }
     return cudaGetLastError();
 }
 
-template <typename T, int D, int W>
+template <typename T, int D, int W, int BS>
 static cudaError_t launch_spread_w(const NodeDesc &nd, const void *c_in, void *H, size_t smem,
                                    cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(spread_sub_kernel<T, D, W>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    spread_sub_kernel<T, D, W><<<(unsigned)nd.nsub, SUB_THREADS, smem, s>>>(
-        nd, (const cx_t<T> *)c_in, (cx_t<T> *)H);
+    const unsigned grid = (unsigned)nd.nsub;
+    if constexpr (sizeof(T) == 4) {
+        cudaError_t e = cudaFuncSetAttribute(spread_f32_kernel<D, W, BS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        spread_f32_kernel<D, W, BS><<<grid, SUB_THREADS, smem, s>>>(nd, (const float2 *)c_in, (float2 *)H);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(spread_sub_kernel<T, D, W, BS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        spread_sub_kernel<T, D, W, BS><<<grid, SUB_THREADS, smem, s>>>(
+            nd, (const cx_t<T> *)c_in, (cx_t<T> *)H);
+    }
     return cudaGetLastError();
 }
 
@@ -550,30 +1185,35 @@ cudaError_t launch_crowd_merge_d(const NodeDesc &nd, void *H, cudaStream_t s) {
         default: return cudaErrorInvalidValue;                                 \
     }
 
-template <typename T, int D>
-cudaError_t launch_interp_d(const NodeDesc &nd, const void *G, void *c_out, int apply_W,
-                            double2 *epart, cudaStream_t s) {
+template <typename T, int D, int BS>
+cudaError_t launch_interp_bs(const NodeDesc &nd, const void *G, void *c_out, int apply_W,
+                             double2 *epart, cudaStream_t s) {
     if (nd.nsub == 0) return cudaSuccess;
     const size_t sm = node_smem(nd, sizeof(T) == 4 ? NLINT_FP32 : NLINT_FP64);
-#define NLINT_CALL_I(WW) launch_interp_w<T, D, WW>(nd, G, c_out, apply_W, epart, sm, s)
+    if (sm > NODE_SMEM_MAX) return cudaErrorInvalidValue;
+#define NLINT_CALL_I(WW) launch_interp_w<T, D, WW, BS>(nd, G, c_out, apply_W, epart, sm, s)
     NLINT_W_SWITCH(NLINT_CALL_I)
 #undef NLINT_CALL_I
 }
 
-template <typename T, int D>
-cudaError_t launch_spread_d(const NodeDesc &nd, const void *c_in, void *H, cudaStream_t s) {
+template <typename T, int D, int BS>
+cudaError_t launch_spread_bs(const NodeDesc &nd, const void *c_in, void *H, cudaStream_t s) {
     if (nd.nsub == 0) return cudaSuccess;
     const size_t sm = node_smem(nd, sizeof(T) == 4 ? NLINT_FP32 : NLINT_FP64);
-#define NLINT_CALL_S(WW) launch_spread_w<T, D, WW>(nd, c_in, H, sm, s)
+    if (sm > NODE_SMEM_MAX) return cudaErrorInvalidValue;
+#define NLINT_CALL_S(WW) launch_spread_w<T, D, WW, BS>(nd, c_in, H, sm, s)
     NLINT_W_SWITCH(NLINT_CALL_S)
 #undef NLINT_CALL_S
 }
 
-#define NLINT_NODE_KERNELS_INSTANTIATE(T, D)                                                    \
-    template cudaError_t launch_interp_d<T, D>(const NodeDesc &, const void *, void *, int,      \
-                                               double2 *, cudaStream_t);                       \
-    template cudaError_t launch_spread_d<T, D>(const NodeDesc &, const void *, void *,           \
-                                               cudaStream_t);                                  \
+// One translation unit per (precision, dimension, bin shape), so the width-specialised
+// kernels compile in parallel.
+#define NLINT_NODE_KERNELS_INSTANTIATE(T, D, BS)                                                \
+    template cudaError_t launch_interp_bs<T, D, BS>(const NodeDesc &, const void *, void *, int, \
+                                                    double2 *, cudaStream_t);                   \
+    template cudaError_t launch_spread_bs<T, D, BS>(const NodeDesc &, const void *, void *,      \
+                                                    cudaStream_t);
+#define NLINT_CROWD_MERGE_INSTANTIATE(T, D) \
     template cudaError_t launch_crowd_merge_d<T, D>(const NodeDesc &, void *, cudaStream_t);
 
 }  // namespace nlint

@@ -1,0 +1,8 @@
+// Interpolation / spreading kernels for float, 3D, bin shape 4 (one translation unit per
+// precision, dimension and bin shape so that the width-specialised kernels compile in parallel).
+#include "node_kernels.cuh"
+
+namespace nlint {
+NLINT_NODE_KERNELS_INSTANTIATE(float, 3, 4)
+
+}  // namespace nlint

@@ -11,10 +11,21 @@ int tile_cells(const NodeDesc &nd) {
 }
 
 // Shared memory of the interpolation / spreading kernels: the tile (real and imaginary
-// planes) plus one table of 2 x 3 x NODE_MAXW kernel values per warp (two nodes at a time).
-size_t node_smem(const NodeDesc &nd, int prec) {
+// planes) plus, for FP64, one table of 2 x 3 x NODE_MAXW kernel values per warp (two nodes
+// at a time).  FP32 kernels evaluate the stencil values in registers and exchange them by
+// warp shuffles.
+size_t node_smem_for(int prec, int d, int w, int bs) {
     const size_t s = prec == NLINT_FP32 ? 4 : 8;  // tile cell: float/int32 or double/int64
-    return 2 * (size_t)tile_cells(nd) * s + (size_t)(NODE_THREADS / 32) * 6 * NODE_MAXW * s;
+    // 3D: T0 x T1 rows of tile_pitch cells (the pitch pads FP32 rows against bank conflicts)
+    size_t cells = 1;
+    for (int a = 0; a < d - 1; a++) cells *= (size_t)(bin_dim(d, bs, a) + w - 1);
+    cells *= (size_t)tile_pitch(prec == NLINT_FP64, d, w, bs);
+    const size_t table = prec == NLINT_FP32 ? 0 : (size_t)(NODE_THREADS / 32) * 6 * NODE_MAXW * s;
+    return 2 * cells * s + table;
+}
+
+size_t node_smem(const NodeDesc &nd, int prec) {
+    return node_smem_for(prec, nd.d, nd.w, nd.bin_shape);
 }
 
 // out[perm[j]] = scale * v_j, out[mirror[j]] = scale * conj(v_j)
@@ -128,16 +139,43 @@ cudaError_t launch_extract_real(int64_t cnt, const void *G, double scale, void *
 
 static inline unsigned nblk(int64_t M, int t) { return (unsigned)((M + t - 1) / t); }
 
+// Dispatch on the plan's dimension and bin shape to the compiled combinations
+// (bin_shape_built): FP32 3D shapes 1, 3, 4; FP64 3D shapes 1, 2; 2D shape 1.
 template <typename T>
 cudaError_t launch_interp(const NodeDesc &nd, const void *G, void *c_out, int apply_W,
                           cudaStream_t s, double2 *epart) {
-    return nd.d == 3 ? launch_interp_d<T, 3>(nd, G, c_out, apply_W, epart, s)
-                     : launch_interp_d<T, 2>(nd, G, c_out, apply_W, epart, s);
+    constexpr bool F64 = sizeof(T) == 8;
+    if (nd.d == 2) return nd.bin_shape == 1 ? launch_interp_bs<T, 2, 1>(nd, G, c_out, apply_W, epart, s)
+                                            : cudaErrorInvalidValue;
+    switch (nd.bin_shape) {
+        case 1: return launch_interp_bs<T, 3, 1>(nd, G, c_out, apply_W, epart, s);
+        case 2: if constexpr (F64) return launch_interp_bs<T, 3, 2>(nd, G, c_out, apply_W, epart, s);
+                break;
+        case 3: if constexpr (!F64) return launch_interp_bs<T, 3, 3>(nd, G, c_out, apply_W, epart, s);
+                break;
+        case 4: if constexpr (!F64) return launch_interp_bs<T, 3, 4>(nd, G, c_out, apply_W, epart, s);
+                break;
+        default: break;
+    }
+    return cudaErrorInvalidValue;
 }
 
 template <typename T>
 cudaError_t launch_spread(const NodeDesc &nd, const void *c_in, void *Hext, cudaStream_t s) {
-    return nd.d == 3 ? launch_spread_d<T, 3>(nd, c_in, Hext, s) : launch_spread_d<T, 2>(nd, c_in, Hext, s);
+    constexpr bool F64 = sizeof(T) == 8;
+    if (nd.d == 2) return nd.bin_shape == 1 ? launch_spread_bs<T, 2, 1>(nd, c_in, Hext, s)
+                                            : cudaErrorInvalidValue;
+    switch (nd.bin_shape) {
+        case 1: return launch_spread_bs<T, 3, 1>(nd, c_in, Hext, s);
+        case 2: if constexpr (F64) return launch_spread_bs<T, 3, 2>(nd, c_in, Hext, s);
+                break;
+        case 3: if constexpr (!F64) return launch_spread_bs<T, 3, 3>(nd, c_in, Hext, s);
+                break;
+        case 4: if constexpr (!F64) return launch_spread_bs<T, 3, 4>(nd, c_in, Hext, s);
+                break;
+        default: break;
+    }
+    return cudaErrorInvalidValue;
 }
 
 template <typename T>

@@ -109,6 +109,44 @@ std::vector<int16_t> build_pair_order(int w, int row, int banks, int lanes, int 
     return out;
 }
 
+void build_node_groups(const int32_t *org, int64_t first, int64_t count, std::vector<int64_t> &order,
+                       std::vector<int> &sizes) {
+    struct Run {
+        int32_t o;
+        int64_t next, end;
+    };
+    std::vector<Run> runs;  // runs of one origin (the nodes are sorted by origin)
+    for (int64_t i = first; i < first + count;) {
+        int64_t k = i;
+        while (k < first + count && org[k] == org[i]) k++;
+        runs.push_back({org[i], i, k});
+        i = k;
+    }
+    std::stable_sort(runs.begin(), runs.end(),
+                     [](const Run &a, const Run &b) { return a.end - a.next > b.end - b.next; });
+    size_t head = 0;  // runs before head are used up
+    int64_t left = count;
+    while (left > 0) {
+        int32_t owner[32];
+        for (int r = 0; r < 32; r++) owner[r] = -1;  // origin offsets are >= 0
+        int slots = 32;
+        while (head < runs.size() && runs[head].next == runs[head].end) head++;
+        for (size_t u = head; u < runs.size() && slots > 0; u++) {
+            Run &ru = runs[u];
+            if (ru.next == ru.end) continue;
+            const int r = ru.o & 31;
+            if (owner[r] >= 0 && owner[r] != ru.o) continue;
+            owner[r] = ru.o;
+            const int64_t take = std::min<int64_t>(slots, ru.end - ru.next);
+            for (int64_t t = 0; t < take; t++) order.push_back(ru.next + t);
+            ru.next += take;
+            slots -= (int)take;
+        }
+        sizes.push_back(32 - slots);
+        left -= 32 - slots;
+    }
+}
+
 }  // namespace nlint
 
 // ---------------------------------------------------------------------------------- plan
@@ -121,15 +159,19 @@ struct nlint_plan_s {
     int device;
     // device memory
     int32_t *d_rel = nullptr;
+    int4 *d_pos = nullptr;       // FP32 plans: per-node origin and offset records
     void *d_ker = nullptr, *d_W = nullptr, *d_fac = nullptr, *d_tw = nullptr;
     int32_t *d_perm = nullptr, *d_mirror = nullptr;
     int4 *d_subs = nullptr, *d_bins = nullptr;
+    int4 *d_gsubs = nullptr;     // FP32 3D: interpolation subproblems over node groups
+    int32_t *d_grp = nullptr;    // FP32 3D: first node of each group (and one past the last)
     int16_t *d_pairs = nullptr, *d_pairs_i = nullptr;  // spreading / interpolation lane tables
     double2 *d_epart = nullptr;  // energy-only path: one partial per subproblem
     int32_t *d_crowd_bin = nullptr;
     double2 *d_crowd = nullptr;
     int B[3], T[3];
-    int64_t nsub = 0, nbins = 0;
+    int bin_shape = 1;
+    int64_t nsub = 0, nbins = 0, ngsub = 0;
     int ncrowd = 0;
     size_t bytes_crowd = 0;
     void *d_bufA = nullptr, *d_bufB = nullptr, *d_bufG = nullptr, *d_c = nullptr;
@@ -266,7 +308,7 @@ static int upload(void **dst, const std::vector<double> &v, size_t &acc) {
 }
 
 static void plan_free(nlint_plan_s *p) {
-    void *ptrs[] = {p->d_rel, p->d_ker, p->d_W, p->d_fac, p->d_tw, p->d_perm, p->d_mirror,
+    void *ptrs[] = {p->d_rel, p->d_pos, p->d_gsubs, p->d_grp, p->d_ker, p->d_W, p->d_fac, p->d_tw, p->d_perm, p->d_mirror,
                     p->d_subs, p->d_bins, p->d_crowd_bin, p->d_crowd, p->d_pairs, p->d_pairs_i, p->d_epart, p->d_fac1, p->d_khat,
                     p->d_win, p->d_bufA, p->d_bufB, p->d_bufG, p->d_bufH, p->d_c, p->d_partials, p->d_E,
                     p->d_rho_io, p->d_u_io, p->d_rho_st[0], p->d_rho_st[1], p->d_u_st[0],
@@ -456,13 +498,28 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
     // (a signed FFT index never exceeds the unwrapped cell index in magnitude, so the bound
     // holds for the stored grid too); a ball that covers the whole grid is no window
     p->ball2 = (ball2 < (int64_t)d * (n / 2) * (n / 2)) ? ball2 : 0;
-    // bins: boxes of B[ax] stencil-origin cells starting at lo[ax]; tile = B + w - 1
+    // bins: boxes of B[ax] stencil-origin cells starting at lo[ax]; tile = B + w - 1.  The
+    // shape is a plan parameter (the autotuner searches it); an automatic choice whose tile
+    // does not fit in shared memory at this width falls back to the smallest shape
+    {
+        const bool f64 = p->prec == NLINT_FP64;
+        int bs = q.bin_shape > 0 ? q.bin_shape : default_bin_shape(f64, d, w);
+        if (!bin_shape_built(f64, d, bs))
+            return fail(NLINT_EINVAL, "bin shape not available for this precision and dimension "
+                                      "(3D FP32: 1, 3, 4; 3D FP64: 1, 2; 2D: 1)");
+        if (node_smem_for(p->prec, d, w, bs) > NODE_SMEM_MAX) {
+            if (q.bin_shape > 0)
+                return fail(NLINT_EUNSUPPORTED, "the bin shape's tile does not fit in shared memory at this width");
+            bs = (d == 3 && f64) ? 2 : 1;
+        }
+        p->bin_shape = bs;
+    }
     for (int ax = 0; ax < 3; ax++) {
         p->B[ax] = 1;
         p->T[ax] = 1;
     }
     for (int ax = 0; ax < d; ax++) {
-        const int b = bin_extent(p->prec == NLINT_FP64, d, w, ax);
+        const int b = bin_dim(d, p->bin_shape, ax);
         p->B[ax] = b;
         p->T[ax] = b + w - 1;
     }
@@ -486,6 +543,34 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
     std::stable_sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) {
         return key[a] != key[b] ? key[a] < key[b] : okey[a] < okey[b];
     });
+    // FP32 3D: each bin's nodes in lane groups for the interpolation (build_node_groups); the
+    // groups keep nodes of one origin together, so the spreading still meets them in pairs
+    const bool grouped = p->prec == NLINT_FP32 && d == 3;
+    std::vector<int> gsize;          // node count of each group, bins in order
+    std::vector<int64_t> gbin_end;   // one past each bin's last group
+    if (grouped) {
+        const int T1 = p->B[1] + w - 1;
+        const int P2 = tile_pitch(false, d, w, p->bin_shape);
+        std::vector<int32_t> org(Mh);
+        for (int64_t o = 0; o < Mh; o++) {
+            const int64_t sidx = ord[o];
+            int32_t r[3];
+            for (int ax = 0; ax < 3; ax++) r[ax] = (l0[(size_t)ax * Mh + sidx] - lo[ax]) % p->B[ax];
+            org[o] = (r[0] * T1 + r[1]) * P2 + r[2];
+        }
+        std::vector<int64_t> neworder;
+        neworder.reserve(Mh);
+        for (int64_t o = 0; o < Mh;) {
+            int64_t e = o;
+            while (e < Mh && key[ord[e]] == key[ord[o]]) e++;
+            build_node_groups(org.data(), o, e - o, neworder, gsize);
+            gbin_end.push_back((int64_t)gsize.size());
+            o = e;
+        }
+        std::vector<int64_t> ord2(Mh);
+        for (int64_t o = 0; o < Mh; o++) ord2[o] = ord[neworder[o]];
+        ord.swap(ord2);
+    }
     std::vector<int32_t> l0s((size_t)d * Mh), perm(Mh), mirror(Mh);
     std::vector<double> frs((size_t)d * Mh), Ws(Mh);
     const double hd = std::pow(p->h, d);
@@ -542,11 +627,52 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
     p->nbins = (int64_t)bins.size();
     p->ncrowd = (int)crowd_bin.size();
     if (p->nsub > (int64_t)INT32_MAX) return fail(NLINT_EUNSUPPORTED, "too many subproblems");
+    // the interpolation's subproblems: runs of at most max_sub / 32 groups of one bin
+    std::vector<int32_t> grp;
+    std::vector<int4> gsubs;
+    if (grouped) {
+        grp.resize(gsize.size() + 1);
+        grp[0] = 0;
+        for (size_t g = 0; g < gsize.size(); g++) grp[g + 1] = grp[g] + gsize[g];
+        const int64_t gmax = std::max(1, max_sub / 32);
+        int64_t g0 = 0;
+        for (size_t bi = 0; bi < bins.size(); bi++) {
+            const int64_t g1 = gbin_end[bi], ng = g1 - g0, ns = (ng + gmax - 1) / gmax;
+            for (int64_t qq = 0; qq < ns; qq++) {
+                const int64_t a = g0 + ng * qq / ns, z = g0 + ng * (qq + 1) / ns;
+                gsubs.push_back(make_int4((int)a, (int)(z - a), (int)bi, 0));
+            }
+            g0 = g1;
+        }
+    }
+    p->ngsub = (int64_t)gsubs.size();
 
-    // ---------------- kernel values phi((q - frac_a) / (w/2)) per node, axis and cell, in FP64
+    // ---------------- FP64 plans: kernel values phi((q - frac_a) / (w/2)) per node, axis and
+    // cell, in FP64.  FP32 plans: per node the packed origin and u_a = frac_a - (w/2 - 1) in
+    // (0, 1] as floats; the kernels evaluate phi from u_a
     const int dw = d * w;
-    std::vector<double> kerv((size_t)Mh * dw);
-    {
+    std::vector<double> kerv(p->prec == NLINT_FP64 ? (size_t)Mh * dw : 0);
+    std::vector<int4> posv(p->prec == NLINT_FP32 ? (size_t)Mh : 0);
+    if (p->prec == NLINT_FP32) {
+        // u = 1 exactly iff frac_a = w/2 exactly, where the first cell's value is 0 (|z| = 1);
+        // every other offset is kept below 1 in FP32 as well, so that its first cell keeps the
+        // value next to the edge, exp(-beta), as in FP64
+        const double off = 0.5 * w - 1.0;
+        const float below1 = std::nextafter(1.0f, 0.0f);
+        for (int64_t o = 0; o < Mh; o++) {
+            float u[3] = {0.0f, 0.0f, 0.0f};
+            for (int ax = 0; ax < d; ax++) {
+                const double fr = frs[(size_t)ax * Mh + o];
+                u[ax] = fr == 0.5 * w ? 1.0f : std::min((float)(fr - off), below1);
+            }
+            int4 r;
+            r.x = rel[o];
+            std::memcpy(&r.y, &u[0], 4);
+            std::memcpy(&r.z, &u[1], 4);
+            std::memcpy(&r.w, &u[2], 4);
+            posv[o] = r;
+        }
+    } else {
         const double beta = p->beta, inv_half = 2.0 / w;
         auto work = [&](int64_t a0, int64_t a1) {
             for (int64_t o = a0; o < a1; o++)
@@ -584,15 +710,25 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
     // ---------------- upload
     size_t acc = 0;
     int rc;
-    CK(cudaMalloc((void **)&p->d_rel, rel.size() * sizeof(int32_t) + 4));
-    CK(cudaMemcpy(p->d_rel, rel.data(), rel.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    if (p->prec == NLINT_FP64) {  // FP32 plans carry the origins in their node records
+        CK(cudaMalloc((void **)&p->d_rel, rel.size() * sizeof(int32_t) + 4));
+        CK(cudaMemcpy(p->d_rel, rel.data(), rel.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    }
     CK(cudaMalloc((void **)&p->d_perm, perm.size() * sizeof(int32_t) + 4));
     CK(cudaMemcpy(p->d_perm, perm.data(), perm.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     CK(cudaMalloc((void **)&p->d_mirror, mirror.size() * sizeof(int32_t) + 4));
     CK(cudaMemcpy(p->d_mirror, mirror.data(), mirror.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-    acc += (rel.size() + perm.size() + mirror.size()) * 4;
+    acc += ((p->prec == NLINT_FP64 ? rel.size() : 0) + perm.size() + mirror.size()) * 4;
     CK(cudaMalloc((void **)&p->d_subs, sizeof(int4) * std::max<size_t>(subs.size(), 1)));
     if (!subs.empty()) CK(cudaMemcpy(p->d_subs, subs.data(), sizeof(int4) * subs.size(), cudaMemcpyHostToDevice));
+    if (grouped) {
+        CK(cudaMalloc((void **)&p->d_gsubs, sizeof(int4) * std::max<size_t>(gsubs.size(), 1)));
+        if (!gsubs.empty())
+            CK(cudaMemcpy(p->d_gsubs, gsubs.data(), sizeof(int4) * gsubs.size(), cudaMemcpyHostToDevice));
+        CK(cudaMalloc((void **)&p->d_grp, sizeof(int32_t) * grp.size()));
+        CK(cudaMemcpy(p->d_grp, grp.data(), sizeof(int32_t) * grp.size(), cudaMemcpyHostToDevice));
+        acc += sizeof(int4) * gsubs.size() + sizeof(int32_t) * grp.size();
+    }
     CK(cudaMalloc((void **)&p->d_bins, sizeof(int4) * std::max<size_t>(bins.size(), 1)));
     if (!bins.empty()) CK(cudaMemcpy(p->d_bins, bins.data(), sizeof(int4) * bins.size(), cudaMemcpyHostToDevice));
     CK(cudaMalloc((void **)&p->d_crowd_bin, sizeof(int32_t) * std::max<size_t>(crowd_bin.size(), 1)));
@@ -600,7 +736,7 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
         CK(cudaMemcpy(p->d_crowd_bin, crowd_bin.data(), sizeof(int32_t) * crowd_bin.size(), cudaMemcpyHostToDevice));
     acc += sizeof(int4) * (subs.size() + bins.size()) + 4 * crowd_bin.size();
     {
-        const int row = (d == 3) ? p->T[2] : p->T[1];
+        const int row = tile_pitch(p->prec == NLINT_FP64, d, w, p->bin_shape);
         // FP32 tiles have 4-byte cells (32 banks, one wavefront per warp), FP64 tiles 8-byte
         // cells (16 banks per half-warp wavefront); both kernels read / add one plane at a time
         const int L = node_lanes(w);
@@ -624,7 +760,10 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
         }
     }
     if (p->prec == NLINT_FP32) {
-        if ((rc = upload<float>(&p->d_ker, kerv, acc))) return rc;
+        CK(cudaMalloc((void **)&p->d_pos, sizeof(int4) * std::max<size_t>(posv.size(), 1)));
+        if (!posv.empty())
+            CK(cudaMemcpy(p->d_pos, posv.data(), sizeof(int4) * posv.size(), cudaMemcpyHostToDevice));
+        acc += sizeof(int4) * posv.size();
         if ((rc = upload<float>(&p->d_W, Ws, acc))) return rc;
         if ((rc = upload<float>(&p->d_fac, fac, acc))) return rc;
         if ((rc = upload<float>(&p->d_tw, tw, acc))) return rc;
@@ -714,8 +853,9 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
     CK(cudaMalloc(&p->d_c, p->bytes_c + cs));
     // + 64: scratch of the two-stage energy fold (launch_energy_final)
     CK(cudaMalloc((void **)&p->d_partials, sizeof(double2) * ((size_t)std::max(p->n_partials, 1024) + 64)));
-    CK(cudaMalloc((void **)&p->d_epart, sizeof(double2) * ((size_t)std::max<int64_t>(p->nsub, 1) + 64)));
-    acc += sizeof(double2) * (size_t)p->nsub;
+    CK(cudaMalloc((void **)&p->d_epart,
+                  sizeof(double2) * ((size_t)std::max<int64_t>(std::max(p->nsub, p->ngsub), 1) + 64)));
+    acc += sizeof(double2) * (size_t)std::max(p->nsub, p->ngsub);
     CK(cudaMalloc((void **)&p->d_E, sizeof(double)));
     acc += p->bytes_A + p->bytes_B + std::max(p->bytes_G, p->bytes_Hext) + p->bytes_c +
            sizeof(double2) * (size_t)std::max(p->n_partials, 1024);
@@ -954,6 +1094,8 @@ static NodeDesc node_desc(nlint_plan_s *p) {
     nd.w = p->w;
     nd.pad = p->pad;
     nd.beta = p->beta;
+    nd.bin_shape = p->bin_shape;
+    nd.pos = p->d_pos;
     nd.rel = p->d_rel;
     nd.ker = p->d_ker;
     nd.W = p->d_W;
@@ -963,6 +1105,9 @@ static NodeDesc node_desc(nlint_plan_s *p) {
     }
     nd.nsub = p->nsub;
     nd.subs = p->d_subs;
+    nd.ngsub = p->ngsub;
+    nd.gsubs = p->d_gsubs;
+    nd.grp = p->d_grp;
     nd.bins = p->d_bins;
     nd.ncrowd = p->ncrowd;
     nd.crowd = p->d_crowd;
@@ -1306,6 +1451,7 @@ int nlint_plan_info(nlint_plan p, nlint_info *info) {
     info->n_subproblems = p->nsub;
     info->n_crowd_bins = p->ncrowd;
     for (int a = 0; a < 3; a++) info->bin[a] = p->B[a];
+    info->bin_shape = p->bin_shape;
     info->device = p->device;
     info->algorithm = p->algorithm;
     info->pu_a = p->pu_a;
@@ -1518,8 +1664,9 @@ int nlint_energy_only(nlint_plan p, const void *rho, double lambda, double *E_de
         CK(launch_interp<double>(node_desc(p), p->d_bufG, nullptr, 1, s, p->d_epart));
     }
     double *E = E_dev ? E_dev : p->d_E;
-    CK(launch_energy_final(p->d_epart, (int)p->nsub, scale, E, s));
-    p->launches += 1 + energy_final_kernels((int)p->nsub);
+    const int nparts = (int)(p->ngsub ? p->ngsub : p->nsub);  // one partial per interpolation CTA
+    CK(launch_energy_final(p->d_epart, nparts, scale, E, s));
+    p->launches += 1 + energy_final_kernels(nparts);
     if (E_host) {
         CK(cudaMemcpyAsync(E_host, E, sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
