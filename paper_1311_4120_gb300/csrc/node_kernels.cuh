@@ -849,12 +849,34 @@ __global__ void __launch_bounds__(SUB_THREADS) interp_grp_kernel(NodeDesc nd, co
     const float beta = (float)nd.beta;
     const float *__restrict__ Wv = reinterpret_cast<const float *>(nd.W);
     EAcc<float> eacc;
-    for (int g = gs.x + wid; g < gs.x + gs.y; g += NW) {
-        const int first = nd.grp[g], cnt = nd.grp[g + 1] - first;
+    // each lane's next record and weight are loaded one group ahead
+    const int gend = gs.x + gs.y;
+    int g = gs.x + wid;
+    int first = 0, cnt = 0;
+    int4 r_n = make_int4(0, 0, 0, 0);
+    float W_n = 1.0f;
+    if (g < gend) {
+        first = nd.grp[g];
+        cnt = nd.grp[g + 1] - first;
         if (lane < cnt) {
-            const int node = first + lane;
-            const int4 r = nd.pos[node];
-            const float Wj = apply_W ? Wv[node] : 1.0f;
+            r_n = nd.pos[first + lane];
+            if (apply_W) W_n = Wv[first + lane];
+        }
+    }
+    for (; g < gend; g += NW) {
+        const int4 r = r_n;
+        const float Wj = W_n;
+        const int node = first + lane;
+        const bool mine = lane < cnt;
+        if (g + NW < gend) {
+            first = nd.grp[g + NW];
+            cnt = nd.grp[g + NW + 1] - first;
+            if (lane < cnt) {
+                r_n = nd.pos[first + lane];
+                if (apply_W) W_n = Wv[first + lane];
+            }
+        }
+        if (mine) {
             float fz[W], fy[W], fx[W];
             es_phi_axis<W>(__int_as_float(r.y), beta, fz);
             es_phi_axis<W>(__int_as_float(r.z), beta, fy);
