@@ -391,16 +391,46 @@ def run_reference(args, rank, world):
 
 
 # ----------------------------------------------------------------------------- batched form
-def run_batched(pkg, torch, dev, precision, reps, flush, stream, loop_too=False):
+def tuned_member_params(pkg, members, precision, dev):
+    """Autotuned parameters for each member of the batch: one tuning per (grid size, kernel)
+    class (width for the tolerance, bin shape, subproblem size), measured on the class's first
+    member and applied to every member of the class with its own dipole axis."""
+    tol = TOL if precision == "fp32" else 1e-10
+    cache = os.environ.get("NLINT_TUNE_CACHE")
+    by_class, reports, out = {}, {}, []
+    for m in members:
+        cls = (m.n, m.kernel)
+        if cls not in by_class:
+            prm = pkg.make_params(3, m.n, m.L, m.kernel, axis=m.axis, nodes=m.nodes,
+                                  precision=precision, device=dev.index)
+            tuned, rep = pkg.autotune(prm, tol, cache)
+            by_class[cls] = tuned
+            reports[f"{m.n}^3 {m.kernel}"] = {k: rep[k] for k in ("w", "bin_shape", "max_sub", "err")}
+        t = by_class[cls]
+        out.append(pkg.make_params(3, m.n, m.L, m.kernel, axis=m.axis, nodes=m.nodes,
+                                   precision=precision, w=t.w, max_sub=t.max_sub,
+                                   bin_shape=t.bin_shape, device=dev.index))
+    return out, reports
+
+
+def run_batched(pkg, torch, dev, precision, reps, flush, stream, loop_too=False, tune=False):
     """64 seeded densities on uneven grids {32,48,64,96,128}^3 (box [-12,12]^3, 16-Gaussian
     mixtures, half Coulomb and half dipolar with seeded axes), one plan each, evaluated by one
     captured CUDA graph.  Returns throughput (total grid points per second) and, optionally, the
-    same plans evaluated one after another on one stream."""
+    same plans evaluated one after another on one stream.  tune=True builds every plan from
+    autotuned parameters (tuned_member_params) instead of the width rule of eps."""
     members = synth.config5(precision)
     eps = 1e-6 if precision == "fp32" else 1e-12
     dt = torch.float32 if precision == "fp32" else torch.float64
-    plans = [pkg.Plan(3, m.n, m.L, m.kernel, axis=m.axis, nodes=m.nodes, precision=precision,
-                      eps=eps, device=dev.index) for m in members]
+    tune_rep = None
+    if tune:
+        t0 = time.perf_counter()
+        prms, tune_rep = tuned_member_params(pkg, members, precision, dev)
+        tune_rep = {"classes": tune_rep, "seconds": time.perf_counter() - t0}
+        plans = [pkg.Plan(3, m.n, m.L, params=q, device=dev.index) for m, q in zip(members, prms)]
+    else:
+        plans = [pkg.Plan(3, m.n, m.L, m.kernel, axis=m.axis, nodes=m.nodes, precision=precision,
+                          eps=eps, device=dev.index) for m in members]
     rhos = [torch.from_numpy(m.rho()).to(dev, dt) for m in members]
     points = sum(m.n_points for m in members)
     batch = pkg.Batch(plans)
@@ -418,7 +448,8 @@ def run_batched(pkg, torch, dev, precision, reps, flush, stream, loop_too=False)
     info = batch.info()
     out = {"value": points / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "densities": len(members),
            "grid_points": points, "kernels_per_eval": info["kernels_per_eval"],
-           "branches": info["branches"], "sizes": sorted({m.n for m in members})}
+           "branches": info["branches"], "sizes": sorted({m.n for m in members}),
+           "autotuned": tune_rep}
     if loop_too:
         us = [torch.empty_like(r) for r in rhos]
         Es = torch.empty(len(rhos), dtype=torch.float64, device=dev)
@@ -659,7 +690,10 @@ def run_ours(args, rank, world, local_rank):
 
     batched = None
     if not args.no_batch:
-        b32 = run_batched(pkg, torch, dev, "fp32", 5, flush, stream, loop_too=True)
+        b32 = run_batched(pkg, torch, dev, "fp32", 5, flush, stream, loop_too=True, tune=True)
+        b32_untuned = run_batched(pkg, torch, dev, "fp32", 5, flush, stream)
+        b32["untuned"] = {"value": b32_untuned["value"], "ms_per_step": b32_untuned["ms_per_step"],
+                          "what": "every plan at the width rule of eps = 1e-6 and default bins"}
         b64 = run_batched(pkg, torch, dev, "fp64", 3, flush, stream)
         batched = {"workload": "64 seeded densities on {32,48,64,96,128}^3 grids over [-12,12]^3, "
                                "half Coulomb, half dipole, one CUDA graph",
@@ -677,7 +711,8 @@ def run_ours(args, rank, world, local_rank):
                                "160x160x320 spherical nodes, FP32 path (FP64 nodes/weights, "
                                "compensated FP64 energy)",
                    "w": info["w"], "sigma": info["sigma"], "n_fine": info["n_fine"],
-                   "max_sub": tuned.max_sub, "tolerance": TOL, "autotune": tune_rep,
+                   "max_sub": tuned.max_sub, "bin_shape": tuned.bin_shape, "tolerance": TOL,
+                   "autotune": tune_rep,
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "energy": E32,

@@ -216,9 +216,11 @@ int nlint_stage_times(nlint_plan plan, float *ms, const char **names, int max_st
 /* Autotuner.  For the plan described by *in and a target relative L-inf error `tol` of u,
  * picks (1) the smallest spreading width w whose error, measured on the device against an FP64
  * plan with the widest stencil (same grid, nodes, cutoff and kernel) on a seeded probe
- * density with content up to the grid's Nyquist radius, is at most tol/2, and (2) the fastest
- * subproblem size (max_sub) among 256..2048 at that width.  *out = *in with w, max_sub and
- * the precision (from tol when in->precision is -1) filled in; rep (may be NULL) reports the
+ * density with content up to the grid's Nyquist radius, is at most tol/2, (2) at that width
+ * the fastest bin shape among those compiled for the precision and dimension whose tile fits
+ * in shared memory (evaluation time by CUDA events), and (3) for that shape the fastest
+ * subproblem size (max_sub) among 256..2048.  *out = *in with w, bin_shape, max_sub and the
+ * precision (from tol when in->precision is -1) filled in; rep (may be NULL) reports the
  * choice, its measured error and time.  The choice is cached as one JSON object per line in
  * cache_path (NULL: $NLINT_TUNE_CACHE; neither: no cache); a cached key skips measurement.
  * Synchronous; creates and destroys several plans (NLINT_ENOMEM etc. pass through). */
@@ -227,6 +229,7 @@ typedef struct nlint_tune_report {
     double err;      /* measured relative L-inf error of the chosen width on the probe */
     double ms;       /* median evaluation time of the choice                           */
     int from_cache;  /* 1: read from the cache, nothing measured                      */
+    int bin_shape;   /* chosen bin shape (nlint_params.bin_shape)                      */
 } nlint_tune_report;
 int nlint_autotune(const nlint_params *in, double tol, const char *cache_path, nlint_params *out,
                    nlint_tune_report *rep);

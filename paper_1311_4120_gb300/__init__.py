@@ -56,7 +56,7 @@ class nlint_params(ctypes.Structure):
 
 class nlint_tune_report(ctypes.Structure):
     _fields_ = [("w", ctypes.c_int), ("max_sub", ctypes.c_int), ("err", ctypes.c_double),
-                ("ms", ctypes.c_double), ("from_cache", ctypes.c_int)]
+                ("ms", ctypes.c_double), ("from_cache", ctypes.c_int), ("bin_shape", ctypes.c_int)]
 
 
 class nlint_info(ctypes.Structure):

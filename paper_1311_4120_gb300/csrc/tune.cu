@@ -7,8 +7,10 @@
 // on a seeded probe density, and keeps the smallest w whose error is at most tol / 2.
 // The probe is a sum of Gaussians whose widths range from two grid cells to an eighth of the
 // box, so it has content up to the grid's Nyquist radius.
-// Speed: for that w it times candidate subproblem sizes (nodes per interpolation / spreading
-// CTA) and keeps the fastest.
+// Speed: for that w it times the bin shapes compiled for the plan's precision and dimension
+// (the tile each interpolation / spreading CTA stages: 3D FP32 8^3, 8x16x16, 16^3; 3D FP64
+// 8^3, 4x8x8; the shapes whose tile fits in shared memory at w), then, for the fastest shape,
+// the subproblem sizes (nodes per CTA), and keeps the fastest pair.
 // Cache: one JSON object per line in `cache_path` (or $NLINT_TUNE_CACHE), keyed by the plan's
 // geometry, kernel, precision and tolerance; a hit skips all measurement.
 #include <algorithm>
@@ -81,7 +83,8 @@ std::string cache_key(const nlint_params &p, double tol) {
     return buf;
 }
 
-bool cache_lookup(const char *path, const std::string &key, int &w, int &max_sub, double &err) {
+bool cache_lookup(const char *path, const std::string &key, int &w, int &max_sub, int &bin_shape,
+                  double &err) {
     if (!path) return false;
     FILE *f = std::fopen(path, "r");
     if (!f) return false;
@@ -92,24 +95,30 @@ bool cache_lookup(const char *path, const std::string &key, int &w, int &max_sub
         if (!std::strstr(line, needle.c_str())) continue;
         const char *pw = std::strstr(line, "\"w\": ");
         const char *pm = std::strstr(line, "\"max_sub\": ");
+        const char *pb = std::strstr(line, "\"bin_shape\": ");
         const char *pe = std::strstr(line, "\"err\": ");
-        if (pw && pm && pe) {
+        if (pw && pm && pb && pe) {  // lines without a bin shape are from an older tuner: a miss
             w = std::atoi(pw + 5);
             max_sub = std::atoi(pm + 11);
+            bin_shape = std::atoi(pb + 13);
             err = std::atof(pe + 7);
-            hit = w >= 2 && w <= NODE_MAXW && max_sub > 0;  // the last matching line wins
+            // the last matching line wins
+            hit = w >= 2 && w <= NODE_MAXW && max_sub > 0 && bin_shape >= 1 && bin_shape <= NBIN_SHAPES;
         }
     }
     std::fclose(f);
     return hit;
 }
 
-void cache_store(const char *path, const std::string &key, int w, int max_sub, double err, double ms) {
+void cache_store(const char *path, const std::string &key, int w, int max_sub, int bin_shape, double err,
+                 double ms) {
     if (!path) return;
     FILE *f = std::fopen(path, "a");
     if (!f) return;
-    std::fprintf(f, "{\"key\": \"%s\", \"w\": %d, \"max_sub\": %d, \"err\": %.6g, \"ms\": %.6g}\n",
-                 key.c_str(), w, max_sub, err, ms);
+    std::fprintf(f,
+                 "{\"key\": \"%s\", \"w\": %d, \"max_sub\": %d, \"bin_shape\": %d, \"err\": %.6g, "
+                 "\"ms\": %.6g}\n",
+                 key.c_str(), w, max_sub, bin_shape, err, ms);
     std::fclose(f);
 }
 
@@ -207,13 +216,14 @@ extern "C" int nlint_autotune(const nlint_params *in, double tol, const char *ca
         p.precision = tol >= 1e-7 ? NLINT_FP32 : NLINT_FP64;
     if (!cache_path) cache_path = std::getenv("NLINT_TUNE_CACHE");
     const std::string key = cache_key(p, tol);
-    int w = 0, max_sub = 0;
+    int w = 0, max_sub = 0, bshape = 0;
     double err = 0.0, ms = 0.0;
-    if (cache_lookup(cache_path, key, w, max_sub, err)) {
+    if (cache_lookup(cache_path, key, w, max_sub, bshape, err)) {
         p.w = w;
         p.max_sub = max_sub;
+        p.bin_shape = bshape;
         *out = p;
-        if (rep) *rep = nlint_tune_report{w, max_sub, err, 0.0, 1};
+        if (rep) *rep = nlint_tune_report{w, max_sub, err, 0.0, 1, bshape};
         return NLINT_OK;
     }
     if (p.device >= 0 && cudaSetDevice(p.device) != cudaSuccess)
@@ -267,20 +277,41 @@ extern "C" int nlint_autotune(const nlint_params *in, double tol, const char *ca
         return tfail(NLINT_EUNSUPPORTED, m.c_str());
     }
 
-    // fastest subproblem size at that width
-    const int cands[] = {256, 512, 1024, 2048};
-    int best_sub = 0;
-    double best_ms = 1e30;
-    for (int cs : cands) {
+    // fastest bin shape at that width (default subproblem size), then the fastest subproblem size
+    // for that shape; a shape whose tile does not fit at this width is skipped
+    auto time_candidate = [&](int bs, int cs, double &t) -> int {
         nlint_params cp = p;
         cp.w = best_w;
         cp.max_sub = cs;
+        cp.bin_shape = bs;
         nlint_plan pl = nullptr;
-        rc = nlint_plan_create_ex(&cp, &pl);
-        if (rc) return rc;
-        double t = 0.0;
-        rc = time_plan(pl, p.precision, rho, 5, s, t);
+        const int crc = nlint_plan_create_ex(&cp, &pl);
+        if (crc == NLINT_EUNSUPPORTED) return crc;
+        if (crc) return crc;
+        const int trc = time_plan(pl, p.precision, rho, 5, s, t);
         nlint_plan_destroy(pl);
+        return trc;
+    };
+    const bool f64 = p.precision == NLINT_FP64;
+    int best_bs = 0, best_sub = 0;
+    double best_ms = 1e30;
+    for (int bs = 1; bs <= NBIN_SHAPES; bs++) {
+        if (!bin_shape_built(f64, p.d, bs)) continue;
+        double t = 0.0;
+        rc = time_candidate(bs, 0, t);
+        if (rc == NLINT_EUNSUPPORTED) continue;
+        if (rc) return rc;
+        if (t < best_ms) {
+            best_ms = t;
+            best_bs = bs;
+        }
+    }
+    if (best_bs == 0) return tfail(NLINT_EUNSUPPORTED, "autotune: no bin shape fits at this width");
+    const int cands[] = {256, 512, 1024, 2048};
+    best_ms = 1e30;
+    for (int cs : cands) {
+        double t = 0.0;
+        rc = time_candidate(best_bs, cs, t);
         if (rc) return rc;
         if (t < best_ms) {
             best_ms = t;
@@ -289,8 +320,9 @@ extern "C" int nlint_autotune(const nlint_params *in, double tol, const char *ca
     }
     p.w = best_w;
     p.max_sub = best_sub;
-    cache_store(cache_path, key, best_w, best_sub, best_err, best_ms);
+    p.bin_shape = best_bs;
+    cache_store(cache_path, key, best_w, best_sub, best_bs, best_err, best_ms);
     *out = p;
-    if (rep) *rep = nlint_tune_report{best_w, best_sub, best_err, best_ms, 0};
+    if (rep) *rep = nlint_tune_report{best_w, best_sub, best_err, best_ms, 0, best_bs};
     return NLINT_OK;
 }

@@ -134,3 +134,34 @@ def test_batch_uses_each_plans_form(pkg):
         assert np.max(np.abs(ub - u)) <= 1e-5 * np.max(np.abs(u)), i
         assert abs(Es[i] - E) <= 1e-5 * abs(E), i
     batch.close()
+
+
+def test_batch_large_members_of_the_64_density_set_match_oracle(pkg, tmp_path):
+    """The 96^3 and 128^3 members of the 64-density workload (its own seeded densities, axes
+    and node counts), on autotuned plans inside a batch graph, against the oracle."""
+    import bench
+    members = synth.config5("fp32")
+    pick = []
+    for n in (96, 128):
+        for kern in ("coulomb", "dipole"):
+            m = next((m for m in members if m.n == n and m.kernel == kern), None)
+            if m is not None:
+                pick.append(m)
+    assert any(m.n == 96 for m in pick) and any(m.n == 128 for m in pick)
+    import os
+    os.environ["NLINT_TUNE_CACHE"] = str(tmp_path / "tune.jsonl")
+    try:
+        prms, reps = bench.tuned_member_params(pkg, pick, "fp32", torch.device("cuda", 0))
+    finally:
+        del os.environ["NLINT_TUNE_CACHE"]
+    plans = [pkg.Plan(3, m.n, m.L, params=q, device=0) for m, q in zip(pick, prms)]
+    rhos = [torch.from_numpy(m.rho()).to("cuda:0", torch.float32) for m in pick]
+    batch = pkg.Batch(plans)
+    us, Es = batch.eval(rhos, lam=1.0)
+    torch.cuda.synchronize()
+    for i, m in enumerate(pick):
+        ref = pipeline.oracle_eval(m.rho(), m.L, m.nodes, m.kernel, axis=m.axis, setting="fp32ref")
+        err = np.max(np.abs(us[i].double().cpu().numpy() - ref["u"])) / np.max(np.abs(ref["u"]))
+        assert err <= 1e-5, (m.n, m.kernel, err)
+        assert abs(float(Es[i]) - ref["E"]) <= 1e-5 * ref["E_scale"], (m.n, m.kernel)
+    batch.close()
