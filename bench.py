@@ -45,14 +45,14 @@ TOL = 1e-5                          # stated relative L-inf tolerance of the FP3
 # Measured with ncu on the 256^3 FP32 workload (one launch of each kernel, one pass of
 # dram__bytes_read.sum and dram__bytes_write.sum).
 TRAFFIC = {
-    "interp": {"bytes": 734.5e6, "src": "aab02eb942c297d4"},
-    "spread": {"bytes": 971.5e6, "src": "aab02eb942c297d4"},
-    "fwd_fft_z": {"bytes": 150.6e6, "src": "2cc1764e7d09412c"},
-    "fwd_fft_y": {"bytes": 342.4e6, "src": "2cc1764e7d09412c"},
-    "fwd_fft_x": {"bytes": 482.4e6, "src": "2cc1764e7d09412c"},
-    "inv_fft_x": {"bytes": 530.3e6, "src": "2cc1764e7d09412c"},
-    "inv_fft_y": {"bytes": 369.6e6, "src": "2cc1764e7d09412c"},
-    "inv_fft_z": {"bytes": 247.5e6, "src": "2cc1764e7d09412c"},
+    "interp": {"bytes": 455.5e6, "src": "bae7b46b82778455"},
+    "spread": {"bytes": 662.1e6, "src": "bae7b46b82778455"},
+    "fwd_fft_z": {"bytes": 153.4e6, "src": "9798d38f2ab10d10"},
+    "fwd_fft_y": {"bytes": 341.3e6, "src": "9798d38f2ab10d10"},
+    "fwd_fft_x": {"bytes": 482.7e6, "src": "9798d38f2ab10d10"},
+    "inv_fft_x": {"bytes": 530.4e6, "src": "9798d38f2ab10d10"},
+    "inv_fft_y": {"bytes": 370.0e6, "src": "9798d38f2ab10d10"},
+    "inv_fft_z": {"bytes": 247.5e6, "src": "9798d38f2ab10d10"},
 }
 
 
@@ -178,13 +178,15 @@ def stage_bytes(info: dict, stage: str) -> float:
 
 def layout_bytes(info: dict, stage: str) -> float:
     """DRAM bytes of one launch as the kernels store their data: the ball once plus the node
-    records each node kernel reads and writes (the packed stencil origin and the d w stencil
-    values the plan precomputes), W and c.  Reported beside the algorithmic model, which ``frac`` divides by."""
+    records each node kernel reads and writes (FP32 plans: a 16-byte record of the packed
+    stencil origin and three offsets; FP64 plans: the packed origin and the d w stencil values
+    the plan precomputes), W and c.  Reported beside the algorithmic model, which ``frac``
+    divides by."""
     s = 4.0 if info["precision"] == 0 else 8.0
     b = 2 * s
     n, M = info["n_fine"], info["n_half_nodes"]
     ball = (np.pi / 12.0) * n ** 3 * b
-    rec = 4.0 + 3 * info["w"] * s
+    rec = 16.0 if info["precision"] == 0 else 4.0 + 3 * info["w"] * s
     if stage == "interp":
         return float(ball + M * (rec + s + b))
     if stage == "spread":

@@ -35,8 +35,12 @@ def test_spread_and_interp_bytes():
               "inv_fft_y", "inv_fft_z")
     tot = sum(bench.stage_bytes(C4, st) for st in stages)
     assert tot == pytest.approx(bench.path_bytes(C4), rel=5e-3)
-    # the stored records: packed origin and 21 stencil values, W and c for the interpolation
-    assert bench.layout_bytes(C4, "interp") == pytest.approx(ball + 4096000 * (4 + 84 + 4 + 8))
+    # the stored records: FP32 16-byte origin/offset record, W and c for the interpolation;
+    # FP64: packed origin and 3 w stencil values
+    assert bench.layout_bytes(C4, "interp") == pytest.approx(ball + 4096000 * (16 + 4 + 8))
+    c4_64 = dict(C4, precision=1, w=13)
+    ball64 = 2 * ball
+    assert bench.layout_bytes(c4_64, "spread") == pytest.approx(ball64 + 4096000 * (4 + 39 * 8 + 16))
 
 
 def test_node_flops():
