@@ -45,7 +45,10 @@ __host__ __device__ constexpr int fft_pprod(int n, int s) {  // product of the r
 // (512^3 fine grid, FP32): the values per thread that gave the shortest pass per mode.
 constexpr int FFT_VPT0 = 16, FFT_MINB0 = 0;                 // column passes
 constexpr int FFT_VPT1 = 16, FFT_MINB1 = 0;                 // row passes
-constexpr int FFT_PACKED_VPT = 8, FFT_PACKED_MINB = 3;      // packed real-data column passes
+// packed real-data column passes: four resident CTAs of 512 threads cap them at 32 registers
+// (40-76 bytes of spills at n = 512) and still measured faster than three (forward 0.094 ->
+// 0.087 ms, inverse 0.156 -> 0.133 ms at n = 512): these passes are bound by load latency
+constexpr int FFT_PACKED_VPT = 8, FFT_PACKED_MINB = 4;
 constexpr int FFT_DUAL_VPT = 16, FFT_DUAL_MINB = 2;         // dual column passes (modes 6, 7)
 __host__ __device__ constexpr int fft_vpt_small(int mode) {
     return mode == 0 ? FFT_VPT0 : mode == 1 ? FFT_VPT1 : mode == 2 ? 8

@@ -178,6 +178,31 @@ __device__ __forceinline__ void flush_tile(const A *tr, const A *ti, int4 bo, co
     const int n = nd.n, pad = nd.pad, slot = bo.w;
     const int nplanes = n / 2 + 1 + 2 * pad;
     const T inv_s = (T)ldexp(1.0, -ex);
+    if constexpr (D == 3 && sizeof(T) == 4) {
+        if (slot < 0 && (bo.z & 1) == 0) {
+            // FP32: two adjacent axis-2 cells per 16-byte vector atomic.  The bin origin along
+            // axis 2 is even (the plan aligns its bins), n is even, so a pair starts at an even
+            // grid index: 16-byte aligned and never split by the periodic wrap
+            const int64_t nn = (int64_t)n * n;
+            constexpr int PPR = (G_::T2 + 1) / 2;  // cell pairs per row
+            for (int cp = threadIdx.x; cp < G_::T1 * PPR; cp += blockDim.x) {
+                const int a1 = cp / PPR, a2 = 2 * (cp - a1 * PPR);
+                const bool two = a2 + 1 < G_::T2;
+                const int64_t gb = (int64_t)wrap1(bo.y + a1, n) * n + wrap1(bo.z + a2, n);
+#pragma unroll 4
+                for (int a0 = 0; a0 < G_::T0; a0++) {
+                    const int c0 = a0 * PLANE + a1 * G_::P2 + a2;
+                    const A qr0 = tr[c0], qi0 = ti[c0];
+                    const A qr1 = two ? tr[c0 + 1] : 0, qi1 = two ? ti[c0 + 1] : 0;
+                    const int pl = bo.x + a0 + pad;
+                    if ((qr0 == 0 && qi0 == 0 && qr1 == 0 && qi1 == 0) || pl < 0 || pl >= nplanes) continue;
+                    atomicAdd(reinterpret_cast<float4 *>(H + pl * nn + gb),
+                              make_float4((T)qr0 * inv_s, (T)qi0 * inv_s, (T)qr1 * inv_s, (T)qi1 * inv_s));
+                }
+            }
+            return;
+        }
+    }
     if (D == 3 && slot < 0) {
         // by (axis-1, axis-2) column, as the tile load: wrapped offsets once, then the planes of
         // the extended grid at a constant stride

@@ -498,6 +498,9 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
     // (a signed FFT index never exceeds the unwrapped cell index in magnitude, so the bound
     // holds for the stored grid too); a ball that covers the whole grid is no window
     p->ball2 = (ball2 < (int64_t)d * (n / 2) * (n / 2)) ? ball2 : 0;
+    // 3D: bins start at even cells along axis 2 (the spreading's tile flush adds two adjacent
+    // cells per 16-byte vector atomic, which must start at an even grid index)
+    if (d == 3 && Mh) lo[2] -= lo[2] & 1;
     // bins: boxes of B[ax] stencil-origin cells starting at lo[ax]; tile = B + w - 1.  The
     // shape is a plan parameter (the autotuner searches it); an automatic choice whose tile
     // does not fit in shared memory at this width falls back to the smallest shape
