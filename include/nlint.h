@@ -130,6 +130,12 @@ int nlint_plan_create(int d, int64_t n, double L, int kernel, const double *dipo
                       double eps, nlint_plan *out);
 int nlint_plan_create_ex(const nlint_params *p, nlint_plan *out);
 int nlint_plan_info(nlint_plan plan, nlint_info *info);
+/* Device-side waits of the plan's kernels (the interpolation's wait for its TMA tile load) give
+ * up after a bounded number of polls and set a status word instead of hanging.  This call
+ * synchronises the plan's device, reads and clears that word: NLINT_ETIMEOUT if a wait ran out
+ * since the last check (the evaluation that saw it produced invalid results), else NLINT_OK.
+ * Errors: NLINT_EINVAL (NULL plan), NLINT_ECUDA. */
+int nlint_plan_check(nlint_plan plan);
 void nlint_plan_destroy(nlint_plan plan); /* NULL is a no-op; waits for the plan's work */
 
 /* u = U * rho on the grid (Algorithm 1 steps 4-5: type-2 NUFFT, multiply by W_j, type-1

@@ -26,6 +26,7 @@ STATUS = {0: "NLINT_OK", -1: "NLINT_EINVAL", -2: "NLINT_ENOMEM", -3: "NLINT_ECUD
 
 EXPORTED = [
     "nlint_params_default", "nlint_plan_create", "nlint_plan_create_ex", "nlint_plan_info",
+    "nlint_plan_check",
     "nlint_plan_destroy", "nlint_eval", "nlint_eval_energy", "nlint_energy", "nlint_eval_host",
     "nlint_eval_host_many",
     "nlint_type2", "nlint_type1", "nlint_plan_nodes", "nlint_set_stage_timing",
@@ -93,6 +94,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.nlint_plan_create.argtypes = [ci, i64, dbl, ci, ctypes.POINTER(dbl), dbl, pplan]
     lib.nlint_plan_create_ex.argtypes = [ctypes.POINTER(nlint_params), pplan]
     lib.nlint_plan_info.argtypes = [vp, ctypes.POINTER(nlint_info)]
+    lib.nlint_plan_check.argtypes = [vp]
     lib.nlint_plan_destroy.argtypes = [vp]
     lib.nlint_plan_destroy.restype = None
     lib.nlint_eval.argtypes = [vp, vp, vp, vp]
@@ -398,6 +400,11 @@ class Plan:
         k = ctypes.c_int()
         _check(self._lib.nlint_stage_times(self._h, ms, names, 32, ctypes.byref(k)))
         return [(names[i].decode(), ms[i]) for i in range(k.value)]
+
+    def check(self):
+        """Raise NlintError (NLINT_ETIMEOUT) if a bounded device-side wait of this plan's kernels
+        ran out since the last check (synchronises the device)."""
+        _check(self._lib.nlint_plan_check(self._h))
 
     def launch_count(self) -> int:
         """Kernels this plan has launched so far (a host-side counter kept by the library)."""

@@ -49,7 +49,7 @@ constexpr int FFT_VPT1 = 16, FFT_MINB1 = 0;                 // row passes
 // (40-76 bytes of spills at n = 512) and still measured faster than three (forward 0.094 ->
 // 0.087 ms, inverse 0.156 -> 0.133 ms at n = 512): these passes are bound by load latency
 constexpr int FFT_PACKED_VPT = 8, FFT_PACKED_MINB = 4;
-constexpr int FFT_DUAL_VPT = 16, FFT_DUAL_MINB = 2;         // dual column passes (modes 6, 7)
+constexpr int FFT_DUAL_VPT = 16, FFT_DUAL_MINB = 3;         // dual column passes (modes 6, 7)
 __host__ __device__ constexpr int fft_vpt_small(int mode) {
     return mode == 0 ? FFT_VPT0 : mode == 1 ? FFT_VPT1 : mode == 2 ? 8
          : (mode == 3 || mode == 4) ? FFT_PACKED_VPT : (mode == 6 || mode == 7) ? FFT_DUAL_VPT : 16;

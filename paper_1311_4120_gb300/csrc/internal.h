@@ -1,5 +1,6 @@
 // Internal declarations shared by the host plan code and the kernel launchers.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -133,12 +134,18 @@ struct NodeDesc {
     int B[3], T[3];      // bin and tile extents per array axis
     int64_t nsub;        // number of subproblems
     const int4 *subs;    // per subproblem {first node, node count, bin, 0}
-    // FP32 3D plans: the nodes of each bin are ordered in groups of at most 32 whose stencil
-    // origins share no shared-memory bank unless they are equal (see build_node_groups); the
-    // interpolation gives each node of a group a lane of its own
-    int64_t ngsub;       // interpolation subproblems (runs of groups of one bin)
-    const int4 *gsubs;   // per interpolation subproblem {first group, group count, bin, 0}
-    const int32_t *grp;  // group g holds nodes grp[g] .. grp[g + 1] - 1
+    // FP32 3D plans: the nodes of each bin are ordered in half-groups of at most 16 whose
+    // stencil origins share no shared-memory bank pair unless they are equal (see
+    // build_node_groups); the interpolation gives each node of a half-group a lane of its own,
+    // two half-groups (one per half-warp) per warp
+    int64_t ngsub;       // interpolation subproblems (runs of half-group pairs of one bin)
+    const int4 *gsubs;   // per interpolation subproblem {first pair, pair count, bin, 0}
+    const int32_t *grp;  // half-group g holds nodes grp[g] .. grp[g + 1] - 1 (bins: even counts)
+    // FP32 3D Algorithm 1 plans: a tiled tensor map of the fine grid G (8-byte cells, the
+    // stored half: n x n x (n/2 + 1)) from which the interpolation stages its tiles by TMA;
+    // NULL: plain loads
+    const CUtensorMap *tmap;
+    int *status;         // device word: bit 0 set when a bounded wait in a kernel ran out
     const int4 *bins;    // per bin {origin axis 0, axis 1, axis 2, crowd slot or -1}
     int ncrowd;          // crowded bins (FP32 plans): their tiles are summed in FP64
     double2 *crowd;      // ncrowd tiles of complex doubles
@@ -155,14 +162,14 @@ struct NodeDesc {
 std::vector<int16_t> build_pair_order(int w, int row, int banks, int lanes, int group);
 
 // Splits one bin's nodes (indices first .. first + count - 1, sorted by stencil origin; org[i]
-// is node i's origin as a tile offset) into groups of at most 32 nodes in which two nodes have
-// either the same origin or origins in different shared-memory banks (offsets that differ mod
-// 32).  A lane per node then reads the node's stencil (the same offsets from every origin)
-// without bank conflicts.  Greedy: origins with the most remaining nodes first, each group
-// taking as many nodes of one origin as fit.  Appends the bin's new node order to `order` and
-// each group's size to `sizes`.
-void build_node_groups(const int32_t *org, int64_t first, int64_t count, std::vector<int64_t> &order,
-                       std::vector<int> &sizes);
+// is node i's origin as a tile offset in cells) into groups of at most `lanes` nodes in which
+// two nodes have either the same origin or origins whose offsets differ mod `banks` (different
+// shared-memory banks, or bank pairs for 8-byte cells).  A lane per node then reads the node's
+// stencil (the same offsets from every origin) without bank conflicts.  Greedy: origins with
+// the most remaining nodes first, each group taking as many nodes of one origin as fit.
+// Appends the bin's new node order to `order` and each group's size to `sizes`.
+void build_node_groups(const int32_t *org, int64_t first, int64_t count, int lanes, int banks,
+                       std::vector<int64_t> &order, std::vector<int> &sizes);
 
 // Bin shapes (stencil-origin cells per array axis).  3D: 1 = 8 x 8 x 8, 2 = 4 x 8 x 8,
 // 3 = 8 x 16 x 16, 4 = 16 x 16 x 16; 2D: 16 x 16 for every shape.  The kernels are compiled

@@ -33,6 +33,7 @@
 #include "internal.h"
 
 #include <climits>
+#include <cstring>
 
 namespace nlint {
 
@@ -839,13 +840,51 @@ __global__ void __launch_bounds__(SUB_THREADS) interp_f32_kernel(NodeDesc nd, co
     }
 }
 
-// FP32 3D interpolation with a lane per node.  The plan orders each bin's nodes in groups of
-// at most 32 whose stencil origins are equal or fall in different shared-memory banks, so a
-// warp reading the same stencil offset from each lane's origin is served by one wavefront
-// (equal origins are broadcasts).  Each lane evaluates its node's 3w stencil values itself and
-// sums its w^3 cells in registers: no value exchange between lanes and no reduction, so the
-// shared reads and their multiply-adds are nearly the whole instruction stream.  Lanes past a
-// group's size idle.
+// Device-side waits give up after this many polls (each try_wait may also suspend the thread
+// for a while); the kernel then sets bit 0 of the plan's status word and returns.
+static constexpr long long WAIT_POLLS = 1ll << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+// true when the mbarrier's phase `parity` has completed
+__device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok) : "r"(mbar), "r"(parity) : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity) {
+    for (long long i = 0; i < WAIT_POLLS; i++)
+        if (mbar_try_wait(mbar, parity)) return true;
+    return false;
+}
+
+// Stages the bin's tile of G as 8-byte complex cells, rows of T2 cells (the layout of the TMA
+// box), by plain loads: tiles that wrap around the periodic grid or reach into the mirrored
+// half (read as conj(G[-l])).
+template <typename G_>
+__device__ __forceinline__ void stage_tile_cx(const float2 *__restrict__ G, int4 bo, int n, float2 *tile) {
+    constexpr int RP = G_::T1 * G_::T2, NC = G_::T0 * RP;
+    const bool inside = bo.x >= 0 && bo.x + G_::T0 - 1 <= n / 2;
+    for (int cell = threadIdx.x; cell < NC; cell += blockDim.x) {
+        const int a0 = cell / RP, rem = cell - a0 * RP, a1 = rem / G_::T2, a2 = rem - a1 * G_::T2;
+        tile[cell] = inside ? G[((int64_t)(bo.x + a0) * n + wrap1(bo.y + a1, n)) * n + wrap1(bo.z + a2, n)]
+                            : fetch_half<float, 3>(G, n, bo.x + a0, bo.y + a1, bo.z + a2);
+    }
+}
+
+// FP32 3D interpolation with a lane per node.  The plan orders each bin's nodes in half-groups
+// of at most 16 whose stencil origins are equal or fall in different shared-memory bank pairs;
+// a warp takes two half-groups, one per half-warp, and its lanes, reading the same stencil
+// offset from their own origins, are served without bank conflicts (8-byte loads are served
+// per half-warp; equal origins are broadcasts).  Each lane evaluates its node's 3w stencil
+// values itself and sums its w^3 cells in registers: no value exchange between lanes and no
+// reduction.  The tile (8-byte complex cells, the layout of a TMA box) is loaded by one TMA
+// copy when it lies in the stored half without wrapping, else by plain loads.
 template <int W>
 __device__ __forceinline__ void es_phi_axis(float u, float beta, float (&f)[W]) {
 #pragma unroll
@@ -857,48 +896,86 @@ __device__ __forceinline__ void es_phi_axis(float u, float beta, float (&f)[W]) 
 }
 
 template <int W, int BS, bool EN>
-__global__ void __launch_bounds__(SUB_THREADS) interp_grp_kernel(NodeDesc nd, const float2 *__restrict__ G,
+__global__ void __launch_bounds__(SUB_THREADS) interp_grp_kernel(NodeDesc nd, const __grid_constant__ CUtensorMap tmap,
+                                                                const float2 *__restrict__ G,
                                                                 float2 *__restrict__ c_out, int apply_W,
                                                                 double2 *__restrict__ epart) {
     using G_ = Geo<float, 3, W, BS>;
-    constexpr int PLANE = G_::PLANE, P2 = G_::P2, NW = SUB_THREADS / 32;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float *tr = reinterpret_cast<float *>(smem_raw);
-    float *ti = tr + G_::NCELL;
+    constexpr int T0 = G_::T0, T1 = G_::T1, T2 = G_::T2, RP = T1 * T2, NW = SUB_THREADS / 32;
+    constexpr unsigned TILE_BYTES = (unsigned)(T0 * RP) * 8u;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // the TMA destination must be 128-byte aligned: the launcher adds 128 bytes of room
+    float2 *tile = reinterpret_cast<float2 *>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
+    __shared__ __align__(8) unsigned long long mbar;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int4 gs = nd.gsubs[blockIdx.x];
     const int4 bo = nd.bins[gs.z];
-    stage_tile<float, G_, 3>(G, bo, nd.n, tr, ti);
-    __syncthreads();
+    const int n = nd.n;
+
+    // one TMA copy of the box (x0, y0, z0) when the tile sits in the stored half without wrapping:
+    // along y and x its cells are bo + a or, for a bin at negative frequencies, n + bo + a
+    const bool wrap_y = bo.y < 0 && bo.y + T1 > 0, wrap_x = bo.z < 0 && bo.z + T2 > 0;
+    const bool tma = nd.tmap && bo.x >= 0 && bo.x + T0 - 1 <= n / 2 && !wrap_y && !wrap_x &&
+                     bo.y + T1 <= n && bo.z + T2 <= n && bo.y >= -n && bo.z >= -n;
+    if (tma) {
+        const uint32_t mb = smem_u32(&mbar);
+        if (threadIdx.x == 0) {
+            const int x0 = bo.z < 0 ? bo.z + n : bo.z, y0 = bo.y < 0 ? bo.y + n : bo.y, z0 = bo.x;
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(TILE_BYTES)
+                         : "memory");
+            asm volatile(
+                "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes "
+                "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(tile)),
+                "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(x0), "r"(y0), "r"(z0), "r"(mb)
+                : "memory");
+        }
+        __syncthreads();  // the mbarrier is initialised before anyone polls it
+        const bool ok = mbar_wait_bounded(mb, 0);
+        if (__syncthreads_or(!ok)) {
+            // the copy did not arrive in time (the whole CTA agrees): report, give the copy a
+            // second bounded wait to land, and return without reading the tile
+            if (threadIdx.x == 0) {
+                if (nd.status) atomicOr(nd.status, 1);
+                (void)mbar_wait_bounded(mb, 0);
+            }
+            return;
+        }
+    } else {
+        stage_tile_cx<G_>(G, bo, n, tile);
+        __syncthreads();
+    }
 
     const float beta = (float)nd.beta;
     const float *__restrict__ Wv = reinterpret_cast<const float *>(nd.W);
     EAcc<float> eacc;
-    // each lane's next record and weight are loaded one group ahead
-    const int gend = gs.x + gs.y;
-    int g = gs.x + wid;
+    const int half = lane >> 4, hl = lane & 15;
+    // each lane's next record and weight are loaded one half-group pair ahead
+    const int pend = gs.x + gs.y;
+    int pr = gs.x + wid;
     int first = 0, cnt = 0;
     int4 r_n = make_int4(0, 0, 0, 0);
     float W_n = 1.0f;
-    if (g < gend) {
-        first = nd.grp[g];
-        cnt = nd.grp[g + 1] - first;
-        if (lane < cnt) {
-            r_n = nd.pos[first + lane];
-            if (apply_W) W_n = Wv[first + lane];
+    if (pr < pend) {
+        first = nd.grp[2 * pr + half];
+        cnt = nd.grp[2 * pr + half + 1] - first;
+        if (hl < cnt) {
+            r_n = nd.pos[first + hl];
+            if (apply_W) W_n = Wv[first + hl];
         }
     }
-    for (; g < gend; g += NW) {
+    for (; pr < pend; pr += NW) {
         const int4 r = r_n;
         const float Wj = W_n;
-        const int node = first + lane;
-        const bool mine = lane < cnt;
-        if (g + NW < gend) {
-            first = nd.grp[g + NW];
-            cnt = nd.grp[g + NW + 1] - first;
-            if (lane < cnt) {
-                r_n = nd.pos[first + lane];
-                if (apply_W) W_n = Wv[first + lane];
+        const int node = first + hl;
+        const bool mine = hl < cnt;
+        if (pr + NW < pend) {
+            first = nd.grp[2 * (pr + NW) + half];
+            cnt = nd.grp[2 * (pr + NW) + half + 1] - first;
+            if (hl < cnt) {
+                r_n = nd.pos[first + hl];
+                if (apply_W) W_n = Wv[first + hl];
             }
         }
         if (mine) {
@@ -906,8 +983,7 @@ __global__ void __launch_bounds__(SUB_THREADS) interp_grp_kernel(NodeDesc nd, co
             es_phi_axis<W>(__int_as_float(r.y), beta, fz);
             es_phi_axis<W>(__int_as_float(r.z), beta, fy);
             es_phi_axis<W>(__int_as_float(r.w), beta, fx);
-            const int o = origin_index<G_, 3>(r.x & 255, (r.x >> 8) & 255, (r.x >> 16) & 255);
-            const float *pr = tr + o, *pi = ti + o;
+            const float2 *pt = tile + ((r.x & 255) * T1 + ((r.x >> 8) & 255)) * T2 + ((r.x >> 16) & 255);
             float ar = 0.0f, ai = 0.0f;
 #pragma unroll(W <= 8 ? W : 1)
             for (int qa = 0; qa < W; qa++) {
@@ -917,9 +993,9 @@ __global__ void __launch_bounds__(SUB_THREADS) interp_grp_kernel(NodeDesc nd, co
                     float sr = 0.0f, si = 0.0f;
 #pragma unroll
                     for (int q0 = 0; q0 < W; q0++) {
-                        const int off = q0 * PLANE + qa * P2 + qb;
-                        sr = fmaf(fz[q0], pr[off], sr);
-                        si = fmaf(fz[q0], pi[off], si);
+                        const float2 g = pt[q0 * RP + qa * T2 + qb];
+                        sr = fmaf(fz[q0], g.x, sr);
+                        si = fmaf(fz[q0], g.y, si);
                     }
                     br = fmaf(fx[qb], sr, br);
                     bi = fmaf(fx[qb], si, bi);
@@ -1124,18 +1200,26 @@ static cudaError_t launch_interp_w(const NodeDesc &nd, const void *G, void *c_ou
         if (!nd.grp) return cudaErrorInvalidValue;
         const unsigned ggrid = (unsigned)nd.ngsub;
         if (ggrid == 0) return cudaSuccess;
+        using G_ = Geo<float, 3, W, BS>;
+        // the interleaved tile plus room to align it to 128 bytes (not above the spreading's
+        // padded planes of 4-byte cells, which node_smem sizes)
+        const size_t tsm = (size_t)G_::T0 * G_::T1 * G_::T2 * 8 + 128;
+        const size_t gsm = tsm > smem ? tsm : smem;
+        CUtensorMap tm;
+        if (nd.tmap) tm = *nd.tmap;
+        else std::memset(&tm, 0, sizeof tm);
         if (epart) {
             cudaError_t e = cudaFuncSetAttribute(interp_grp_kernel<W, BS, true>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
             if (e != cudaSuccess) return e;
-            interp_grp_kernel<W, BS, true><<<ggrid, SUB_THREADS, smem, s>>>(
-                nd, (const float2 *)G, (float2 *)c_out, apply_W, epart);
+            interp_grp_kernel<W, BS, true><<<ggrid, SUB_THREADS, gsm, s>>>(
+                nd, tm, (const float2 *)G, (float2 *)c_out, apply_W, epart);
         } else {
             cudaError_t e = cudaFuncSetAttribute(interp_grp_kernel<W, BS, false>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
             if (e != cudaSuccess) return e;
-            interp_grp_kernel<W, BS, false><<<ggrid, SUB_THREADS, smem, s>>>(
-                nd, (const float2 *)G, (float2 *)c_out, apply_W, nullptr);
+            interp_grp_kernel<W, BS, false><<<ggrid, SUB_THREADS, gsm, s>>>(
+                nd, tm, (const float2 *)G, (float2 *)c_out, apply_W, nullptr);
         }
     } else if constexpr (sizeof(T) == 4) {
         if (epart) {

@@ -109,8 +109,8 @@ std::vector<int16_t> build_pair_order(int w, int row, int banks, int lanes, int 
     return out;
 }
 
-void build_node_groups(const int32_t *org, int64_t first, int64_t count, std::vector<int64_t> &order,
-                       std::vector<int> &sizes) {
+void build_node_groups(const int32_t *org, int64_t first, int64_t count, int lanes, int banks,
+                       std::vector<int64_t> &order, std::vector<int> &sizes) {
     struct Run {
         int32_t o;
         int64_t next, end;
@@ -129,12 +129,12 @@ void build_node_groups(const int32_t *org, int64_t first, int64_t count, std::ve
     while (left > 0) {
         int32_t owner[32];
         for (int r = 0; r < 32; r++) owner[r] = -1;  // origin offsets are >= 0
-        int slots = 32;
+        int slots = lanes;
         while (head < runs.size() && runs[head].next == runs[head].end) head++;
         for (size_t u = head; u < runs.size() && slots > 0; u++) {
             Run &ru = runs[u];
             if (ru.next == ru.end) continue;
-            const int r = ru.o & 31;
+            const int r = ru.o % banks;
             if (owner[r] >= 0 && owner[r] != ru.o) continue;
             owner[r] = ru.o;
             const int64_t take = std::min<int64_t>(slots, ru.end - ru.next);
@@ -142,9 +142,42 @@ void build_node_groups(const int32_t *org, int64_t first, int64_t count, std::ve
             ru.next += take;
             slots -= (int)take;
         }
-        sizes.push_back(32 - slots);
-        left -= 32 - slots;
+        sizes.push_back(lanes - slots);
+        left -= lanes - slots;
     }
+}
+
+// A tiled tensor map of the stored half of the fine grid G (n x n x (n/2 + 1) complex floats,
+// handled as 8-byte cells, x fastest) with boxes of T[2] x T[1] x T[0] cells, for TMA loads of
+// the interpolation's tiles.  cuTensorMapEncodeTiled is reached through the runtime's driver
+// entry points (the library does not link the driver library).  false: no tensor map (the
+// kernels then stage by plain loads).
+typedef CUresult (*tmap_encode_fn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                                   CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                   CUtensorMapFloatOOBfill);
+
+bool encode_grid_tmap(CUtensorMap *map, void *G, int n, const int *T) {
+    static tmap_encode_fn encode = nullptr;
+    if (!encode) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !f) {
+            (void)cudaGetLastError();
+            return false;
+        }
+        encode = (tmap_encode_fn)f;
+    }
+    const cuuint64_t dims[3] = {(cuuint64_t)n, (cuuint64_t)n, (cuuint64_t)(n / 2 + 1)};
+    const cuuint64_t strides[2] = {(cuuint64_t)n * 8, (cuuint64_t)n * n * 8};  // bytes, dims 1 and 2
+    const cuuint32_t box[3] = {(cuuint32_t)T[2], (cuuint32_t)T[1], (cuuint32_t)T[0]};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    if (box[0] > 256 || box[1] > 256 || box[2] > 256 || (box[0] * 8) % 16 != 0) return false;
+    return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3, G, dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace nlint
@@ -164,6 +197,9 @@ struct nlint_plan_s {
     int32_t *d_perm = nullptr, *d_mirror = nullptr;
     int4 *d_subs = nullptr, *d_bins = nullptr;
     int4 *d_gsubs = nullptr;     // FP32 3D: interpolation subproblems over node groups
+    CUtensorMap tmapG;           // FP32 3D Algorithm 1: the fine grid as a TMA tensor (has_tmap)
+    bool has_tmap = false;
+    int *d_status = nullptr;     // bit 0: a bounded device-side wait ran out
     int32_t *d_grp = nullptr;    // FP32 3D: first node of each group (and one past the last)
     int16_t *d_pairs = nullptr, *d_pairs_i = nullptr;  // spreading / interpolation lane tables
     double2 *d_epart = nullptr;  // energy-only path: one partial per subproblem
@@ -308,7 +344,7 @@ static int upload(void **dst, const std::vector<double> &v, size_t &acc) {
 }
 
 static void plan_free(nlint_plan_s *p) {
-    void *ptrs[] = {p->d_rel, p->d_pos, p->d_gsubs, p->d_grp, p->d_ker, p->d_W, p->d_fac, p->d_tw, p->d_perm, p->d_mirror,
+    void *ptrs[] = {p->d_rel, p->d_pos, p->d_gsubs, p->d_grp, p->d_status, p->d_ker, p->d_W, p->d_fac, p->d_tw, p->d_perm, p->d_mirror,
                     p->d_subs, p->d_bins, p->d_crowd_bin, p->d_crowd, p->d_pairs, p->d_pairs_i, p->d_epart, p->d_fac1, p->d_khat,
                     p->d_win, p->d_bufA, p->d_bufB, p->d_bufG, p->d_bufH, p->d_c, p->d_partials, p->d_E,
                     p->d_rho_io, p->d_u_io, p->d_rho_st[0], p->d_rho_st[1], p->d_u_st[0],
@@ -552,8 +588,10 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
     std::vector<int> gsize;          // node count of each group, bins in order
     std::vector<int64_t> gbin_end;   // one past each bin's last group
     if (grouped) {
+        // the interpolation's tile: 8-byte complex cells, rows of T2 cells (no padding: the
+        // lanes of a warp read one offset from their own origins, so only the origins matter)
         const int T1 = p->B[1] + w - 1;
-        const int P2 = tile_pitch(false, d, w, p->bin_shape);
+        const int P2 = p->B[2] + w - 1;
         std::vector<int32_t> org(Mh);
         for (int64_t o = 0; o < Mh; o++) {
             const int64_t sidx = ord[o];
@@ -566,7 +604,8 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
         for (int64_t o = 0; o < Mh;) {
             int64_t e = o;
             while (e < Mh && key[ord[e]] == key[ord[o]]) e++;
-            build_node_groups(org.data(), o, e - o, neworder, gsize);
+            build_node_groups(org.data(), o, e - o, 16, 16, neworder, gsize);
+            if (gsize.size() & 1) gsize.push_back(0);  // half-groups pair up within a bin
             gbin_end.push_back((int64_t)gsize.size());
             o = e;
         }
@@ -630,7 +669,7 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
     p->nbins = (int64_t)bins.size();
     p->ncrowd = (int)crowd_bin.size();
     if (p->nsub > (int64_t)INT32_MAX) return fail(NLINT_EUNSUPPORTED, "too many subproblems");
-    // the interpolation's subproblems: runs of at most max_sub / 32 groups of one bin
+    // the interpolation's subproblems: runs of at most max_sub / 32 half-group pairs of one bin
     std::vector<int32_t> grp;
     std::vector<int4> gsubs;
     if (grouped) {
@@ -639,8 +678,8 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
         for (size_t g = 0; g < gsize.size(); g++) grp[g + 1] = grp[g] + gsize[g];
         const int64_t gmax = std::max(1, max_sub / 32);
         int64_t g0 = 0;
-        for (size_t bi = 0; bi < bins.size(); bi++) {
-            const int64_t g1 = gbin_end[bi], ng = g1 - g0, ns = (ng + gmax - 1) / gmax;
+        for (size_t bi = 0; bi < bins.size(); bi++) {  // in pairs of half-groups
+            const int64_t g1 = gbin_end[bi] / 2, ng = g1 - g0, ns = (ng + gmax - 1) / gmax;
             for (int64_t qq = 0; qq < ns; qq++) {
                 const int64_t a = g0 + ng * qq / ns, z = g0 + ng * (qq + 1) / ns;
                 gsubs.push_back(make_int4((int)a, (int)(z - a), (int)bi, 0));
@@ -874,6 +913,12 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
             p->d_bufH = nullptr;
         }
     }
+    // FP32 3D Algorithm 1: a tensor map of the fine grid (the stored half, 8-byte cells) for the
+    // interpolation's TMA tile loads; without one the kernels stage tiles by plain loads
+    CK(cudaMalloc((void **)&p->d_status, sizeof(int)));
+    CK(cudaMemset(p->d_status, 0, sizeof(int)));
+    if (p->prec == NLINT_FP32 && d == 3 && p->algorithm == 1 && p->ngsub > 0)
+        p->has_tmap = encode_grid_tmap(&p->tmapG, p->d_bufG, n, p->T);
     p->ws_bytes = acc;
     if (p->algorithm == 2) return alg2_setup(p);
     return NLINT_OK;
@@ -1111,6 +1156,8 @@ static NodeDesc node_desc(nlint_plan_s *p) {
     nd.ngsub = p->ngsub;
     nd.gsubs = p->d_gsubs;
     nd.grp = p->d_grp;
+    nd.tmap = p->has_tmap ? &p->tmapG : nullptr;
+    nd.status = p->d_status;
     nd.bins = p->d_bins;
     nd.ncrowd = p->ncrowd;
     nd.crowd = p->d_crowd;
@@ -1429,6 +1476,20 @@ void nlint_plan_destroy(nlint_plan p) {
     cudaDeviceSynchronize();
     plan_free(p);
     delete p;
+}
+
+int nlint_plan_check(nlint_plan p) {
+    if (!p) return fail(NLINT_EINVAL, "NULL plan");
+    if (cudaSetDevice(p->device) != cudaSuccess) return fail(NLINT_ECUDA, "cudaSetDevice failed");
+    int st = 0;
+    if (cudaMemcpy(&st, p->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(NLINT_ECUDA, "reading the plan's status word failed");
+    if (st) {
+        if (cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess)
+            return fail(NLINT_ECUDA, "clearing the plan's status word failed");
+        return fail(NLINT_ETIMEOUT, "a bounded device-side wait ran out (the results of that evaluation are invalid)");
+    }
+    return NLINT_OK;
 }
 
 int nlint_plan_info(nlint_plan p, nlint_info *info) {

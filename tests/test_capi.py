@@ -87,6 +87,7 @@ def test_null_arguments(lib):
     assert lib.nlint_plan_create_ex(None, None) == -1
     assert lib.nlint_eval(None, None, None, None) == -1
     assert lib.nlint_plan_info(None, None) == -1
+    assert lib.nlint_plan_check(None) == -1
     assert lib.nlint_eval_host_many(None, 2, None, None, 1.0, None, None) == -1
     lib.nlint_plan_destroy(None)  # no-op
 

@@ -1,9 +1,12 @@
 """FP32 node kernels for every bin shape and for widths that take each lane layout.
 
-The FP32 interpolation and spreading evaluate the spreading function from each node's
-fractional offsets and exchange the values by warp shuffles; the lane layout depends on the
-width (32 lanes per node with one or two values per lane: w = 7, 11; 16 lanes per node, two
-nodes per warp, with one, two or three values per lane: w = 4, 6, 12).  Each case is checked
+The FP32 kernels evaluate the spreading function from each node's fractional offsets.  The 3D
+interpolation gives each node a lane (half-groups of bank-disjoint origins; tiles staged by
+TMA where they do not wrap, by plain loads where they do); the spreading, and the 2D kernels,
+exchange the values by warp shuffles, with a lane layout that depends on the width (32 lanes
+per node with one or two values per lane: w = 7, 11; 16 lanes per node, two nodes per warp,
+with one, two or three values per lane: w = 4, 6, 12).  After each evaluation the plan's status
+word must show that no bounded device-side wait ran out.  Each case is checked
 
   * against the FP64 oracle (eqs. 3.2 and 3.7 by Section 2's NUFFT at its parity setting), to
     the accuracy the width allows (the exponential-of-semicircle error at sigma = 2, about
@@ -67,6 +70,7 @@ def _eval(pkg, d, prec, w, bin_shape):
     u, E = plan.eval_energy(torch.from_numpy(rho).to("cuda:0", dt), lam=0.9)
     torch.cuda.synchronize()
     res = u.double().cpu().numpy(), float(E.item())
+    plan.check()  # no bounded device-side wait (the interpolation's TMA tile load) ran out
     plan.close()
     return res
 
