@@ -45,14 +45,14 @@ TOL = 1e-5                          # stated relative L-inf tolerance of the FP3
 # Measured with ncu on the 256^3 FP32 workload (one launch of each kernel, one pass of
 # dram__bytes_read.sum and dram__bytes_write.sum).
 TRAFFIC = {
-    "interp": {"bytes": 455.5e6, "src": "bae7b46b82778455"},
-    "spread": {"bytes": 662.1e6, "src": "bae7b46b82778455"},
-    "fwd_fft_z": {"bytes": 153.4e6, "src": "9798d38f2ab10d10"},
-    "fwd_fft_y": {"bytes": 341.3e6, "src": "9798d38f2ab10d10"},
-    "fwd_fft_x": {"bytes": 482.7e6, "src": "9798d38f2ab10d10"},
-    "inv_fft_x": {"bytes": 530.4e6, "src": "9798d38f2ab10d10"},
-    "inv_fft_y": {"bytes": 370.0e6, "src": "9798d38f2ab10d10"},
-    "inv_fft_z": {"bytes": 247.5e6, "src": "9798d38f2ab10d10"},
+    "interp": {"bytes": 461.0e6, "src": "b1267fc215a948ca"},
+    "spread": {"bytes": 659.1e6, "src": "b1267fc215a948ca"},
+    "fwd_fft_z": {"bytes": 167.7e6, "src": "55fb4cf0b4e622f2"},
+    "fwd_fft_y": {"bytes": 341.3e6, "src": "55fb4cf0b4e622f2"},
+    "fwd_fft_x": {"bytes": 482.4e6, "src": "55fb4cf0b4e622f2"},
+    "inv_fft_x": {"bytes": 530.7e6, "src": "55fb4cf0b4e622f2"},
+    "inv_fft_y": {"bytes": 370.2e6, "src": "55fb4cf0b4e622f2"},
+    "inv_fft_z": {"bytes": 257.2e6, "src": "55fb4cf0b4e622f2"},
 }
 
 
@@ -334,12 +334,21 @@ def path_bytes(info: dict) -> float:
 
 # ----------------------------------------------------------------------------- oracle arm
 def cpu_model() -> str:
+    """The host CPU's model name: /proc/cpuinfo on x86, lscpu's "Model name" on Arm (whose
+    /proc/cpuinfo has part numbers only), else the machine type."""
     try:
         with open("/proc/cpuinfo") as f:
             for ln in f:
                 if ln.lower().startswith(("model name", "cpu model")):
                     return ln.split(":", 1)[1].strip()
     except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
         pass
     import platform
     return platform.machine()
