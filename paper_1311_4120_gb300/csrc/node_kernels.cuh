@@ -56,6 +56,13 @@ struct Geo {
     static constexpr int LPN = node_lanes(W);
     static constexpr int NPW = 32 / LPN;                 // nodes per warp iteration
     static constexpr int PASSES = (PAIRS + LPN - 1) / LPN;
+    // resident CTAs of the FP32 spreading that the shared memory allows (its two int32 planes
+    // and the per-CTA reserve of the 228 KB per SM), at most 4 (w <= 8) or 2 (wider stencils,
+    // whose per-lane state needs more than 64 registers): its register budget follows
+    static constexpr int SPREAD_MINB_RAW = (228 * 1024) / (NCELL * 8 + 1024 + 256);
+    static constexpr int SPREAD_MINB_CAP = W <= 8 ? 4 : 2;
+    static constexpr int SPREAD_MINB = SPREAD_MINB_RAW < 1 ? 1
+                                     : (SPREAD_MINB_RAW > SPREAD_MINB_CAP ? SPREAD_MINB_CAP : SPREAD_MINB_RAW);
 };
 
 // l mod n for l in [-n, 2n)
@@ -254,7 +261,8 @@ __device__ __forceinline__ void flush_tile(const A *tr, const A *ti, int4 bo, co
 // [2^52, 2^53) for |a * b| < 2^51, where the spacing of doubles is 1, so its low mantissa bits
 // are a * b rounded to the nearest integer (the classic magic-number conversion) -- one
 // operation on the FP64 units, which bound the FP64 path, instead of a multiply and a convert.
-// FP32 3D forms the product in integers instead (see mulq31).
+// FP32 3D uses the same conversion in single precision where a contribution is within its
+// range (see fmaq and spread_f32_kernel).
 template <typename T> struct FixAcc;
 template <> struct FixAcc<float> {
     using A = int;
@@ -572,10 +580,39 @@ __device__ __forceinline__ V shfl_slot(const V (&v)[KV], int t) {
     return r;
 }
 
-// round(a b / 2^32) for |a| < 2^31 and 0 <= b < 2^31, as the high word of one 32 x 32 -> 64-bit
-// integer multiply-add (no float-to-integer conversion per stencil cell)
-__device__ __forceinline__ int mulq31(int a, int b) {
-    return (int)(((long long)a * (long long)b + 0x80000000LL) >> 32);
+// round(a b) for |a b| <= 2^22, by one fused multiply-add: a b + 1.5 * 2^23 lies in [2^23, 2^24],
+// where the spacing of floats is 1, so the sum is rounded once, to the nearest integer, and its
+// bit pattern minus that of 1.5 * 2^23 is that integer (the classic magic-number conversion in
+// single precision; no float-to-integer conversion instruction per stencil cell)
+__device__ __forceinline__ int fmaq(float a, float b) {
+    return __float_as_int(fmaf(a, b, 12582912.0f)) - 0x4B400000;
+}
+static constexpr float FMAQ_MAX = 4194304.0f;  // 2^22
+
+// Adds one stencil column of one node, or of two nodes with the same origin, into the
+// fixed-point tile along axis 0 (FAST: every weight within 2^22, contributions by fmaq; else by
+// the rounded product and a conversion).
+template <bool FAST>
+__device__ __forceinline__ int fix_contrib(float w, float k) {
+    if constexpr (FAST) return fmaq(w, k);
+    else return __float2int_rn(w * k);
+}
+template <bool FAST, int L, int PLANE>
+__device__ __forceinline__ void add_column(int *pr, int *pi, float wr, float wi, const float (&k)[L]) {
+#pragma unroll
+    for (int q0 = 0; q0 < L; q0++) {
+        atomicAdd(pr + q0 * PLANE, fix_contrib<FAST>(wr, k[q0]));
+        atomicAdd(pi + q0 * PLANE, fix_contrib<FAST>(wi, k[q0]));
+    }
+}
+template <bool FAST, int L, int PLANE>
+__device__ __forceinline__ void add_column2(int *pr, int *pi, float wr, float wi, const float (&k)[L],
+                                            float wr2, float wi2, const float (&k2)[L]) {
+#pragma unroll
+    for (int q0 = 0; q0 < L; q0++) {
+        atomicAdd(pr + q0 * PLANE, fix_contrib<FAST>(wr, k[q0]) + fix_contrib<FAST>(wr2, k2[q0]));
+        atomicAdd(pi + q0 * PLANE, fix_contrib<FAST>(wi, k[q0]) + fix_contrib<FAST>(wi2, k2[q0]));
+    }
 }
 
 // Sums four per-lane values over the warp with five shuffles (a transposed butterfly: the
@@ -951,10 +988,12 @@ __global__ void __launch_bounds__(SUB_THREADS) interp_grp_kernel(NodeDesc nd, co
     const float *__restrict__ Wv = reinterpret_cast<const float *>(nd.W);
     EAcc<float> eacc;
     const int half = lane >> 4, hl = lane & 15;
-    // each lane's next record and weight are loaded one half-group pair ahead
+    // each lane's next record and weight are loaded one half-group pair ahead, and the
+    // half-group bounds that locate them two pairs ahead, so that no record load waits on the
+    // load of its own bounds
     const int pend = gs.x + gs.y;
     int pr = gs.x + wid;
-    int first = 0, cnt = 0;
+    int first = 0, cnt = 0, first_n = 0, cnt_n = 0;
     int4 r_n = make_int4(0, 0, 0, 0);
     float W_n = 1.0f;
     if (pr < pend) {
@@ -965,18 +1004,26 @@ __global__ void __launch_bounds__(SUB_THREADS) interp_grp_kernel(NodeDesc nd, co
             if (apply_W) W_n = Wv[first + hl];
         }
     }
+    if (pr + NW < pend) {
+        first_n = nd.grp[2 * (pr + NW) + half];
+        cnt_n = nd.grp[2 * (pr + NW) + half + 1] - first_n;
+    }
     for (; pr < pend; pr += NW) {
         const int4 r = r_n;
         const float Wj = W_n;
         const int node = first + hl;
         const bool mine = hl < cnt;
-        if (pr + NW < pend) {
-            first = nd.grp[2 * (pr + NW) + half];
-            cnt = nd.grp[2 * (pr + NW) + half + 1] - first;
-            if (hl < cnt) {
-                r_n = nd.pos[first + hl];
-                if (apply_W) W_n = Wv[first + hl];
-            }
+        if (hl < cnt_n) {  // (cnt_n = 0 past the end)
+            r_n = nd.pos[first_n + hl];
+            if (apply_W) W_n = Wv[first_n + hl];
+        }
+        first = first_n;
+        cnt = cnt_n;
+        if (pr + 2 * NW < pend) {
+            first_n = nd.grp[2 * (pr + 2 * NW) + half];
+            cnt_n = nd.grp[2 * (pr + 2 * NW) + half + 1] - first_n;
+        } else {
+            cnt_n = 0;
         }
         if (mine) {
             float fz[W], fy[W], fx[W];
@@ -1014,13 +1061,18 @@ __global__ void __launch_bounds__(SUB_THREADS) interp_grp_kernel(NodeDesc nd, co
     }
 }
 
-// FP32 spreading.  In 3D each lane converts its column's weight c_j phi_1 phi_2 (times 2S) to
-// an integer once per pass, and each axis-0 value phi_0(q) to Q31 once per node; a cell's
-// contribution round(c_j phi_0 phi_1 phi_2 S) is then the high word of one integer
-// multiply-add (mulq31): about 0.75 of a fixed-point unit of rounding, as the FP32 product
-// rounded once, with no float-to-integer conversion per cell.
+// FP32 spreading.  In 3D each lane forms its column's weight w = c_j phi_1 phi_2 S once per pass
+// and a cell's contribution round(w phi_0(q)) by one fused multiply-add (fmaq): half a
+// fixed-point unit of rounding, one rounding of the exact product, and no float-to-integer
+// conversion per cell.  fmaq needs |w phi_0| <= 2^22, while S only bounds the cell sums (S B <=
+// 2^29): a node with S |Re c_j| or S |Im c_j| above 2^22 (one carrying more than about 1/128 of
+// its subproblem's sum B) takes the rounded product and a conversion instead (the choice is
+// per node, so the same for every lane of its warp: phi <= 1 bounds every column by S |c_j|).
+// Lowering S instead, so that every node fits fmaq's range, measured faster (0.94 vs 0.97 ms
+// at 256^3) but coarsened the small nodes of dominated subproblems: 3-5x the FP32 error on a
+// dipole case.
 template <int D, int W, int BS>
-__global__ void __launch_bounds__(SUB_THREADS) spread_f32_kernel(NodeDesc nd, const float2 *__restrict__ c_in,
+__global__ void __launch_bounds__(SUB_THREADS, (Geo<float, D, W, BS>::SPREAD_MINB)) spread_f32_kernel(NodeDesc nd, const float2 *__restrict__ c_in,
                                                                 float2 *__restrict__ H) {
     using G_ = Geo<float, D, W, BS>;
     using LN = F32Lane<D, W, BS>;
@@ -1039,8 +1091,7 @@ __global__ void __launch_bounds__(SUB_THREADS) spread_f32_kernel(NodeDesc nd, co
 
     const int ex = spread_scale<float, int, G_::NCELL, F::E, F::MAXEXP>(c_in, sb, tr, ti, red, H);
     if (ex == INT_MIN) return;
-    // 3D: weights carry 2S, so that mulq31 (a product over 2^32) lands on units of 1/S
-    const float S = ldexpf(1.0f, ex + (D == 3 ? 1 : 0));
+    const float S = ldexpf(1.0f, ex);
 
     int ja, jb;
     warp_chunk(sb, wid, ja, jb);
@@ -1076,50 +1127,40 @@ __global__ void __launch_bounds__(SUB_THREADS) spread_f32_kernel(NodeDesc nd, co
             float phA[KV], phB[KV];
             ln.values(pos, j, jb, rA, beta, phA);
             ln.values(pos, j + 1, jb, rB, beta, phB);
-            int qA[KV], qB[KV];
-#pragma unroll
-            for (int v = 0; v < KV; v++) {
-                qA[v] = __float2int_rn(phA[v] * 2147483648.0f);  // Q31 (saturates at 1)
-                qB[v] = __float2int_rn(phB[v] * 2147483648.0f);
-            }
-            int kA[L], kB[L];
+            float kA[L], kB[L];
 #pragma unroll
             for (int q = 0; q < L; q++) {
-                kA[q] = shfl_slot<KV>(qA, q);
-                kB[q] = shfl_slot<KV>(qB, q);
+                kA[q] = shfl_slot<KV>(phA, q);
+                kB[q] = shfl_slot<KV>(phB, q);
             }
             const int oA = origin_index<G_, D>(rA.x & 255, (rA.x >> 8) & 255, (rA.x >> 16) & 255);
             const int oB = origin_index<G_, D>(rB.x & 255, (rB.x >> 8) & 255, (rB.x >> 16) & 255);
             const bool same = hasB && rA.x == rB.x;  // the same for every lane
             const float sAr = cA.x * S, sAi = cA.y * S, sBr = cB.x * S, sBi = cB.y * S;
+            const bool fast = fmaxf(fmaxf(fabsf(sAr), fabsf(sAi)), fmaxf(fabsf(sBr), fabsf(sBi))) <= FMAQ_MAX;
 #pragma unroll
             for (int ps = 0; ps < PASSES; ps++) {
                 const float kabA = shfl_slot<KV>(phA, ln.sa[ps]) * shfl_slot<KV>(phA, ln.sb[ps]);
                 const float kabB = shfl_slot<KV>(phB, ln.sa[ps]) * shfl_slot<KV>(phB, ln.sb[ps]);
                 if (ln.coff[ps] >= 0) {
-                    const int wAr = __float2int_rn(sAr * kabA), wAi = __float2int_rn(sAi * kabA);
-                    const int wBr = __float2int_rn(sBr * kabB), wBi = __float2int_rn(sBi * kabB);
+                    const float wAr = sAr * kabA, wAi = sAi * kabA, wBr = sBr * kabB, wBi = sBi * kabB;
                     int *prA = tr + oA + ln.coff[ps], *piA = ti + oA + ln.coff[ps];
-                    if (same) {
-                        // |A + B| < 2^30: each contribution is below 2^29 (S B <= 2^29)
-#pragma unroll
-                        for (int q0 = 0; q0 < L; q0++) {
-                            F::add(prA + q0 * PLANE, mulq31(wAr, kA[q0]) + mulq31(wBr, kB[q0]));
-                            F::add(piA + q0 * PLANE, mulq31(wAi, kA[q0]) + mulq31(wBi, kB[q0]));
+                    int *prB = tr + oB + ln.coff[ps], *piB = ti + oB + ln.coff[ps];
+                    // a shared origin: the two contributions are added before one atomic (|A + B|
+                    // < 2^30, as each is below S B <= 2^29)
+                    if (fast) {
+                        if (same) {
+                            add_column2<true, L, PLANE>(prA, piA, wAr, wAi, kA, wBr, wBi, kB);
+                        } else {
+                            add_column<true, L, PLANE>(prA, piA, wAr, wAi, kA);
+                            if (hasB) add_column<true, L, PLANE>(prB, piB, wBr, wBi, kB);
                         }
                     } else {
-#pragma unroll
-                        for (int q0 = 0; q0 < L; q0++) {
-                            F::add(prA + q0 * PLANE, mulq31(wAr, kA[q0]));
-                            F::add(piA + q0 * PLANE, mulq31(wAi, kA[q0]));
-                        }
-                        if (hasB) {
-                            int *prB = tr + oB + ln.coff[ps], *piB = ti + oB + ln.coff[ps];
-#pragma unroll
-                            for (int q0 = 0; q0 < L; q0++) {
-                                F::add(prB + q0 * PLANE, mulq31(wBr, kB[q0]));
-                                F::add(piB + q0 * PLANE, mulq31(wBi, kB[q0]));
-                            }
+                        if (same) {
+                            add_column2<false, L, PLANE>(prA, piA, wAr, wAi, kA, wBr, wBi, kB);
+                        } else {
+                            add_column<false, L, PLANE>(prA, piA, wAr, wAi, kA);
+                            if (hasB) add_column<false, L, PLANE>(prB, piB, wBr, wBi, kB);
                         }
                     }
                 }
@@ -1153,31 +1194,28 @@ __global__ void __launch_bounds__(SUB_THREADS) spread_f32_kernel(NodeDesc nd, co
             me_nn = pos[j + 2 * NPW + half];
             c_nn = c_in[j + 2 * NPW + half];
         }
-        int k0i[L];
+        float k0[L];
         if constexpr (D == 3) {
-            int phq[KV];
 #pragma unroll
-            for (int v = 0; v < KV; v++) phq[v] = __float2int_rn(phv[v] * 2147483648.0f);  // saturates at 1
-#pragma unroll
-            for (int q = 0; q < L; q++) k0i[q] = shfl_slot<KV>(phq, half * DW + q);
+            for (int q = 0; q < L; q++) k0[q] = shfl_slot<KV>(phv, half * DW + q);
         }
         const float csr = c.x * S, csi = c.y * S;
+        const bool fast = fmaxf(fabsf(csr), fabsf(csi)) <= FMAQ_MAX;  // the same for the node's lanes
         const int obase = origin_index<G_, D>(me.x & 255, (me.x >> 8) & 255, (me.x >> 16) & 255);
 #pragma unroll
         for (int ps = 0; ps < PASSES; ps++) {
             const float kab = shfl_slot<KV>(phv, ln.sa[ps]) * shfl_slot<KV>(phv, ln.sb[ps]);
             if (act && ln.coff[ps] >= 0) {
-                const int cwr = __float2int_rn(csr * kab), cwi = __float2int_rn(csi * kab);
                 int *pr = tr + obase + ln.coff[ps], *pi = ti + obase + ln.coff[ps];
                 if constexpr (D == 3) {
-#pragma unroll
-                    for (int q0 = 0; q0 < L; q0++) {
-                        F::add(pr + q0 * PLANE, mulq31(cwr, k0i[q0]));
-                        F::add(pi + q0 * PLANE, mulq31(cwi, k0i[q0]));
-                    }
+                    const float cwr = csr * kab, cwi = csi * kab;
+                    if (fast)
+                        add_column<true, L, PLANE>(pr, pi, cwr, cwi, k0);
+                    else
+                        add_column<false, L, PLANE>(pr, pi, cwr, cwi, k0);
                 } else {
-                    F::add(pr, cwr);
-                    F::add(pi, cwi);
+                    F::add(pr, __float2int_rn(csr * kab));
+                    F::add(pi, __float2int_rn(csi * kab));
                 }
             }
         }

@@ -160,6 +160,25 @@ def test_type1_matches_direct_sums(pkg, prec, tol):
     assert rel_inf(got, ref) < tol
 
 
+def test_type1_dominant_nodes_match_direct_sums(pkg):
+    # a few nodes carry most of the weight (1e4 x the rest, 1e-3 of the nodes): their FP32
+    # contributions exceed the range of the fused-multiply-add rounding and take the
+    # conversion path, while the other nodes of the same subproblems stay on the fast one
+    d, n, L, nodes = 3, 24, 8.0, (10, 10, 20)
+    rng = np.random.default_rng(3)
+    k, W = quadrature.nodes_weights(d, n, L, nodes)
+    M = k.shape[0]
+    c = rng.standard_normal(M) + 1j * rng.standard_normal(M)
+    heavy = rng.choice(M, size=max(2, M // 1000), replace=False)
+    c[heavy] *= 1e4
+    for cc, tol in ((c, 1e-5), (np.where(np.isin(np.arange(M), heavy), 0, c), 1e-5)):
+        ref = direct.type1(cc, d, n, L, k).real
+        plan = pkg.Plan(d, n, L, nodes=nodes, precision="fp32", eps=1e-6, device=0)
+        got = plan.type1(torch.from_numpy(cc).to("cuda:0", torch.complex64)).double().cpu().numpy()
+        plan.close()
+        assert rel_inf(got, ref) < tol
+
+
 def test_energy_entry_point_and_host_path(pkg):
     wl = synth.config1()
     rho = wl.rho()
