@@ -426,25 +426,23 @@ def run_reference(args, rank, world):
 
 # ----------------------------------------------------------------------------- batched form
 def tuned_member_params(pkg, members, precision, dev):
-    """Autotuned parameters for each member of the batch: one tuning per (grid size, kernel)
-    class (width for the tolerance, bin shape, subproblem size), measured on the class's first
-    member and applied to every member of the class with its own dipole axis."""
+    """Autotuned parameters for every member of the batch (nlint_autotune_batch): one tuning per
+    (grid size, kernel) class (width for the tolerance, bin shape, subproblem size), then the
+    whole batch timed with the classes' own fastest decompositions and with the default one, the
+    faster kept.  Returns the member parameters (each with its own dipole axis) and the report."""
     tol = TOL if precision == "fp32" else 1e-10
     cache = os.environ.get("NLINT_TUNE_CACHE")
-    by_class, reports, out = {}, {}, []
-    for m in members:
-        cls = (m.n, m.kernel)
-        if cls not in by_class:
-            prm = pkg.make_params(3, m.n, m.L, m.kernel, axis=m.axis, nodes=m.nodes,
-                                  precision=precision, device=dev.index)
-            tuned, rep = pkg.autotune(prm, tol, cache)
-            by_class[cls] = tuned
-            reports[f"{m.n}^3 {m.kernel}"] = {k: rep[k] for k in ("w", "bin_shape", "max_sub", "err")}
-        t = by_class[cls]
-        out.append(pkg.make_params(3, m.n, m.L, m.kernel, axis=m.axis, nodes=m.nodes,
-                                   precision=precision, w=t.w, max_sub=t.max_sub,
-                                   bin_shape=t.bin_shape, device=dev.index))
-    return out, reports
+    prm = [pkg.make_params(3, m.n, m.L, m.kernel, axis=m.axis, nodes=m.nodes, precision=precision,
+                           device=dev.index) for m in members]
+    out, reps, brep = pkg.autotune_batch(prm, tol, cache)
+    classes = {}
+    for m, r in zip(members, reps):
+        classes.setdefault(f"{m.n}^3 {m.kernel}", {k: r[k] for k in ("w", "bin_shape", "max_sub", "err",
+                                                                       "w_alt", "err_alt")})
+    kinds = ("each class's own fastest decomposition and width", "the default decomposition",
+             "the default decomposition at each class's other width")
+    batch = {"kept": kinds[brep["choice"]], "ms": {k: t for k, t in zip(kinds, brep["ms"]) if t > 0}}
+    return out, {"classes": classes, "batch": batch}
 
 
 def run_batched(pkg, torch, dev, precision, reps, flush, stream, loop_too=False, tune=False):
@@ -460,7 +458,7 @@ def run_batched(pkg, torch, dev, precision, reps, flush, stream, loop_too=False,
     if tune:
         t0 = time.perf_counter()
         prms, tune_rep = tuned_member_params(pkg, members, precision, dev)
-        tune_rep = {"classes": tune_rep, "seconds": time.perf_counter() - t0}
+        tune_rep["seconds"] = time.perf_counter() - t0
         plans = [pkg.Plan(3, m.n, m.L, params=q, device=dev.index) for m, q in zip(members, prms)]
     else:
         plans = [pkg.Plan(3, m.n, m.L, m.kernel, axis=m.axis, nodes=m.nodes, precision=precision,

@@ -222,10 +222,10 @@ int nlint_stage_times(nlint_plan plan, float *ms, const char **names, int max_st
 /* Autotuner.  For the plan described by *in and a target relative L-inf error `tol` of u,
  * picks (1) the smallest spreading width w whose error, measured on the device against an FP64
  * plan with the widest stencil (same grid, nodes, cutoff and kernel) on a seeded probe
- * density with content up to the grid's Nyquist radius, is at most tol/2, (2) at that width
- * the fastest bin shape among those compiled for the precision and dimension whose tile fits
- * in shared memory (evaluation time by CUDA events), and (3) for that shape the fastest
- * subproblem size (max_sub) among 256..2048.  *out = *in with w, bin_shape, max_sub and the
+ * density with content up to the grid's Nyquist radius, is at most tol/2, (2) of that width and
+ * the next one the fastest, each with its fastest bin shape among those compiled for the
+ * precision and dimension whose tile fits in shared memory (evaluation time by CUDA events),
+ * and (3) for that width and shape the fastest subproblem size (max_sub) among 256..2048.  *out = *in with w, bin_shape, max_sub and the
  * precision (from tol when in->precision is -1) filled in; rep (may be NULL) reports the
  * choice, its measured error and time.  The choice is cached as one JSON object per line in
  * cache_path (NULL: $NLINT_TUNE_CACHE; neither: no cache); a cached key skips measurement.
@@ -236,9 +236,39 @@ typedef struct nlint_tune_report {
     double ms;       /* median evaluation time of the choice                           */
     int from_cache;  /* 1: read from the cache, nothing measured                      */
     int bin_shape;   /* chosen bin shape (nlint_params.bin_shape)                      */
+    int w_alt;       /* the other width timed in (2), also within tol/2 (0: none)      */
+    double err_alt;  /* its measured error                                             */
 } nlint_tune_report;
 int nlint_autotune(const nlint_params *in, double tol, const char *cache_path, nlint_params *out,
                    nlint_tune_report *rep);
+
+/* Batch autotuner, for `count` densities evaluated together by nlint_batch_*: members with the
+ * same geometry, kernel and precision form a class (dipoles of any orientation share one: the
+ * width's error does not depend on it), each class is tuned once by nlint_autotune on its first
+ * member (its width for `tol`, and its own fastest bin shape and subproblem size when evaluated alone),
+ * and the whole batch graph (nlint_batch_create with `branches`, on each member's probe density)
+ * is then timed with three parameter sets: (0) every class at its own fastest decomposition and
+ * width, (1) every class at the default decomposition (bin_shape 0, max_sub 0) and its tuned
+ * width, (2) the default decomposition at each class's other timed width (w_alt, also within
+ * the tolerance).  Evaluated alone a small grid gains from many small subproblems (and a width
+ * from its lane layout), but in a batch the GPU is already filled by the other members and those
+ * extra CTAs only add tile work, so the batch keeps whichever set measured fastest.
+ * out[i] = in[i] with w, bin_shape, max_sub and precision filled in; member_reps (may be NULL)
+ * holds count per-member reports of the chosen parameters (err from the class tuning, ms the
+ * class's own time); rep (may be NULL) the batch choice and both times.  The class tunings use
+ * the cache as nlint_autotune does; the batch timing is not cached.  Synchronous; creates and
+ * destroys plans, a batch and count density/potential buffers on in[0]'s device.  Errors:
+ * NLINT_EINVAL (count < 1, NULL in/out, members on different devices), and those of
+ * nlint_autotune, nlint_plan_create_ex and nlint_batch_create. */
+typedef struct nlint_batch_tune_report {
+    int choice;     /* 0, 1 or 2: the parameter set kept (see above)                     */
+    int classes;    /* distinct (geometry, kernel, precision) classes tuned              */
+    double ms[3];   /* median batch evaluation time of each set (ms; 0: not timed, when  */
+                    /* no class has another width, set 2 equals set 1)                   */
+} nlint_batch_tune_report;
+int nlint_autotune_batch(int count, const nlint_params *in, double tol, const char *cache_path,
+                         int branches, nlint_params *out, nlint_tune_report *member_reps,
+                         nlint_batch_tune_report *rep);
 
 /* Batched evaluation of independent densities (Algorithm 1 applied to each), e.g. grids of
  * mixed sizes, kernels and precisions.  A plan whose Toeplitz kernel has been precomputed

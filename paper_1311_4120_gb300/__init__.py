@@ -32,6 +32,7 @@ EXPORTED = [
     "nlint_type2", "nlint_type1", "nlint_plan_nodes", "nlint_set_stage_timing",
     "nlint_stage_times", "nlint_launch_count", "nlint_energy_noalloc", "nlint_batch_create",
     "nlint_batch_eval", "nlint_batch_info", "nlint_batch_destroy", "nlint_autotune",
+    "nlint_autotune_batch",
     "nlint_energy_only", "nlint_plan_toeplitz", "nlint_eval_toeplitz", "nlint_last_error",
 ]
 
@@ -57,7 +58,12 @@ class nlint_params(ctypes.Structure):
 
 class nlint_tune_report(ctypes.Structure):
     _fields_ = [("w", ctypes.c_int), ("max_sub", ctypes.c_int), ("err", ctypes.c_double),
-                ("ms", ctypes.c_double), ("from_cache", ctypes.c_int), ("bin_shape", ctypes.c_int)]
+                ("ms", ctypes.c_double), ("from_cache", ctypes.c_int), ("bin_shape", ctypes.c_int),
+                ("w_alt", ctypes.c_int), ("err_alt", ctypes.c_double)]
+
+
+class nlint_batch_tune_report(ctypes.Structure):
+    _fields_ = [("choice", ctypes.c_int), ("classes", ctypes.c_int), ("ms", ctypes.c_double * 3)]
 
 
 class nlint_info(ctypes.Structure):
@@ -118,6 +124,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.nlint_batch_destroy.restype = None
     lib.nlint_autotune.argtypes = [ctypes.POINTER(nlint_params), dbl, ctypes.c_char_p,
                                    ctypes.POINTER(nlint_params), ctypes.POINTER(nlint_tune_report)]
+    lib.nlint_autotune_batch.argtypes = [ci, ctypes.POINTER(nlint_params), dbl, ctypes.c_char_p, ci,
+                                         ctypes.POINTER(nlint_params),
+                                         ctypes.POINTER(nlint_tune_report),
+                                         ctypes.POINTER(nlint_batch_tune_report)]
     lib.nlint_energy_only.argtypes = [vp, vp, dbl, vp, ctypes.POINTER(dbl), vp]
     lib.nlint_plan_toeplitz.argtypes = [vp, vp]
     lib.nlint_eval_toeplitz.argtypes = [vp, vp, vp, dbl, vp, vp]
@@ -189,6 +199,24 @@ def autotune(params: nlint_params, tol: float, cache_path: Optional[str] = None)
                               cache_path.encode() if cache_path else None, ctypes.byref(out),
                               ctypes.byref(rep)))
     return out, {f: getattr(rep, f) for f, _ in nlint_tune_report._fields_}
+
+
+def autotune_batch(params: Sequence[nlint_params], tol: float, cache_path: Optional[str] = None,
+                   branches: int = 0):
+    """Tuned copies of the batch members' ``params`` (nlint_autotune_batch): per-member reports
+    and the batch report (which decomposition was kept, both measured batch times)."""
+    lib = load_library()
+    count = len(params)
+    arr = (nlint_params * count)(*params)
+    out = (nlint_params * count)()
+    reps = (nlint_tune_report * count)()
+    brep = nlint_batch_tune_report()
+    _check(lib.nlint_autotune_batch(count, arr, float(tol),
+                                    cache_path.encode() if cache_path else None, int(branches),
+                                    out, reps, ctypes.byref(brep)))
+    members = [{f: getattr(r, f) for f, _ in nlint_tune_report._fields_} for r in reps]
+    batch = {"choice": brep.choice, "classes": brep.classes, "ms": list(brep.ms)}
+    return list(out), members, batch
 
 
 class Plan:

@@ -89,7 +89,19 @@ def test_null_arguments(lib):
     assert lib.nlint_plan_info(None, None) == -1
     assert lib.nlint_plan_check(None) == -1
     assert lib.nlint_eval_host_many(None, 2, None, None, 1.0, None, None) == -1
+    assert lib.nlint_autotune_batch(0, None, 1e-5, None, 0, None, None, None) == -1
     lib.nlint_plan_destroy(None)  # no-op
+
+
+def test_batch_autotune_rejects_mixed_devices(lib):
+    import paper_1311_4120_gb300 as pkg
+    arr = (pkg.nlint_params * 2)()
+    for i in range(2):
+        lib.nlint_params_default(ctypes.byref(arr[i]))
+        arr[i].n, arr[i].device = 32, i
+    out = (pkg.nlint_params * 2)()
+    assert lib.nlint_autotune_batch(2, arr, 1e-5, None, 0, out, None, None) == -1
+    assert "different devices" in lib.nlint_last_error().decode()
 
 
 def test_params_default(lib):
