@@ -438,7 +438,7 @@ def tuned_member_params(pkg, members, precision, dev):
     classes = {}
     for m, r in zip(members, reps):
         classes.setdefault(f"{m.n}^3 {m.kernel}", {k: r[k] for k in ("w", "bin_shape", "max_sub", "err",
-                                                                       "w_alt", "err_alt")})
+                                                                       "w_alt", "err_alt", "fft_sched")})
     kinds = ("each class's own fastest decomposition and width", "the default decomposition",
              "the default decomposition at each class's other width")
     batch = {"kept": kinds[brep["choice"]], "ms": {k: t for k, t in zip(kinds, brep["ms"]) if t > 0}}
@@ -743,7 +743,8 @@ def run_ours(args, rank, world, local_rank):
                                "160x160x320 spherical nodes, FP32 path (FP64 nodes/weights, "
                                "compensated FP64 energy)",
                    "w": info["w"], "sigma": info["sigma"], "n_fine": info["n_fine"],
-                   "max_sub": tuned.max_sub, "bin_shape": tuned.bin_shape, "tolerance": TOL,
+                   "max_sub": tuned.max_sub, "bin_shape": tuned.bin_shape,
+                   "fft_sched": tuned.fft_sched, "tolerance": TOL,
                    "autotune": tune_rep,
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single"},

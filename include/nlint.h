@@ -96,6 +96,11 @@ typedef struct nlint_params {
      * 16x16.  A shape whose tile does not fit in shared memory at the plan's width is
      * NLINT_EUNSUPPORTED (automatic: the smallest shape is taken instead).                  */
     int bin_shape;
+    /* FFT pass schedules (FP32 plans; ignored in FP64): bit set = the second values-per-thread
+     * choice (and with it threads per line and lines per CTA) for, bit 0: the column passes,
+     * 1: the row passes, 2: the first inverse row pass (fold), 3: the real-data column passes
+     * along the slowest axis; lines of 3 * 2^a points have one schedule.  0..15; 0 = default. */
+    int fft_sched;
 } nlint_params;
 
 /* Read-only description of a plan. */
@@ -114,6 +119,7 @@ typedef struct nlint_info {
     double pu_a, pu_r0, pu_r1, P2; /* Algorithm 2's partition parameters (0 if unused)  */
     int toeplitz;           /* 1 once nlint_plan_toeplitz has precomputed K_hat          */
     int bin_shape;          /* the bin shape in use (see nlint_params.bin_shape)         */
+    int fft_sched;          /* the FFT pass schedules in use (nlint_params.fft_sched)    */
 } nlint_info;
 
 /* Fill *p with defaults (d = 3, Coulomb, eps = 1e-6, everything else automatic). */
@@ -225,7 +231,9 @@ int nlint_stage_times(nlint_plan plan, float *ms, const char **names, int max_st
  * density with content up to the grid's Nyquist radius, is at most tol/2, (2) of that width and
  * the next one the fastest, each with its fastest bin shape among those compiled for the
  * precision and dimension whose tile fits in shared memory (evaluation time by CUDA events),
- * and (3) for that width and shape the fastest subproblem size (max_sub) among 256..2048.  *out = *in with w, bin_shape, max_sub and the
+ * (3) for that width and shape the fastest subproblem size (max_sub) among 256..2048, and (4)
+ * for FP32 plans the FFT pass schedules (nlint_params.fft_sched), one pass class at a time,
+ * each kept when it measured faster.  *out = *in with w, bin_shape, max_sub, fft_sched and the
  * precision (from tol when in->precision is -1) filled in; rep (may be NULL) reports the
  * choice, its measured error and time.  The choice is cached as one JSON object per line in
  * cache_path (NULL: $NLINT_TUNE_CACHE; neither: no cache); a cached key skips measurement.
@@ -238,6 +246,7 @@ typedef struct nlint_tune_report {
     int bin_shape;   /* chosen bin shape (nlint_params.bin_shape)                      */
     int w_alt;       /* the other width timed in (2), also within tol/2 (0: none)      */
     double err_alt;  /* its measured error                                             */
+    int fft_sched;   /* chosen FFT pass schedules (nlint_params.fft_sched), step (4)    */
 } nlint_tune_report;
 int nlint_autotune(const nlint_params *in, double tol, const char *cache_path, nlint_params *out,
                    nlint_tune_report *rep);

@@ -53,13 +53,13 @@ class nlint_params(ctypes.Structure):
                 ("max_sub", ctypes.c_int), ("crowd_min", ctypes.c_int),
                 ("algorithm", ctypes.c_int), ("pu_a", ctypes.c_double),
                 ("pu_r0", ctypes.c_double), ("pu_r1", ctypes.c_double), ("P2", ctypes.c_double),
-                ("bin_shape", ctypes.c_int)]
+                ("bin_shape", ctypes.c_int), ("fft_sched", ctypes.c_int)]
 
 
 class nlint_tune_report(ctypes.Structure):
     _fields_ = [("w", ctypes.c_int), ("max_sub", ctypes.c_int), ("err", ctypes.c_double),
                 ("ms", ctypes.c_double), ("from_cache", ctypes.c_int), ("bin_shape", ctypes.c_int),
-                ("w_alt", ctypes.c_int), ("err_alt", ctypes.c_double)]
+                ("w_alt", ctypes.c_int), ("err_alt", ctypes.c_double), ("fft_sched", ctypes.c_int)]
 
 
 class nlint_batch_tune_report(ctypes.Structure):
@@ -78,7 +78,7 @@ class nlint_info(ctypes.Structure):
                 ("bin", ctypes.c_int * 3), ("device", ctypes.c_int),
                 ("algorithm", ctypes.c_int), ("pu_a", ctypes.c_double),
                 ("pu_r0", ctypes.c_double), ("pu_r1", ctypes.c_double), ("P2", ctypes.c_double),
-                ("toeplitz", ctypes.c_int), ("bin_shape", ctypes.c_int)]
+                ("toeplitz", ctypes.c_int), ("bin_shape", ctypes.c_int), ("fft_sched", ctypes.c_int)]
 
 
 _lib = None
@@ -164,7 +164,7 @@ def make_params(d: int, n: int, L: float, kernel: str = "coulomb", axis=None, ax
                 w: int = 0, sigma: float = 0.0, P: float = 0.0, device: int = -1,
                 max_sub: int = 0, crowd_min: int = 0, algorithm: int = 1, pu_a: float = 0.0,
                 pu_r0: float = 0.0, pu_r1: float = 0.0, P2: float = 0.0,
-                bin_shape: int = 0) -> nlint_params:
+                bin_shape: int = 0, fft_sched: int = 0) -> nlint_params:
     """A filled nlint_params (the C-ABI's complete parameter set)."""
     lib = load_library()
     prm = nlint_params()
@@ -187,6 +187,7 @@ def make_params(d: int, n: int, L: float, kernel: str = "coulomb", axis=None, ax
     prm.algorithm, prm.pu_a, prm.pu_r0, prm.pu_r1, prm.P2 = (int(algorithm), float(pu_a),
                                                              float(pu_r0), float(pu_r1), float(P2))
     prm.bin_shape = int(bin_shape)
+    prm.fft_sched = int(fft_sched)
     return prm
 
 
@@ -238,7 +239,8 @@ class Plan:
                  axis2: Optional[Sequence[float]] = None, alpha: float = 0.0,
                  max_sub: int = 0, crowd_min: int = 0, algorithm: int = 1, pu_a: float = 0.0,
                  pu_r0: float = 0.0, pu_r1: float = 0.0, P2: float = 0.0,
-                 bin_shape: int = 0, params: Optional["nlint_params"] = None):
+                 bin_shape: int = 0, fft_sched: int = 0,
+                 params: Optional["nlint_params"] = None):
         lib = load_library()
         prm = nlint_params()
         lib.nlint_params_default(ctypes.byref(prm))
@@ -267,6 +269,7 @@ class Plan:
         prm.algorithm, prm.pu_a, prm.pu_r0, prm.pu_r1, prm.P2 = (
             int(algorithm), float(pu_a), float(pu_r0), float(pu_r1), float(P2))
         prm.bin_shape = int(bin_shape)
+        prm.fft_sched = int(fft_sched)
         if params is not None:  # a complete parameter set, e.g. from autotune()
             prm = params
             prm.device = int(device)

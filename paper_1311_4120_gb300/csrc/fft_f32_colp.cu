@@ -3,8 +3,8 @@
 #include "fft_kernels.cuh"
 
 namespace nlint {
-template cudaError_t launch_pass_mode<float, 3>(const PassDesc &, const void *, void *, const void *,
-                                            cudaStream_t);
-template cudaError_t launch_pass_mode<float, 4>(const PassDesc &, const void *, void *, const void *,
-                                            cudaStream_t);
+template cudaError_t launch_pass_mode_v<float, 3, 0>(const PassDesc &, const void *, void *,
+                                                 const void *, cudaStream_t);
+template cudaError_t launch_pass_mode_v<float, 4, 0>(const PassDesc &, const void *, void *,
+                                                 const void *, cudaStream_t);
 }  // namespace nlint

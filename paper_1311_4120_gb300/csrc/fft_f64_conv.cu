@@ -3,6 +3,6 @@
 #include "fft_kernels.cuh"
 
 namespace nlint {
-template cudaError_t launch_pass_mode<double, 5>(const PassDesc &, const void *, void *, const void *,
-                                            cudaStream_t);
+template cudaError_t launch_pass_mode_v<double, 5, 0>(const PassDesc &, const void *, void *,
+                                                 const void *, cudaStream_t);
 }  // namespace nlint

@@ -3,8 +3,8 @@
 #include "fft_kernels.cuh"
 
 namespace nlint {
-template cudaError_t launch_pass_mode<double, 6>(const PassDesc &, const void *, void *, const void *,
-                                            cudaStream_t);
-template cudaError_t launch_pass_mode<double, 7>(const PassDesc &, const void *, void *, const void *,
-                                            cudaStream_t);
+template cudaError_t launch_pass_mode_v<double, 6, 0>(const PassDesc &, const void *, void *,
+                                                 const void *, cudaStream_t);
+template cudaError_t launch_pass_mode_v<double, 7, 0>(const PassDesc &, const void *, void *,
+                                                 const void *, cudaStream_t);
 }  // namespace nlint

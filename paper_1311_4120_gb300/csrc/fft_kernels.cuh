@@ -54,11 +54,21 @@ __host__ __device__ constexpr int fft_vpt_small(int mode) {
     return mode == 0 ? FFT_VPT0 : mode == 1 ? FFT_VPT1 : mode == 2 ? 8
          : (mode == 3 || mode == 4) ? FFT_PACKED_VPT : (mode == 6 || mode == 7) ? FFT_DUAL_VPT : 16;
 }
-__host__ __device__ constexpr int fft_vpt(int n, int mode = 0) {
-    return fft_has3(n) ? 24 : (n <= 512 ? fft_vpt_small(mode) : 32);
+// Schedule variants: a plan picks, per pass class (nlint_params.fft_sched, searched by the
+// autotuner), schedule 0 above or schedule 1, the other values-per-thread choice of 2^a lines
+// (column and row passes 8 instead of 16, the fold and packed passes 16 instead of 8, lines
+// longer than 512 16 instead of 32) and with it the threads per line and lines per CTA.
+// 3 * 2^a lines and modes 5-7 have one schedule.
+__host__ __device__ constexpr bool fft_has_alt(int n, int mode) { return !fft_has3(n) && mode <= 4; }
+__host__ __device__ constexpr int fft_vpt_alt(int n, int mode) {
+    return n > 512 ? 16 : ((mode == 0 || mode == 1) ? 8 : 16);
+}
+__host__ __device__ constexpr int fft_vpt(int n, int mode = 0, int v = 0) {
+    return (v && fft_has_alt(n, mode)) ? fft_vpt_alt(n, mode)
+                                       : (fft_has3(n) ? 24 : (n <= 512 ? fft_vpt_small(mode) : 32));
 }
 __host__ __device__ constexpr int fft_vpt_ref(int n) { return fft_has3(n) ? 24 : (n <= 512 ? 16 : 32); }
-__host__ __device__ constexpr int fft_tpl(int n, int mode = 0) { return n / fft_vpt(n, mode); }  // 2^k
+__host__ __device__ constexpr int fft_tpl(int n, int mode = 0, int v = 0) { return n / fft_vpt(n, mode, v); }  // 2^k
 __host__ __device__ constexpr int fft_row_ld(int n) { return n + n / 16; }  // padded row line
 // Lines per CTA.  Column pass: 128-byte rows (16 FP32 / 8 FP64 complex), fewer for the
 // longest lines (shared memory <= 192 KB), at least one warp.
@@ -71,22 +81,22 @@ __host__ __device__ constexpr int fft_col_b(int n, int cs) {  // at the referenc
     return fft_col_b_raw(n, cs) * (n / fft_vpt_ref(n)) >= 32 ? fft_col_b_raw(n, cs) : 32 / (n / fft_vpt_ref(n));
 }
 // per mode: column passes with half the values per thread take half the lines per CTA
-__host__ __device__ constexpr int fft_col_b_m(int n, int cs, int mode) {
-    return (fft_vpt(n, mode) * 2 == fft_vpt_ref(n) && fft_col_b(n, cs) >= 2) ? fft_col_b(n, cs) / 2
-                                                                             : fft_col_b(n, cs);
+__host__ __device__ constexpr int fft_col_b_m(int n, int cs, int mode, int v = 0) {
+    return (fft_vpt(n, mode, v) * 2 == fft_vpt_ref(n) && fft_col_b(n, cs) >= 2) ? fft_col_b(n, cs) / 2
+                                                                                : fft_col_b(n, cs);
 }
 // Row pass: about 256 threads (mode 1) or 512 threads (mode 2) per CTA.
 __host__ __device__ constexpr int fft_row_thr(int mode) { return mode == 2 ? 512 : 256; }
-__host__ __device__ constexpr int fft_row_b_raw(int n, int cs, int mode) {
-    return (fft_row_thr(mode) / fft_tpl(n, mode)) < (96 * 1024) / (fft_row_ld(n) * cs)
-               ? fft_row_thr(mode) / fft_tpl(n, mode)
+__host__ __device__ constexpr int fft_row_b_raw(int n, int cs, int mode, int v = 0) {
+    return (fft_row_thr(mode) / fft_tpl(n, mode, v)) < (96 * 1024) / (fft_row_ld(n) * cs)
+               ? fft_row_thr(mode) / fft_tpl(n, mode, v)
                : (96 * 1024) / (fft_row_ld(n) * cs);
 }
-__host__ __device__ constexpr int fft_row_b(int n, int cs, int mode = 1) {
-    return fft_row_b_raw(n, cs, mode) < 1 ? 1
-         : (fft_tpl(n, mode) < 32 && fft_row_b_raw(n, cs, mode) >= 32 / fft_tpl(n, mode))
-               ? fft_row_b_raw(n, cs, mode) / (32 / fft_tpl(n, mode)) * (32 / fft_tpl(n, mode))
-               : fft_row_b_raw(n, cs, mode);
+__host__ __device__ constexpr int fft_row_b(int n, int cs, int mode = 1, int v = 0) {
+    return fft_row_b_raw(n, cs, mode, v) < 1 ? 1
+         : (fft_tpl(n, mode, v) < 32 && fft_row_b_raw(n, cs, mode, v) >= 32 / fft_tpl(n, mode, v))
+               ? fft_row_b_raw(n, cs, mode, v) / (32 / fft_tpl(n, mode, v)) * (32 / fft_tpl(n, mode, v))
+               : fft_row_b_raw(n, cs, mode, v);
 }
 
 // Modes 3 and 4 are column passes that carry two real lines per complex FFT line: mode 3
@@ -121,21 +131,21 @@ __host__ __device__ constexpr unsigned fft_out_mask(int mode) {
                      : (1u << OUT_CPLX_MODES);  // 2, 5
 }
 
-template <typename T, int NF, int MODE>
+template <typename T, int NF, int MODE, int V = 0>
 struct FftCfg {
     static constexpr int CS = (int)(2 * sizeof(T));
-    static constexpr int TPL = fft_tpl(NF, MODE);  // threads per line
+    static constexpr int TPL = fft_tpl(NF, MODE, V);  // threads per line
     static constexpr int NST = fft_nstages(NF);
-    static constexpr int B = fft_is_row(MODE) ? fft_row_b(NF, CS, MODE) : fft_col_b_m(NF, CS, MODE);  // lines
+    static constexpr int B = fft_is_row(MODE) ? fft_row_b(NF, CS, MODE, V) : fft_col_b_m(NF, CS, MODE, V);  // lines
     static constexpr int ROW_LD = fft_row_ld(NF);
     static constexpr int THREADS = B * TPL;
     // packed passes hold two lines' loads in flight: ask for two resident CTAs of 512 threads
-    static constexpr bool F32_512 = THREADS == 512 && NF <= 512 && sizeof(T) == 4;
+    static constexpr bool F32_512 = THREADS == 512 && NF <= 512 && sizeof(T) == 4 && V == 0;
     static constexpr int MIN_BLOCKS = (fft_packed(MODE) && F32_512) ? FFT_PACKED_MINB
                                     : (fft_dual(MODE) && F32_512) ? FFT_DUAL_MINB
                                     : (MODE == 0 && F32_512) ? FFT_MINB0
                                     : (MODE == 1 && F32_512) ? FFT_MINB1
-                                    : (MODE == 5 && NF <= 512 && sizeof(T) == 4) ? 3 : 0;
+                                    : (MODE == 5 && NF <= 512 && sizeof(T) == 4 && V == 0) ? 3 : 0;
 };
 
 // ------------------------------------------------------------------ butterflies
@@ -238,11 +248,11 @@ struct LineIO {
 // MODE 1, 2: row pass, each line is contiguous (B lines per CTA);
 // MODE 3, 4: column pass with two data columns per FFT line (2B adjacent columns per CTA);
 // MODE 6, 7: column pass with two transforms of one data column per FFT line (B columns).
-template <typename T, int NF, int MODE>
-__global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MODE>::MIN_BLOCKS) fft_pass_kernel(
+template <typename T, int NF, int MODE, int V>
+__global__ void __launch_bounds__(FftCfg<T, NF, MODE, V>::THREADS, FftCfg<T, NF, MODE, V>::MIN_BLOCKS) fft_pass_kernel(
     PassDesc P, const void *__restrict__ vin, void *__restrict__ vout, const cx_t<T> *__restrict__ tw) {
     using T2 = cx_t<T>;
-    using C = FftCfg<T, NF, MODE>;
+    using C = FftCfg<T, NF, MODE, V>;
     constexpr bool ROW = fft_is_row(MODE);
     constexpr bool PACK = fft_packed(MODE);
     constexpr bool DUAL = fft_dual(MODE);
@@ -592,41 +602,51 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE>::THREADS, FftCfg<T, NF, MO
 }
 
 // ------------------------------------------------------------------ launchers
-template <typename T, int NF, int MODE>
+template <typename T, int NF, int MODE, int V>
 cudaError_t launch_nf(const PassDesc &p, const void *in, void *out, const void *tw, cudaStream_t s) {
     if (!(fft_in_mask(MODE) & (1u << p.in_kind)) || !(fft_out_mask(MODE) & (1u << p.out_kind)))
         return cudaErrorInvalidValue;  // a pass descriptor this mode was not compiled for
     if (fft_dual(MODE) && (!p.fac2 || (MODE == 6 ? !p.out2 : !p.in2) || p.win <= 0 || p.win > NF / 2))
         return cudaErrorInvalidValue;  // a dual pass needs its second factors, buffer and window
+    if (p.TPC != FftCfg<T, NF, MODE, V>::TPL || p.B != FftCfg<T, NF, MODE, V>::B)
+        return cudaErrorInvalidValue;  // the descriptor was configured for another schedule
     const size_t smem = pass_smem(p, sizeof(T) == 4 ? NLINT_FP32 : NLINT_FP64);
-    cudaError_t e = cudaFuncSetAttribute(fft_pass_kernel<T, NF, MODE>,
+    cudaError_t e = cudaFuncSetAttribute(fft_pass_kernel<T, NF, MODE, V>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t nb = pass_blocks(p, fft_is_row(MODE));
     if (nb == 0) return cudaSuccess;
-    fft_pass_kernel<T, NF, MODE><<<(unsigned)nb, FftCfg<T, NF, MODE>::THREADS, smem, s>>>(
+    fft_pass_kernel<T, NF, MODE, V><<<(unsigned)nb, FftCfg<T, NF, MODE, V>::THREADS, smem, s>>>(
         p, in, out, reinterpret_cast<const cx_t<T> *>(tw));
     return cudaGetLastError();
 }
 
-template <typename T, int MODE>
-cudaError_t launch_pass_mode(const PassDesc &p, const void *in, void *out, const void *tw, cudaStream_t s) {
+// Schedule V of every supported length; for V = 1 a length without a second schedule runs
+// schedule 0 (launch_pass_mode_v<T, MODE, 0>, instantiated in its own translation unit).
+template <typename T, int NF, int MODE, int V>
+cudaError_t launch_nf_v(const PassDesc &p, const void *in, void *out, const void *tw, cudaStream_t s) {
+    if constexpr (V == 1 && !fft_has_alt(NF, MODE)) return launch_pass_mode_v<T, MODE, 0>(p, in, out, tw, s);
+    else return launch_nf<T, NF, MODE, V>(p, in, out, tw, s);
+}
+
+template <typename T, int MODE, int V>
+cudaError_t launch_pass_mode_v(const PassDesc &p, const void *in, void *out, const void *tw, cudaStream_t s) {
     switch (p.n) {
-        case 16: return launch_nf<T, 16, MODE>(p, in, out, tw, s);
-        case 24: return launch_nf<T, 24, MODE>(p, in, out, tw, s);
-        case 32: return launch_nf<T, 32, MODE>(p, in, out, tw, s);
-        case 48: return launch_nf<T, 48, MODE>(p, in, out, tw, s);
-        case 64: return launch_nf<T, 64, MODE>(p, in, out, tw, s);
-        case 96: return launch_nf<T, 96, MODE>(p, in, out, tw, s);
-        case 128: return launch_nf<T, 128, MODE>(p, in, out, tw, s);
-        case 192: return launch_nf<T, 192, MODE>(p, in, out, tw, s);
-        case 256: return launch_nf<T, 256, MODE>(p, in, out, tw, s);
-        case 384: return launch_nf<T, 384, MODE>(p, in, out, tw, s);
-        case 512: return launch_nf<T, 512, MODE>(p, in, out, tw, s);
-        case 768: return launch_nf<T, 768, MODE>(p, in, out, tw, s);
-        case 1024: return launch_nf<T, 1024, MODE>(p, in, out, tw, s);
-        case 1536: return launch_nf<T, 1536, MODE>(p, in, out, tw, s);
-        case 2048: return launch_nf<T, 2048, MODE>(p, in, out, tw, s);
+        case 16: return launch_nf_v<T, 16, MODE, V>(p, in, out, tw, s);
+        case 24: return launch_nf_v<T, 24, MODE, V>(p, in, out, tw, s);
+        case 32: return launch_nf_v<T, 32, MODE, V>(p, in, out, tw, s);
+        case 48: return launch_nf_v<T, 48, MODE, V>(p, in, out, tw, s);
+        case 64: return launch_nf_v<T, 64, MODE, V>(p, in, out, tw, s);
+        case 96: return launch_nf_v<T, 96, MODE, V>(p, in, out, tw, s);
+        case 128: return launch_nf_v<T, 128, MODE, V>(p, in, out, tw, s);
+        case 192: return launch_nf_v<T, 192, MODE, V>(p, in, out, tw, s);
+        case 256: return launch_nf_v<T, 256, MODE, V>(p, in, out, tw, s);
+        case 384: return launch_nf_v<T, 384, MODE, V>(p, in, out, tw, s);
+        case 512: return launch_nf_v<T, 512, MODE, V>(p, in, out, tw, s);
+        case 768: return launch_nf_v<T, 768, MODE, V>(p, in, out, tw, s);
+        case 1024: return launch_nf_v<T, 1024, MODE, V>(p, in, out, tw, s);
+        case 1536: return launch_nf_v<T, 1536, MODE, V>(p, in, out, tw, s);
+        case 2048: return launch_nf_v<T, 2048, MODE, V>(p, in, out, tw, s);
         default: return cudaErrorInvalidValue;
     }
 }

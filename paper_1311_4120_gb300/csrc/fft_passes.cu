@@ -4,23 +4,29 @@
 
 namespace nlint {
 
-// the kernels are instantiated in fft_{f32,f64}_{col,row,colp,conv,dual}.cu
-extern template cudaError_t launch_pass_mode<float, 0>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
-extern template cudaError_t launch_pass_mode<float, 1>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
-extern template cudaError_t launch_pass_mode<float, 2>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
-extern template cudaError_t launch_pass_mode<double, 0>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
-extern template cudaError_t launch_pass_mode<double, 1>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
-extern template cudaError_t launch_pass_mode<double, 2>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
-extern template cudaError_t launch_pass_mode<float, 3>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
-extern template cudaError_t launch_pass_mode<float, 4>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
-extern template cudaError_t launch_pass_mode<double, 3>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
-extern template cudaError_t launch_pass_mode<double, 4>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
-extern template cudaError_t launch_pass_mode<float, 5>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
-extern template cudaError_t launch_pass_mode<double, 5>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
-extern template cudaError_t launch_pass_mode<float, 6>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
-extern template cudaError_t launch_pass_mode<float, 7>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
-extern template cudaError_t launch_pass_mode<double, 6>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
-extern template cudaError_t launch_pass_mode<double, 7>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
+// the kernels are instantiated in fft_{f32,f64}_{col,row,rowr,colp,conv,dual}.cu (schedule 0) and
+// fft_f32_{col,row,rowr,colp}_s1.cu (schedule 1)
+extern template cudaError_t launch_pass_mode_v<float, 0, 0>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
+extern template cudaError_t launch_pass_mode_v<float, 1, 0>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
+extern template cudaError_t launch_pass_mode_v<float, 2, 0>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
+extern template cudaError_t launch_pass_mode_v<float, 3, 0>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
+extern template cudaError_t launch_pass_mode_v<float, 4, 0>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
+extern template cudaError_t launch_pass_mode_v<float, 5, 0>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
+extern template cudaError_t launch_pass_mode_v<float, 6, 0>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
+extern template cudaError_t launch_pass_mode_v<float, 7, 0>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
+extern template cudaError_t launch_pass_mode_v<double, 0, 0>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
+extern template cudaError_t launch_pass_mode_v<double, 1, 0>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
+extern template cudaError_t launch_pass_mode_v<double, 2, 0>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
+extern template cudaError_t launch_pass_mode_v<double, 3, 0>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
+extern template cudaError_t launch_pass_mode_v<double, 4, 0>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
+extern template cudaError_t launch_pass_mode_v<double, 5, 0>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
+extern template cudaError_t launch_pass_mode_v<double, 6, 0>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
+extern template cudaError_t launch_pass_mode_v<double, 7, 0>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
+extern template cudaError_t launch_pass_mode_v<float, 0, 1>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
+extern template cudaError_t launch_pass_mode_v<float, 1, 1>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
+extern template cudaError_t launch_pass_mode_v<float, 2, 1>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
+extern template cudaError_t launch_pass_mode_v<float, 3, 1>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
+extern template cudaError_t launch_pass_mode_v<float, 4, 1>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
 
 int pass_mode(const PassDesc &p, bool row) {
     if (!row) {
@@ -63,12 +69,21 @@ void make_radix(int n, PassDesc &p) {
     p.nrad = k;
 }
 
-void config_pass(PassDesc &p, int prec, bool row) {
+void config_pass(PassDesc &p, int prec, bool row, unsigned sched) {
     const int cs = prec == NLINT_FP32 ? 8 : 16;
     const int mode = pass_mode(p, row);
-    p.TPC = fft_tpl(p.n, mode);
-    p.B = row ? fft_row_b(p.n, cs, mode) : fft_col_b_m(p.n, cs, mode);
+    const int bit = mode == 0 ? 0 : mode == 1 ? 1 : mode == 2 ? 2 : (mode == 3 || mode == 4) ? 3 : -1;
+    p.sched = (prec == NLINT_FP32 && bit >= 0 && fft_has_alt(p.n, mode)) ? (int)((sched >> bit) & 1u) : 0;
+    p.TPC = fft_tpl(p.n, mode, p.sched);
+    p.B = row ? fft_row_b(p.n, cs, mode, p.sched) : fft_col_b_m(p.n, cs, mode, p.sched);
     p.LD = row ? fft_row_ld(p.n) : p.B;
+}
+
+template <typename T, int MODE>
+cudaError_t launch_pass_mode(const PassDesc &p, const void *in, void *out, const void *tw, cudaStream_t s) {
+    if constexpr (sizeof(T) == 4 && MODE <= 4)
+        if (p.sched) return launch_pass_mode_v<T, MODE, 1>(p, in, out, tw, s);
+    return launch_pass_mode_v<T, MODE, 0>(p, in, out, tw, s);
 }
 
 int pass_threads(const PassDesc &p) { return p.B * p.TPC; }

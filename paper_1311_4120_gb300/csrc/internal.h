@@ -84,6 +84,7 @@ struct PassDesc {
     // the convolution pass (mode 5) every multiplier row with s0^2 + s1^2 > ball2 is zero, so
     // those rows write zeros without transforming
     int64_t ball2;
+    int sched;           // schedule variant of this pass (0 or 1), set by config_pass
 };
 
 void make_radix(int n, PassDesc &p);
@@ -92,13 +93,20 @@ int fft_next_size(int64_t m);     // smallest supported size >= m, or -1
 int64_t pass_blocks(const PassDesc &p, bool row);
 int pass_threads(const PassDesc &p);
 size_t pass_smem(const PassDesc &p, int prec);
-void config_pass(PassDesc &p, int prec, bool row);
+// CTA geometry of a pass; `sched` is the plan's schedule mask (nlint_params.fft_sched: bit 0
+// column passes, 1 row passes, 2 the fold pass, 3 the packed real-data passes; FP32 only)
+void config_pass(PassDesc &p, int prec, bool row, unsigned sched = 0);
 bool pass_fits(const PassDesc &p);
 
 // pass mode 0: column pass; 1: row pass; 2: row pass reading the fold input;
 // 3: column pass real -> Hermitian half, two lines per FFT; 4: Hermitian half -> real, two lines;
 // 5: row pass forward FFT, multiply, inverse FFT; 6, 7: dual column passes (forward, inverse)
 int pass_mode(const PassDesc &p, bool row);
+// Launch of a pass of mode MODE with schedule V (see fft_kernels.cuh); launch_pass_mode picks V
+// from the descriptor (p.sched, FP32 modes 0-4 only).
+template <typename T, int MODE, int V>
+cudaError_t launch_pass_mode_v(const PassDesc &p, const void *in, void *out, const void *tw,
+                               cudaStream_t s);
 template <typename T, int MODE>
 cudaError_t launch_pass_mode(const PassDesc &p, const void *in, void *out, const void *tw,
                              cudaStream_t s);

@@ -940,7 +940,7 @@ __global__ void __launch_bounds__(SUB_THREADS) interp_grp_kernel(NodeDesc nd, co
     using G_ = Geo<float, 3, W, BS>;
     constexpr int T0 = G_::T0, T1 = G_::T1, T2 = G_::T2, RP = T1 * T2, NW = SUB_THREADS / 32;
     constexpr unsigned TILE_BYTES = (unsigned)(T0 * RP) * 8u;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     // the TMA destination must be 128-byte aligned: the launcher adds 128 bytes of room
     float2 *tile = reinterpret_cast<float2 *>(smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u));
     __shared__ __align__(8) unsigned long long mbar;

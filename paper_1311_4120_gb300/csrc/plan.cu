@@ -207,6 +207,7 @@ struct nlint_plan_s {
     double2 *d_crowd = nullptr;
     int B[3], T[3];
     int bin_shape = 1;
+    unsigned fft_sched = 0;      // FFT pass schedules (nlint_params.fft_sched; FP32 only)
     int64_t nsub = 0, nbins = 0, ngsub = 0;
     int ncrowd = 0;
     size_t bytes_crowd = 0;
@@ -373,6 +374,7 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
         return fail(NLINT_EINVAL, "kernel must be NLINT_COULOMB or NLINT_DIPOLE");
     if (q.max_sub < 0 || q.max_sub > (1 << 20)) return fail(NLINT_EINVAL, "max_sub must be in [0, 2^20]");
     if (q.crowd_min < 0) return fail(NLINT_EINVAL, "crowd_min must be >= 0");
+    if (q.fft_sched < 0 || q.fft_sched > 15) return fail(NLINT_EINVAL, "fft_sched must be in [0, 15]");
     p->d = q.d;
     p->N = q.n;
     p->L = q.L;
@@ -417,6 +419,7 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
     if (eps < 1e-15) eps = 1e-15;
     p->prec = (q.precision == NLINT_FP32 || q.precision == NLINT_FP64) ? q.precision
                                                                        : (eps >= 1e-7 ? NLINT_FP32 : NLINT_FP64);
+    p->fft_sched = p->prec == NLINT_FP32 ? (unsigned)q.fft_sched : 0u;
     int w = q.w > 0 ? q.w : (int)std::ceil(-std::log10(eps)) + 1;
     if (w < 2) w = 2;
     if (w > 16) return fail(NLINT_EINVAL, "spreading width must be <= 16");
@@ -875,13 +878,13 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
     }
     if (p->P1.nrad < 0) return fail(NLINT_EUNSUPPORTED, "fine grid size is not 2^a 3^b");
     p->P3.ball2 = p->Q1.ball2 = p->ball2;
-    config_pass(p->P1, p->prec, false);
-    config_pass(p->P3, p->prec, true);
-    config_pass(p->Q1, p->prec, true);
-    config_pass(p->Q3, p->prec, false);
+    config_pass(p->P1, p->prec, false, p->fft_sched);
+    config_pass(p->P3, p->prec, true, p->fft_sched);
+    config_pass(p->Q1, p->prec, true, p->fft_sched);
+    config_pass(p->Q3, p->prec, false, p->fft_sched);
     if (d == 3) {
-        config_pass(p->P2, p->prec, false);
-        config_pass(p->Q2, p->prec, false);
+        config_pass(p->P2, p->prec, false, p->fft_sched);
+        config_pass(p->Q2, p->prec, false, p->fft_sched);
     }
     for (PassDesc *pd : {&p->P1, &p->P3, &p->Q1, &p->Q3})
         if (!pass_fits(*pd)) return fail(NLINT_EUNSUPPORTED, "internal: FFT pass does not fit");
@@ -957,7 +960,7 @@ static void conv_passes(nlint_plan_s *p) {
     p->X.out_so = N;
     p->X.mult = p->d_khat;
     p->X.conv = 1;
-    config_pass(p->X, p->prec, true);
+    config_pass(p->X, p->prec, true, p->fft_sched);
 }
 
 // Algorithm 2: I_1's multiplier M(k) / n_fine^d on the real half grid of the fine grid's DFT
@@ -1049,9 +1052,9 @@ static void alg2_window(nlint_plan_s *p) {
         p->Q2w.out_so = N * N; p->Q2w.out_sa = N;
         base(p->Q3w, +1, IN_CPLX_HERM, OUT_REAL_MODES);
         p->Q3w.I = N * N; p->Q3w.n_outer = 1; p->Q3w.in_sa = N * N; p->Q3w.out_sa = N * N;
-        config_pass(p->P2w, p->prec, false);
-        config_pass(p->P3w, p->prec, true);
-        config_pass(p->Q2w, p->prec, false);
+        config_pass(p->P2w, p->prec, false, p->fft_sched);
+        config_pass(p->P3w, p->prec, true, p->fft_sched);
+        config_pass(p->Q2w, p->prec, false, p->fft_sched);
         p->bytes_Hwin = (size_t)(win + 2 * p->pad + 1) * n * n * cs;
     } else {
         base(p->P1w, -1, IN_REAL_MODES, OUT_CPLX_HALF);
@@ -1063,12 +1066,12 @@ static void alg2_window(nlint_plan_s *p) {
         p->Q1w.fold_plane = n; p->Q1w.fold_rows_per_plane = 1;
         base(p->Q3w, +1, IN_CPLX_HERM, OUT_REAL_MODES);
         p->Q3w.I = N; p->Q3w.n_outer = 1; p->Q3w.in_sa = N; p->Q3w.out_sa = N;
-        config_pass(p->P3w, p->prec, true);
+        config_pass(p->P3w, p->prec, true, p->fft_sched);
         p->bytes_Hwin = (size_t)(win + 2 * p->pad + 1) * n * cs;
     }
-    config_pass(p->P1w, p->prec, false);
-    config_pass(p->Q1w, p->prec, true);
-    config_pass(p->Q3w, p->prec, false);
+    config_pass(p->P1w, p->prec, false, p->fft_sched);
+    config_pass(p->Q1w, p->prec, true, p->fft_sched);
+    config_pass(p->Q3w, p->prec, false, p->fft_sched);
     if (pass_blocks(p->Q3w, false) > p->n_partials) return;  // (same grid as Q3: never)
     p->win = win;
     // the dual z passes (I_1 with unit factors, I_2 with the deconvolution) when their grid fits
@@ -1078,7 +1081,7 @@ static void alg2_window(nlint_plan_s *p) {
         dst.dual = 1;
         dst.fac = p->d_fac1;
         dst.fac2 = p->d_fac;
-        config_pass(dst, p->prec, false);
+        config_pass(dst, p->prec, false, p->fft_sched);
     };
     dual(p->D6, p->P1w);
     dual(p->D7, p->Q3w);
@@ -1516,6 +1519,7 @@ int nlint_plan_info(nlint_plan p, nlint_info *info) {
     info->n_crowd_bins = p->ncrowd;
     for (int a = 0; a < 3; a++) info->bin[a] = p->B[a];
     info->bin_shape = p->bin_shape;
+    info->fft_sched = (int)p->fft_sched;
     info->device = p->device;
     info->algorithm = p->algorithm;
     info->pu_a = p->pu_a;
@@ -1656,9 +1660,9 @@ int nlint_plan_toeplitz(nlint_plan p, void *stream) {
         kpass(K2, IN_CPLX_MODES, OUT_CPLX_FULL);
         K2.I = n; K2.n_outer = nh; K2.in_so = (int64_t)n * n; K2.in_sa = n; K2.out_so = (int64_t)n * n; K2.out_sa = n;
         K3.I = nh * n; K3.in_so = n; K3.out_so = n;
-        config_pass(K1, p->prec, false);
-        config_pass(K2, p->prec, false);
-        config_pass(K3, p->prec, true);
+        config_pass(K1, p->prec, false, p->fft_sched);
+        config_pass(K2, p->prec, false, p->fft_sched);
+        config_pass(K3, p->prec, true, p->fft_sched);
         if (p->prec == NLINT_FP32) {
             CK(launch_colpass<float>(K1, t.kbuf, p->d_bufG, p->d_tw, s));
             CK(launch_colpass<float>(K2, p->d_bufG, t.kbuf, p->d_tw, s));
@@ -1672,8 +1676,8 @@ int nlint_plan_toeplitz(nlint_plan p, void *stream) {
     } else {
         K1.I = n; K1.n_outer = 1; K1.in_sa = n; K1.out_sa = n;
         K3.I = nh; K3.in_so = n; K3.out_so = n;
-        config_pass(K1, p->prec, false);
-        config_pass(K3, p->prec, true);
+        config_pass(K1, p->prec, false, p->fft_sched);
+        config_pass(K3, p->prec, true, p->fft_sched);
         if (p->prec == NLINT_FP32) {
             CK(launch_colpass<float>(K1, t.kbuf, p->d_bufG, p->d_tw, s));
             CK(launch_rowpass<float>(K3, p->d_bufG, t.kbuf, p->d_tw, s));

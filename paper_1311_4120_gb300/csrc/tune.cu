@@ -11,7 +11,9 @@
 // node kernels' lane layout depends on w) it times the bin shapes compiled for the plan's
 // precision and dimension (the tile each interpolation / spreading CTA stages: 3D FP32 8^3,
 // 8x16x16, 16^3; 3D FP64 8^3, 4x8x8; the shapes whose tile fits in shared memory at w), then,
-// for the fastest width and shape, the subproblem sizes (nodes per CTA), and keeps the fastest.
+// for the fastest width and shape, the subproblem sizes (nodes per CTA), and keeps the fastest;
+// then (FP32) the FFT pass schedules, one pass class at a time (coordinate descent over the
+// four bits of nlint_params.fft_sched), each kept when it measured faster.
 // Cache: one JSON object per line in `cache_path` (or $NLINT_TUNE_CACHE), keyed by the plan's
 // geometry, kernel, precision and tolerance; a hit skips all measurement.
 #include <algorithm>
@@ -85,7 +87,7 @@ std::string cache_key(const nlint_params &p, double tol) {
 }
 
 bool cache_lookup(const char *path, const std::string &key, int &w, int &max_sub, int &bin_shape,
-                  double &err, int &w_alt, double &err_alt) {
+                  double &err, int &w_alt, double &err_alt, int &fft_sched) {
     if (!path) return false;
     FILE *f = std::fopen(path, "r");
     if (!f) return false;
@@ -100,6 +102,7 @@ bool cache_lookup(const char *path, const std::string &key, int &w, int &max_sub
         const char *pe = std::strstr(line, "\"err\": ");
         const char *pa = std::strstr(line, "\"w_alt\": ");
         const char *pea = std::strstr(line, "\"err_alt\": ");
+        const char *pfs = std::strstr(line, "\"fft_sched\": ");
         if (pw && pm && pb && pe) {  // lines without a bin shape are from an older tuner: a miss
             w = std::atoi(pw + 5);
             max_sub = std::atoi(pm + 11);
@@ -107,6 +110,7 @@ bool cache_lookup(const char *path, const std::string &key, int &w, int &max_sub
             err = std::atof(pe + 7);
             w_alt = (pa && pea) ? std::atoi(pa + 9) : 0;
             err_alt = (pa && pea) ? std::atof(pea + 11) : 0.0;
+            fft_sched = pfs ? std::atoi(pfs + 13) : 0;
             // the last matching line wins
             hit = w >= 2 && w <= NODE_MAXW && max_sub > 0 && bin_shape >= 1 && bin_shape <= NBIN_SHAPES;
         }
@@ -116,14 +120,14 @@ bool cache_lookup(const char *path, const std::string &key, int &w, int &max_sub
 }
 
 void cache_store(const char *path, const std::string &key, int w, int max_sub, int bin_shape, double err,
-                 double ms, int w_alt, double err_alt) {
+                 double ms, int w_alt, double err_alt, int fft_sched) {
     if (!path) return;
     FILE *f = std::fopen(path, "a");
     if (!f) return;
     std::fprintf(f,
                  "{\"key\": \"%s\", \"w\": %d, \"max_sub\": %d, \"bin_shape\": %d, \"err\": %.6g, "
-                 "\"ms\": %.6g, \"w_alt\": %d, \"err_alt\": %.6g}\n",
-                 key.c_str(), w, max_sub, bin_shape, err, ms, w_alt, err_alt);
+                 "\"ms\": %.6g, \"w_alt\": %d, \"err_alt\": %.6g, \"fft_sched\": %d}\n",
+                 key.c_str(), w, max_sub, bin_shape, err, ms, w_alt, err_alt, fft_sched);
     std::fclose(f);
 }
 
@@ -221,14 +225,15 @@ extern "C" int nlint_autotune(const nlint_params *in, double tol, const char *ca
         p.precision = tol >= 1e-7 ? NLINT_FP32 : NLINT_FP64;
     if (!cache_path) cache_path = std::getenv("NLINT_TUNE_CACHE");
     const std::string key = cache_key(p, tol);
-    int w = 0, max_sub = 0, bshape = 0, walt = 0;
+    int w = 0, max_sub = 0, bshape = 0, walt = 0, fsched = 0;
     double err = 0.0, ealt = 0.0;
-    if (cache_lookup(cache_path, key, w, max_sub, bshape, err, walt, ealt)) {
+    if (cache_lookup(cache_path, key, w, max_sub, bshape, err, walt, ealt, fsched)) {
         p.w = w;
         p.max_sub = max_sub;
         p.bin_shape = bshape;
+        p.fft_sched = fsched;
         *out = p;
-        if (rep) *rep = nlint_tune_report{w, max_sub, err, 0.0, 1, bshape, walt, ealt};
+        if (rep) *rep = nlint_tune_report{w, max_sub, err, 0.0, 1, bshape, walt, ealt, fsched};
         return NLINT_OK;
     }
     if (p.device >= 0 && cudaSetDevice(p.device) != cudaSuccess)
@@ -286,11 +291,12 @@ extern "C" int nlint_autotune(const nlint_params *in, double tol, const char *ca
     // width and the next one (which also meets the tolerance, with a smaller error, and can be
     // faster: the lane layout of the node kernels depends on w), then the fastest subproblem size
     // for that pair; a shape whose tile does not fit at a width is skipped
-    auto time_candidate = [&](int cw, int bs, int cs, double &t) -> int {
+    auto time_candidate = [&](int cw, int bs, int cs, double &t, int fs = 0) -> int {
         nlint_params cp = p;
         cp.w = cw;
         cp.max_sub = cs;
         cp.bin_shape = bs;
+        cp.fft_sched = fs;
         nlint_plan pl = nullptr;
         const int crc = nlint_plan_create_ex(&cp, &pl);
         if (crc == NLINT_EUNSUPPORTED) return crc;
@@ -356,12 +362,26 @@ extern "C" int nlint_autotune(const nlint_params *in, double tol, const char *ca
             best_sub = cs;
         }
     }
+    // FFT pass schedules (FP32): one pass class at a time, kept when faster
+    int best_fs = 0;
+    if (!f64) {
+        for (int bit = 0; bit < 4; bit++) {
+            double t = 0.0;
+            rc = time_candidate(best_w, best_bs, best_sub, t, best_fs | (1 << bit));
+            if (rc) return rc;
+            if (t < best_ms) {
+                best_ms = t;
+                best_fs |= 1 << bit;
+            }
+        }
+    }
     p.w = best_w;
     p.max_sub = best_sub;
     p.bin_shape = best_bs;
-    cache_store(cache_path, key, best_w, best_sub, best_bs, best_err, best_ms, alt_w, alt_err);
+    p.fft_sched = best_fs;
+    cache_store(cache_path, key, best_w, best_sub, best_bs, best_err, best_ms, alt_w, alt_err, best_fs);
     *out = p;
-    if (rep) *rep = nlint_tune_report{best_w, best_sub, best_err, best_ms, 0, best_bs, alt_w, alt_err};
+    if (rep) *rep = nlint_tune_report{best_w, best_sub, best_err, best_ms, 0, best_bs, alt_w, alt_err, best_fs};
     return NLINT_OK;
 }
 
@@ -479,6 +499,7 @@ extern "C" int nlint_autotune_batch(int count, const nlint_params *in, double to
         p.w = t.w;
         p.bin_shape = t.bin_shape;
         p.max_sub = t.max_sub;
+        p.fft_sched = t.fft_sched;  // the class's FFT schedules in every set
         cand[0].push_back(p);
         p.bin_shape = 0;
         p.max_sub = 0;

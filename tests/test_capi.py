@@ -76,6 +76,8 @@ def _create(lib, **kw):
     (dict(algorithm=2, pu_a=float("nan")), -1, "Algorithm 2"),
     (dict(algorithm=2, P2=100.0), -1, "P2"),
     (dict(algorithm=2, d=2, pu_r0=2.0, pu_r1=1.0), -1, "pu_r0 < pu_r1"),
+    (dict(fft_sched=16), -1, "fft_sched"),
+    (dict(fft_sched=-1), -1, "fft_sched"),
 ])
 def test_bad_arguments_are_rejected_before_any_gpu_work(lib, kw, code, word):
     rc, msg = _create(lib, **kw)
@@ -112,6 +114,7 @@ def test_params_default(lib):
     assert prm.eps == 1e-6
     # the last fields: the ctypes mirror of the struct ends where the C struct does
     assert prm.algorithm == 1 and prm.pu_a == 0.0 and prm.pu_r0 == 0.0 and prm.P2 == 0.0
+    assert prm.bin_shape == 0 and prm.fft_sched == 0
     sentinel = (ctypes.c_char * (ctypes.sizeof(prm) + 64))()
     ctypes.memset(sentinel, 0x5A, len(sentinel))
     lib.nlint_params_default(ctypes.cast(sentinel, ctypes.POINTER(pkg.nlint_params)))
