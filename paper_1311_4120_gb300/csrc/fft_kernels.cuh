@@ -21,21 +21,31 @@
 namespace nlint {
 
 // ------------------------------------------------------------------ compile-time schedule
+// Schedule 0: radix 8 stages, then one radix 4 or 2, then one radix 3.  Schedule 1 (lines of 2^a
+// points, a >= 7; chosen per plan and pass class, nlint_params.fft_sched): two stages of radix
+// 2^ceil(a/2) and 2^floor(a/2) (a <= 10; a = 11: 16, 16, 8), so that a line takes one exchange
+// through shared memory instead of two, with each thread holding one or two whole butterflies
+// of the larger radix.
 __host__ __device__ constexpr bool fft_has3(int n) { return n % 3 == 0; }
 __host__ __device__ constexpr int fft_log2(int m) { return m <= 1 ? 0 : 1 + fft_log2(m / 2); }
+__host__ __device__ constexpr bool fft_two_stage(int n, int v) { return v && !fft_has3(n) && n >= 128; }
 __host__ __device__ constexpr int fft_pow2(int n) { return fft_log2(fft_has3(n) ? n / 3 : n); }
 __host__ __device__ constexpr int fft_eights(int n) { return fft_pow2(n) / 3; }
 __host__ __device__ constexpr int fft_tail(int n) {  // 4, 2 or 1 after the radix-8 stages
     return fft_pow2(n) % 3 == 2 ? 4 : (fft_pow2(n) % 3 == 1 ? 2 : 1);
 }
-__host__ __device__ constexpr int fft_nstages(int n) {
-    return fft_eights(n) + (fft_tail(n) > 1 ? 1 : 0) + (fft_has3(n) ? 1 : 0);
+__host__ __device__ constexpr int fft_nstages(int n, int v = 0) {
+    return fft_two_stage(n, v) ? (fft_log2(n) <= 10 ? 2 : 3)
+                               : fft_eights(n) + (fft_tail(n) > 1 ? 1 : 0) + (fft_has3(n) ? 1 : 0);
 }
-__host__ __device__ constexpr int fft_radix(int n, int s) {
-    return s < fft_eights(n) ? 8 : (s == fft_eights(n) && fft_tail(n) > 1) ? fft_tail(n) : 3;
+__host__ __device__ constexpr int fft_radix(int n, int s, int v = 0) {
+    return fft_two_stage(n, v)
+               ? (fft_log2(n) <= 10 ? (s == 0 ? 1 << ((fft_log2(n) + 1) / 2) : 1 << (fft_log2(n) / 2))
+                                    : (s < 2 ? 16 : 8))
+               : (s < fft_eights(n) ? 8 : (s == fft_eights(n) && fft_tail(n) > 1) ? fft_tail(n) : 3);
 }
-__host__ __device__ constexpr int fft_pprod(int n, int s) {  // product of the radices before s
-    return s == 0 ? 1 : fft_pprod(n, s - 1) * fft_radix(n, s - 1);
+__host__ __device__ constexpr int fft_pprod(int n, int s, int v = 0) {  // product of the radices before s
+    return s == 0 ? 1 : fft_pprod(n, s - 1, v) * fft_radix(n, s - 1, v);
 }
 // Pass modes: 0 column pass; 1 row pass; 2 row pass that reads more than it writes (the fold
 // input of the first inverse pass), which wants more threads per line.
@@ -54,22 +64,22 @@ __host__ __device__ constexpr int fft_vpt_small(int mode) {
     return mode == 0 ? FFT_VPT0 : mode == 1 ? FFT_VPT1 : mode == 2 ? 8
          : (mode == 3 || mode == 4) ? FFT_PACKED_VPT : (mode == 6 || mode == 7) ? FFT_DUAL_VPT : 16;
 }
-// Schedule variants: a plan picks, per pass class (nlint_params.fft_sched, searched by the
-// autotuner), schedule 0 above or schedule 1, the other values-per-thread choice of 2^a lines
-// (column and row passes 8 instead of 16, the fold and packed passes 16 instead of 8, lines
-// longer than 512 16 instead of 32) and with it the threads per line and lines per CTA.
-// 3 * 2^a lines and modes 5-7 have one schedule.
-__host__ __device__ constexpr bool fft_has_alt(int n, int mode) { return !fft_has3(n) && mode <= 4; }
-__host__ __device__ constexpr int fft_vpt_alt(int n, int mode) {
-    return n > 512 ? 16 : ((mode == 0 || mode == 1) ? 8 : 16);
-}
+// Schedule 1 (the two-stage radix schedule above) for modes 0-4 on lines of 2^a >= 128 points:
+// each thread holds the larger radix's worth of values (16 or 32).  3 * 2^a lines, shorter lines
+// and modes 5-7 have schedule 0 only.
+__host__ __device__ constexpr bool fft_has_alt(int n, int mode) { return fft_two_stage(n, 1) && mode <= 4; }
+__host__ __device__ constexpr int fft_vpt_alt(int n, int mode) { return fft_radix(n, 0, 1) + 0 * mode; }
 __host__ __device__ constexpr int fft_vpt(int n, int mode = 0, int v = 0) {
     return (v && fft_has_alt(n, mode)) ? fft_vpt_alt(n, mode)
                                        : (fft_has3(n) ? 24 : (n <= 512 ? fft_vpt_small(mode) : 32));
 }
 __host__ __device__ constexpr int fft_vpt_ref(int n) { return fft_has3(n) ? 24 : (n <= 512 ? 16 : 32); }
 __host__ __device__ constexpr int fft_tpl(int n, int mode = 0, int v = 0) { return n / fft_vpt(n, mode, v); }  // 2^k
-__host__ __device__ constexpr int fft_row_ld(int n) { return n + n / 16; }  // padded row line
+// padded row line: one pad cell per 16 (schedule 0) or per radix of the first stage (schedule 1,
+// whose first stage writes each thread's butterfly as a run of that many cells)
+__host__ __device__ constexpr int fft_row_ld(int n, int v = 0) {
+    return fft_two_stage(n, v) ? n + n / fft_radix(n, 0, 1) : n + n / 16;
+}
 // Lines per CTA.  Column pass: 128-byte rows (16 FP32 / 8 FP64 complex), fewer for the
 // longest lines (shared memory <= 192 KB), at least one warp.
 // Row pass: about 512 threads, at most 96 KB of shared memory, whole warps where possible.
@@ -85,12 +95,12 @@ __host__ __device__ constexpr int fft_col_b_m(int n, int cs, int mode, int v = 0
     return (fft_vpt(n, mode, v) * 2 == fft_vpt_ref(n) && fft_col_b(n, cs) >= 2) ? fft_col_b(n, cs) / 2
                                                                                 : fft_col_b(n, cs);
 }
-// Row pass: about 256 threads (mode 1) or 512 threads (mode 2) per CTA.
-__host__ __device__ constexpr int fft_row_thr(int mode) { return mode == 2 ? 512 : 256; }
+// Row pass: about 256 threads (mode 1, and every schedule-1 pass) or 512 threads (mode 2) per CTA.
+__host__ __device__ constexpr int fft_row_thr(int mode, int v = 0) { return (mode == 2 && !v) ? 512 : 256; }
 __host__ __device__ constexpr int fft_row_b_raw(int n, int cs, int mode, int v = 0) {
-    return (fft_row_thr(mode) / fft_tpl(n, mode, v)) < (96 * 1024) / (fft_row_ld(n) * cs)
-               ? fft_row_thr(mode) / fft_tpl(n, mode, v)
-               : (96 * 1024) / (fft_row_ld(n) * cs);
+    return (fft_row_thr(mode, v) / fft_tpl(n, mode, v)) < (96 * 1024) / (fft_row_ld(n, v) * cs)
+               ? fft_row_thr(mode, v) / fft_tpl(n, mode, v)
+               : (96 * 1024) / (fft_row_ld(n, v) * cs);
 }
 __host__ __device__ constexpr int fft_row_b(int n, int cs, int mode = 1, int v = 0) {
     return fft_row_b_raw(n, cs, mode, v) < 1 ? 1
@@ -135,9 +145,11 @@ template <typename T, int NF, int MODE, int V = 0>
 struct FftCfg {
     static constexpr int CS = (int)(2 * sizeof(T));
     static constexpr int TPL = fft_tpl(NF, MODE, V);  // threads per line
-    static constexpr int NST = fft_nstages(NF);
+    static constexpr int NST = fft_nstages(NF, V);
     static constexpr int B = fft_is_row(MODE) ? fft_row_b(NF, CS, MODE, V) : fft_col_b_m(NF, CS, MODE, V);  // lines
-    static constexpr int ROW_LD = fft_row_ld(NF);
+    static constexpr int ROW_LD = fft_row_ld(NF, V);
+    // row passes: shared index of line entry e, one pad cell per 2^PADSH entries
+    static constexpr int PADSH = fft_two_stage(NF, V) ? fft_log2(fft_radix(NF, 0, 1)) : 4;
     static constexpr int THREADS = B * TPL;
     // packed passes hold two lines' loads in flight: ask for two resident CTAs of 512 threads
     static constexpr bool F32_512 = THREADS == 512 && NF <= 512 && sizeof(T) == 4 && V == 0;
@@ -149,6 +161,69 @@ struct FftCfg {
 };
 
 // ------------------------------------------------------------------ butterflies
+// cos and sin of 2 pi m / R at compile time (R a multiple of 4): the quadrant is taken out
+// exactly, the rest (below pi / 2) by Taylor series to double precision
+__host__ __device__ constexpr double ct_sin_q(double x) {
+    double t = x, s = x;
+    for (int k = 1; k < 14; k++) {
+        t *= -x * x / (double)((2 * k) * (2 * k + 1));
+        s += t;
+    }
+    return s;
+}
+__host__ __device__ constexpr double ct_cos_q(double x) {
+    double t = 1.0, s = 1.0;
+    for (int k = 1; k < 14; k++) {
+        t *= -x * x / (double)((2 * k - 1) * (2 * k));
+        s += t;
+    }
+    return s;
+}
+__host__ __device__ constexpr double ct_cos2pi(int m, int R) {
+    const int q = (4 * (m % R)) / R;
+    const double ph = 6.283185307179586476925286766559 * (double)((m % R) - q * (R / 4)) / (double)R;
+    return q == 0 ? ct_cos_q(ph) : q == 1 ? -ct_sin_q(ph) : q == 2 ? -ct_cos_q(ph) : ct_sin_q(ph);
+}
+__host__ __device__ constexpr double ct_sin2pi(int m, int R) {
+    const int q = (4 * (m % R)) / R;
+    const double ph = 6.283185307179586476925286766559 * (double)((m % R) - q * (R / 4)) / (double)R;
+    return q == 0 ? ct_sin_q(ph) : q == 1 ? ct_cos_q(ph) : q == 2 ? -ct_sin_q(ph) : -ct_cos_q(ph);
+}
+
+template <typename T, int R>
+__device__ __forceinline__ void dft_small(cx_t<T> *v, int sign);
+
+// DFT of R = P Q points in registers (Cooley-Tukey, input index j1 + P j2, output k1 + Q k2):
+// Q-point DFTs over j2, twiddles W_R^(j1 k1) (compile-time constants), P-point DFTs over j1
+template <typename T, int P, int Q>
+__device__ __forceinline__ void dft_split(cx_t<T> *v, int sign) {
+    using T2 = cx_t<T>;
+    constexpr int R = P * Q;
+    T2 y[P][Q];
+#pragma unroll
+    for (int j1 = 0; j1 < P; j1++) {
+#pragma unroll
+        for (int j2 = 0; j2 < Q; j2++) y[j1][j2] = v[j1 + P * j2];
+        dft_small<T, Q>(y[j1], sign);
+    }
+    static_for<1, P>([&](auto J1) {
+        static_for<1, Q>([&](auto K1) {
+            constexpr int j1 = decltype(J1)::value, k1 = decltype(K1)::value, m = (j1 * k1) % R;
+            constexpr T c = (T)ct_cos2pi(m, R), sn = (T)ct_sin2pi(m, R);
+            y[j1][k1] = cmul(y[j1][k1], cmake<T2>(c, T(sign) * sn));
+        });
+    });
+#pragma unroll
+    for (int k1 = 0; k1 < Q; k1++) {
+        T2 x[P];
+#pragma unroll
+        for (int j1 = 0; j1 < P; j1++) x[j1] = y[j1][k1];
+        dft_small<T, P>(x, sign);
+#pragma unroll
+        for (int k2 = 0; k2 < P; k2++) v[k1 + Q * k2] = x[k2];
+    }
+}
+
 template <typename T, int R>
 __device__ __forceinline__ void dft_small(cx_t<T> *v, int sign) {
     using T2 = cx_t<T>;
@@ -190,6 +265,10 @@ __device__ __forceinline__ void dft_small(cx_t<T> *v, int sign) {
         v[6] = csub(e[2], o2);
         v[3] = cadd(e[3], o3);
         v[7] = csub(e[3], o3);
+    } else if constexpr (R == 16) {
+        dft_split<T, 4, 4>(v, sign);
+    } else if constexpr (R == 32) {
+        dft_split<T, 8, 4>(v, sign);
     }
 }
 
@@ -366,13 +445,13 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE, V>::THREADS, FftCfg<T, NF,
     // entry e of a row pass inside the ball window
     auto in_ball = [&](int e) { return (e <= NF / 2 ? e : NF - e) <= xl; };
 
-    auto sidx = [&](int e) -> int { return ROW ? ll * C::ROW_LD + e + (e >> 4) : e * B + ll; };
+    auto sidx = [&](int e) -> int { return ROW ? ll * C::ROW_LD + e + (e >> C::PADSH) : e * B + ll; };
 
     constexpr unsigned KM = fft_in_mask(MODE), OM = fft_out_mask(MODE);
     // ---- stage 0: global -> registers -> DFT -> shared
     int sgn = MODE == 5 ? -1 : sign;  // mode 5: forward transform first
     {
-        constexpr int R = fft_radix(NF, 0);
+        constexpr int R = fft_radix(NF, 0, V);
         constexpr int NB = NF / R;
         constexpr int MB = NB / TPL;
         T2 v[MB][R];
@@ -427,10 +506,10 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE, V>::THREADS, FftCfg<T, NF,
     EAcc<T> eacc;  // this thread's u*rho products
     auto stage = [&](auto S_) {
         constexpr int S = decltype(S_)::value;
-        constexpr int R = fft_radix(NF, S);
+        constexpr int R = fft_radix(NF, S, V);
         constexpr int NB = NF / R;
         constexpr int MB = NB / TPL;
-        constexpr int PP = fft_pprod(NF, S);
+        constexpr int PP = fft_pprod(NF, S, V);
         constexpr int STEP = NF / (PP * R);
         constexpr bool LAST = (S == C::NST - 1);
         T2 v[MB][R];
@@ -506,7 +585,7 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE, V>::THREADS, FftCfg<T, NF,
     if constexpr (MODE == 5) {  // the inverse transform of the multiplied line (natural order)
         __syncthreads();
         sgn = +1;
-        constexpr int R = fft_radix(NF, 0);
+        constexpr int R = fft_radix(NF, 0, V);
         constexpr int NB = NF / R;
         constexpr int MB = NB / TPL;
         T2 v[MB][R];
@@ -608,7 +687,8 @@ cudaError_t launch_nf(const PassDesc &p, const void *in, void *out, const void *
         return cudaErrorInvalidValue;  // a pass descriptor this mode was not compiled for
     if (fft_dual(MODE) && (!p.fac2 || (MODE == 6 ? !p.out2 : !p.in2) || p.win <= 0 || p.win > NF / 2))
         return cudaErrorInvalidValue;  // a dual pass needs its second factors, buffer and window
-    if (p.TPC != FftCfg<T, NF, MODE, V>::TPL || p.B != FftCfg<T, NF, MODE, V>::B)
+    if (p.TPC != FftCfg<T, NF, MODE, V>::TPL || p.B != FftCfg<T, NF, MODE, V>::B ||
+        (fft_is_row(MODE) && p.LD != FftCfg<T, NF, MODE, V>::ROW_LD))
         return cudaErrorInvalidValue;  // the descriptor was configured for another schedule
     const size_t smem = pass_smem(p, sizeof(T) == 4 ? NLINT_FP32 : NLINT_FP64);
     cudaError_t e = cudaFuncSetAttribute(fft_pass_kernel<T, NF, MODE, V>,

@@ -76,7 +76,7 @@ void config_pass(PassDesc &p, int prec, bool row, unsigned sched) {
     p.sched = (prec == NLINT_FP32 && bit >= 0 && fft_has_alt(p.n, mode)) ? (int)((sched >> bit) & 1u) : 0;
     p.TPC = fft_tpl(p.n, mode, p.sched);
     p.B = row ? fft_row_b(p.n, cs, mode, p.sched) : fft_col_b_m(p.n, cs, mode, p.sched);
-    p.LD = row ? fft_row_ld(p.n) : p.B;
+    p.LD = row ? fft_row_ld(p.n, p.sched) : p.B;
 }
 
 template <typename T, int MODE>
