@@ -60,6 +60,7 @@ constexpr int FFT_VPT1 = 16, FFT_MINB1 = 0;                 // row passes
 // 0.087 ms, inverse 0.156 -> 0.133 ms at n = 512): these passes are bound by load latency
 constexpr int FFT_PACKED_VPT = 8, FFT_PACKED_MINB = 4;
 constexpr int FFT_DUAL_VPT = 16, FFT_DUAL_MINB = 3;         // dual column passes (modes 6, 7)
+constexpr int FFT_STAGED_MINB = 4;  // packed passes with staged input (kernel variant 2)
 __host__ __device__ constexpr int fft_vpt_small(int mode) {
     return mode == 0 ? FFT_VPT0 : mode == 1 ? FFT_VPT1 : mode == 2 ? 8
          : (mode == 3 || mode == 4) ? FFT_PACKED_VPT : (mode == 6 || mode == 7) ? FFT_DUAL_VPT : 16;
@@ -124,6 +125,20 @@ __host__ __device__ constexpr bool fft_packed(int mode) { return mode == 3 || mo
 __host__ __device__ constexpr bool fft_dual(int mode) { return mode == 6 || mode == 7; }
 __host__ __device__ constexpr int fft_pack(int mode) { return fft_packed(mode) ? 2 : 1; }
 
+// Kernel variant 2 of the FP32 packed real-data passes (modes 3, 4; the geometry of schedule 0):
+// the CTA's input is staged in shared memory by 16-byte asynchronous copies (cp.async) before
+// the first stage.  Used whenever the rows of a CTA's data columns are 16-byte aligned runs
+// (fft_stage_ok): at four resident CTAs the register loads of schedule 0 (32 registers per
+// thread) cannot hold a line's loads in flight, while the copies need no registers.  Rows
+// staged: mode 3 the N real modes of each column, mode 4 the Hermitian half (entries 0..n/2,
+// or 0..win within a window); elements of 4 (mode 3) or 8 (mode 4) bytes.
+__host__ __device__ constexpr bool fft_stages_input(int mode, int v, int cs) {
+    return (mode == 3 || mode == 4) && v == 2 && cs == 8;
+}
+__host__ __device__ constexpr int fft_stage_rows(int mode, int n, int N, int win) {
+    return mode == 3 ? N : ((win > 0 && win < n / 2) ? win + 1 : n / 2 + 1);
+}
+
 // Input and output kinds each mode is launched with (compile-time, so a single-kind mode has no
 // branch on the kind; the launcher rejects anything else).
 __host__ __device__ constexpr unsigned fft_in_mask(int mode) {
@@ -144,16 +159,18 @@ __host__ __device__ constexpr unsigned fft_out_mask(int mode) {
 template <typename T, int NF, int MODE, int V = 0>
 struct FftCfg {
     static constexpr int CS = (int)(2 * sizeof(T));
-    static constexpr int TPL = fft_tpl(NF, MODE, V);  // threads per line
-    static constexpr int NST = fft_nstages(NF, V);
-    static constexpr int B = fft_is_row(MODE) ? fft_row_b(NF, CS, MODE, V) : fft_col_b_m(NF, CS, MODE, V);  // lines
-    static constexpr int ROW_LD = fft_row_ld(NF, V);
+    static constexpr int VG = V == 1 ? 1 : 0;  // the schedule that sets the geometry
+    static constexpr int TPL = fft_tpl(NF, MODE, VG);  // threads per line
+    static constexpr int NST = fft_nstages(NF, VG);
+    static constexpr int B = fft_is_row(MODE) ? fft_row_b(NF, CS, MODE, VG) : fft_col_b_m(NF, CS, MODE, VG);  // lines
+    static constexpr int ROW_LD = fft_row_ld(NF, VG);
     // row passes: shared index of line entry e, one pad cell per 2^PADSH entries
-    static constexpr int PADSH = fft_two_stage(NF, V) ? fft_log2(fft_radix(NF, 0, 1)) : 4;
+    static constexpr int PADSH = fft_two_stage(NF, VG) ? fft_log2(fft_radix(NF, 0, 1)) : 4;
     static constexpr int THREADS = B * TPL;
     // packed passes hold two lines' loads in flight: ask for two resident CTAs of 512 threads
     static constexpr bool F32_512 = THREADS == 512 && NF <= 512 && sizeof(T) == 4 && V == 0;
-    static constexpr int MIN_BLOCKS = (fft_packed(MODE) && F32_512) ? FFT_PACKED_MINB
+    static constexpr int MIN_BLOCKS = (V == 2 && THREADS == 512 && NF <= 512) ? FFT_STAGED_MINB
+                                    : (fft_packed(MODE) && F32_512) ? FFT_PACKED_MINB
                                     : (fft_dual(MODE) && F32_512) ? FFT_DUAL_MINB
                                     : (MODE == 0 && F32_512) ? FFT_MINB0
                                     : (MODE == 1 && F32_512) ? FFT_MINB1
@@ -448,10 +465,57 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE, V>::THREADS, FftCfg<T, NF,
     auto sidx = [&](int e) -> int { return ROW ? ll * C::ROW_LD + e + (e >> C::PADSH) : e * B + ll; };
 
     constexpr unsigned KM = fft_in_mask(MODE), OM = fft_out_mask(MODE);
+    // ---- staged input (FP32 modes 3, 4): the CTA's 2B data columns, row by row, by cp.async
+    constexpr bool STAGE = fft_stages_input(MODE, V, C::CS);
+    constexpr int CPT2 = 2 * B;                                  // data columns of the CTA
+    constexpr int SES = MODE == 3 ? (int)sizeof(T) : (int)sizeof(T2);  // staged element bytes
+    constexpr int EPC = 16 / SES;                                // elements per 16-byte copy
+    int srows = 0;
+    if constexpr (STAGE && !ROW) {
+        const int64_t tiles = (P.I + CPT2 - 1) / CPT2;
+        const int64_t i0 = (blockIdx.x % tiles) * CPT2;
+        const int64_t in0 = (blockIdx.x / tiles) * P.in_so + i0;
+        {
+            srows = fft_stage_rows(MODE, NF, N, P.win);
+            constexpr int CPR = CPT2 / EPC;  // copies per row
+            const unsigned char *src = reinterpret_cast<const unsigned char *>(vin);
+            const uint32_t dst0 = (uint32_t)__cvta_generic_to_shared(smem_raw);
+            for (int c = threadIdx.x; c < srows * CPR; c += blockDim.x) {
+                const int row = c / CPR, k = c - row * CPR;
+                if (i0 + (int64_t)k * EPC < P.I) {
+                    const unsigned char *g = src + (in0 + row * P.in_sa + (int64_t)k * EPC) * SES;
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst0 + (uint32_t)((row * CPT2 + k * EPC) * SES)),
+                                 "l"(g)
+                                 : "memory");
+                }
+            }
+            asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+            __syncthreads();
+        }
+    }
+    // staged entry e of data column col (0..2B-1) of the CTA, as io.load would give it
+    auto sload = [&](int e, int col, const LineIO<T> &L) -> T2 {
+        T2 v = czero<T2>();
+        if (!L.valid) return v;
+        if constexpr (MODE == 3) {
+            const int m = e < NF / 2 ? e : e - NF;
+            if (m >= -h && m < h) {
+                const int a = m + h;
+                v.x = reinterpret_cast<const T *>(smem_raw)[a * CPT2 + col] * L.fac[a] * L.bfac;
+            }
+        } else {
+            const int f = e <= NF / 2 ? e : NF - e;
+            if (f < srows) {
+                v = reinterpret_cast<const T2 *>(smem_raw)[f * CPT2 + col];
+                if (e > NF / 2) v = cconj(v);
+            }
+        }
+        return v;
+    };
     // ---- stage 0: global -> registers -> DFT -> shared
     int sgn = MODE == 5 ? -1 : sign;  // mode 5: forward transform first
     {
-        constexpr int R = fft_radix(NF, 0, V);
+        constexpr int R = fft_radix(NF, 0, C::VG);
         constexpr int NB = NF / R;
         constexpr int MB = NB / TPL;
         T2 v[MB][R];
@@ -460,7 +524,14 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE, V>::THREADS, FftCfg<T, NF,
 #pragma unroll
             for (int r = 0; r < R; r++) {
                 const int e = t + b * TPL + r * NB;
-                if constexpr (MODE == 3 || MODE == 6) {  // z = x + i y from two real lines
+                if constexpr (STAGE) {  // (modes 3, 4) the two columns of this FFT line from the stage
+                    if constexpr (MODE == 3) {
+                        v[b][r] = cmake<T2>(sload(e, ll, io).x, sload(e, ll + B, io2).x);
+                    } else {
+                        const T2 X = sload(e, ll, io), Y = sload(e, ll + B, io2);
+                        v[b][r] = cmake<T2>(X.x - Y.y, X.y + Y.x);
+                    }
+                } else if constexpr (MODE == 3 || MODE == 6) {  // z = x + i y from two real lines
                     v[b][r] = cmake<T2>(io.template load<KM>(e, vin).x, io2.template load<KM>(e, vin).x);
                 } else if constexpr (MODE == 7) {  // Z = X1 + i X2, X2 from the second input
                     const T2 X = io.template load<KM>(e, vin), Y = io2.template load<KM>(e, P.in2);
@@ -492,6 +563,7 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE, V>::THREADS, FftCfg<T, NF,
                     for (int r = 0; r < R; r++) v[b][r] = cadd(v[b][r], cconj(m[b][r]));
             }
         }
+        if constexpr (STAGE) __syncthreads();  // the stage (aliasing buf) is read before buf is written
 #pragma unroll
         for (int b = 0; b < MB; b++) {
             dft_small<T, R>(v[b], sgn);
@@ -506,10 +578,10 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE, V>::THREADS, FftCfg<T, NF,
     EAcc<T> eacc;  // this thread's u*rho products
     auto stage = [&](auto S_) {
         constexpr int S = decltype(S_)::value;
-        constexpr int R = fft_radix(NF, S, V);
+        constexpr int R = fft_radix(NF, S, C::VG);
         constexpr int NB = NF / R;
         constexpr int MB = NB / TPL;
-        constexpr int PP = fft_pprod(NF, S, V);
+        constexpr int PP = fft_pprod(NF, S, C::VG);
         constexpr int STEP = NF / (PP * R);
         constexpr bool LAST = (S == C::NST - 1);
         T2 v[MB][R];
@@ -585,7 +657,7 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE, V>::THREADS, FftCfg<T, NF,
     if constexpr (MODE == 5) {  // the inverse transform of the multiplied line (natural order)
         __syncthreads();
         sgn = +1;
-        constexpr int R = fft_radix(NF, 0, V);
+        constexpr int R = fft_radix(NF, 0, C::VG);
         constexpr int NB = NF / R;
         constexpr int MB = NB / TPL;
         T2 v[MB][R];
@@ -681,6 +753,15 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE, V>::THREADS, FftCfg<T, NF,
 }
 
 // ------------------------------------------------------------------ launchers
+// kernel variant 2 applies: FP32 packed pass of schedule 0 whose staged rows are 16-byte runs
+template <typename T, int MODE>
+bool fft_stage_ok(const PassDesc &p, const void *in) {
+    if (!fft_stages_input(MODE, 2, (int)(2 * sizeof(T))) || p.sched != 0) return false;
+    const int64_t epc = 16 / (MODE == 3 ? (int64_t)sizeof(T) : (int64_t)(2 * sizeof(T)));
+    return (2 * p.B) % epc == 0 && p.I % epc == 0 && p.in_so % epc == 0 && p.in_sa % epc == 0 &&
+           (reinterpret_cast<uintptr_t>(in) & 15) == 0;
+}
+
 template <typename T, int NF, int MODE, int V>
 cudaError_t launch_nf(const PassDesc &p, const void *in, void *out, const void *tw, cudaStream_t s) {
     if (!(fft_in_mask(MODE) & (1u << p.in_kind)) || !(fft_out_mask(MODE) & (1u << p.out_kind)))
@@ -706,6 +787,8 @@ cudaError_t launch_nf(const PassDesc &p, const void *in, void *out, const void *
 template <typename T, int NF, int MODE, int V>
 cudaError_t launch_nf_v(const PassDesc &p, const void *in, void *out, const void *tw, cudaStream_t s) {
     if constexpr (V == 1 && !fft_has_alt(NF, MODE)) return launch_pass_mode_v<T, MODE, 0>(p, in, out, tw, s);
+    else if constexpr (V == 2 && !fft_stages_input(MODE, 2, (int)(2 * sizeof(T))))
+        return launch_pass_mode_v<T, MODE, 0>(p, in, out, tw, s);
     else return launch_nf<T, NF, MODE, V>(p, in, out, tw, s);
 }
 

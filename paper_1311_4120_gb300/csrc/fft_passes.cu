@@ -5,7 +5,7 @@
 namespace nlint {
 
 // the kernels are instantiated in fft_{f32,f64}_{col,row,rowr,colp,conv,dual}.cu (schedule 0) and
-// fft_f32_{col,row,rowr,colp}_s1.cu (schedule 1)
+// fft_f32_{col,row,rowr,colp}_s1.cu (schedule 1) and fft_f32_colp_s2.cu (staged input)
 extern template cudaError_t launch_pass_mode_v<float, 0, 0>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
 extern template cudaError_t launch_pass_mode_v<float, 1, 0>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
 extern template cudaError_t launch_pass_mode_v<float, 2, 0>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
@@ -27,6 +27,8 @@ extern template cudaError_t launch_pass_mode_v<float, 1, 1>(const PassDesc &, co
 extern template cudaError_t launch_pass_mode_v<float, 2, 1>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
 extern template cudaError_t launch_pass_mode_v<float, 3, 1>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
 extern template cudaError_t launch_pass_mode_v<float, 4, 1>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
+extern template cudaError_t launch_pass_mode_v<float, 3, 2>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
+extern template cudaError_t launch_pass_mode_v<float, 4, 2>(const PassDesc &, const void *, void *, const void *, cudaStream_t);
 
 int pass_mode(const PassDesc &p, bool row) {
     if (!row) {
@@ -83,6 +85,8 @@ template <typename T, int MODE>
 cudaError_t launch_pass_mode(const PassDesc &p, const void *in, void *out, const void *tw, cudaStream_t s) {
     if constexpr (sizeof(T) == 4 && MODE <= 4)
         if (p.sched) return launch_pass_mode_v<T, MODE, 1>(p, in, out, tw, s);
+    if constexpr (sizeof(T) == 4 && (MODE == 3 || MODE == 4))
+        if (fft_stage_ok<T, MODE>(p, in)) return launch_pass_mode_v<T, MODE, 2>(p, in, out, tw, s);
     return launch_pass_mode_v<T, MODE, 0>(p, in, out, tw, s);
 }
 
@@ -99,7 +103,13 @@ int64_t pass_blocks(const PassDesc &p, bool row) {
 size_t pass_smem(const PassDesc &p, int prec) {
     const size_t cs = (prec == NLINT_FP32) ? 8 : 16;
     const size_t a = (size_t)p.B * p.LD * cs, b = (size_t)p.n * p.B * cs;
-    const size_t s = a > b ? a : b;
+    size_t s = a > b ? a : b;
+    const int mode = pass_mode(p, false);
+    if (fft_stages_input(mode, p.sched == 0 ? 2 : 1, (int)cs)) {  // variant 2's staged input rows
+        const size_t es = mode == 3 ? cs / 2 : cs;
+        const size_t st = (size_t)fft_stage_rows(mode, p.n, p.N, p.win) * 2 * p.B * es;
+        if (st > s) s = st;
+    }
     return s > 64 * sizeof(double) ? s : 64 * sizeof(double);  // >= the energy scratch
 }
 

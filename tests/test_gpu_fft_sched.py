@@ -88,3 +88,23 @@ def test_fp64_plans_ignore_the_mask(pkg):
     p = pkg.Plan(3, 32, 12.0, "coulomb", precision="fp64", eps=1e-12, fft_sched=15, device=0)
     assert p.info["fft_sched"] == 0
     p.close()
+
+
+def test_staged_and_register_loads_of_the_real_data_passes_agree(pkg):
+    # the first z pass stages its input by 16-byte copies when the density is 16-byte aligned;
+    # a density 4 bytes into a buffer takes the register loads instead: the same transform
+    n, L = 64, 16.0
+    rho = _rho(3, n, L, 9).astype(np.float32)
+    plan = pkg.Plan(3, n, L, "coulomb", precision="fp32", eps=1e-6, device=0)
+    aligned = torch.from_numpy(rho).to("cuda:0")
+    assert aligned.data_ptr() % 16 == 0
+    buf = torch.zeros(rho.size + 4, dtype=torch.float32, device="cuda:0")
+    shifted = buf[1:1 + rho.size].view(rho.shape)
+    shifted.copy_(aligned)
+    assert shifted.data_ptr() % 16 == 4
+    ua, Ea = plan.eval_energy(aligned, lam=1.0)
+    us, Es = plan.eval_energy(shifted, lam=1.0)
+    ua, us = ua.double().cpu().numpy(), us.double().cpu().numpy()
+    plan.close()
+    assert _rel(us, ua) <= 2e-6
+    assert abs(float(Es.item()) - float(Ea.item())) <= 2e-6 * abs(float(Ea.item()))
