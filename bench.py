@@ -45,14 +45,14 @@ TOL = 1e-5                          # stated relative L-inf tolerance of the FP3
 # Measured with ncu on the 256^3 FP32 workload (one launch of each kernel, one pass of
 # dram__bytes_read.sum and dram__bytes_write.sum).
 TRAFFIC = {
-    "interp": {"bytes": 461.2e6, "src": "9b9ec3fc17e60eca"},
-    "spread": {"bytes": 659.0e6, "src": "9b9ec3fc17e60eca"},
-    "fwd_fft_z": {"bytes": 167.7e6, "src": "55fb4cf0b4e622f2"},
-    "fwd_fft_y": {"bytes": 341.3e6, "src": "55fb4cf0b4e622f2"},
-    "fwd_fft_x": {"bytes": 482.4e6, "src": "55fb4cf0b4e622f2"},
-    "inv_fft_x": {"bytes": 530.7e6, "src": "55fb4cf0b4e622f2"},
-    "inv_fft_y": {"bytes": 370.2e6, "src": "55fb4cf0b4e622f2"},
-    "inv_fft_z": {"bytes": 257.2e6, "src": "55fb4cf0b4e622f2"},
+    "interp": {"bytes": 461.4e6, "src": "a9688af65e35d826"},
+    "spread": {"bytes": 659.0e6, "src": "a9688af65e35d826"},
+    "fwd_fft_z": {"bytes": 155.1e6, "src": "7e39491ddbdf40d2"},
+    "fwd_fft_y": {"bytes": 341.2e6, "src": "7e39491ddbdf40d2"},
+    "fwd_fft_x": {"bytes": 481.8e6, "src": "7e39491ddbdf40d2"},
+    "inv_fft_x": {"bytes": 530.1e6, "src": "7e39491ddbdf40d2"},
+    "inv_fft_y": {"bytes": 370.0e6, "src": "7e39491ddbdf40d2"},
+    "inv_fft_z": {"bytes": 255.6e6, "src": "7e39491ddbdf40d2"},
 }
 
 
