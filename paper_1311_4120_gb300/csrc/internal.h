@@ -123,6 +123,13 @@ cudaError_t launch_rowpass(const PassDesc &p, const void *in, void *out, const v
 // starting at the bin's origin.  A subproblem is a run of at most a few hundred nodes of one
 // bin and is processed by one CTA on a shared-memory copy of the tile.  Axis 0 is the half
 // (slowest) axis; in 2D only axes 0 and 1 are used.
+static constexpr int NODE_MAXW = 16;     // widest stencil
+// Stencil-value polynomials of the FP32 3D interpolation: degree 8 at w = 7, 7 above (the fits
+// reach about 1e-7 absolute in FP32 there; below w = 7 the function's square-root edge at
+// |z| = 1 carries exp(-beta) >= 1e-6 and the formula is kept)
+constexpr int PH_NC = 9;
+__host__ __device__ constexpr int ph_degree(int w) { return w == 7 ? 8 : 7; }
+
 struct NodeDesc {
     int d;
     int64_t M;           // number of nodes (half set)
@@ -160,6 +167,11 @@ struct NodeDesc {
     const int32_t *crowd_bin;  // bin of each crowd slot
     const int16_t *pair_order; // per pass and node lane: column (q_a << 8 | q_b) or -1 (spreading)
     const int16_t *pair_order_i;  // the same for the interpolation (8-byte tile cells)
+    // FP32 3D interpolation, w >= 7: phi on each of the w stencil cells as a polynomial of degree
+    // ph_degree(w) in t = 2 u - 1 (u the node's offset, as above), monomial coefficients
+    // phc[q * PH_NC + k] (k = 0 lowest); phpoly = 0: evaluate phi by its formula instead
+    int phpoly;
+    float phc[NODE_MAXW * PH_NC];
 };
 
 // Deals the w*w stencil columns (q_a, q_b) of a node to passes of `lanes` lanes so that,
@@ -199,7 +211,6 @@ __host__ __device__ constexpr int default_bin_shape(bool fp64, int d, int w) {
     return d == 2 ? 1 : (fp64 ? (w >= 10 ? 2 : 1) : 3);
 }
 
-static constexpr int NODE_MAXW = 16;     // widest stencil
 // Lanes per node in the interpolation / spreading kernels: 16 when the w*w stencil columns
 // waste fewer lane slots in passes of 16 than in passes of 32 (w = 4, 6, 10..13, ...), else 32.
 __host__ __device__ constexpr int node_lanes(int w) {

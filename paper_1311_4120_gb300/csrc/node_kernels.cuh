@@ -932,6 +932,21 @@ __device__ __forceinline__ void es_phi_axis(float u, float beta, float (&f)[W]) 
     }
 }
 
+// The same w values from the plan's polynomials (NodeDesc::phc, w >= 7): Horner in t = 2u - 1 by
+// fused multiply-adds, the coefficients uniform across the warp (kernel-parameter operands).
+template <int W>
+__device__ __forceinline__ void es_phi_axis_poly(float u, const NodeDesc &nd, float (&f)[W]) {
+    constexpr int D = ph_degree(W);
+    const float t = fmaf(2.0f, u, -1.0f);
+#pragma unroll
+    for (int q = 0; q < W; q++) {
+        float acc = nd.phc[q * PH_NC + D];
+#pragma unroll
+        for (int k = D - 1; k >= 0; k--) acc = fmaf(acc, t, nd.phc[q * PH_NC + k]);
+        f[q] = (q == 0 && u >= 1.0f) ? 0.0f : acc;  // the edge rule of es_phi_axis
+    }
+}
+
 template <int W, int BS, bool EN>
 __global__ void __launch_bounds__(SUB_THREADS) interp_grp_kernel(NodeDesc nd, const __grid_constant__ CUtensorMap tmap,
                                                                 const float2 *__restrict__ G,
@@ -1027,9 +1042,15 @@ __global__ void __launch_bounds__(SUB_THREADS) interp_grp_kernel(NodeDesc nd, co
         }
         if (mine) {
             float fz[W], fy[W], fx[W];
-            es_phi_axis<W>(__int_as_float(r.y), beta, fz);
-            es_phi_axis<W>(__int_as_float(r.z), beta, fy);
-            es_phi_axis<W>(__int_as_float(r.w), beta, fx);
+            if (W >= 7 && nd.phpoly) {  // (uniform)
+                es_phi_axis_poly<W>(__int_as_float(r.y), nd, fz);
+                es_phi_axis_poly<W>(__int_as_float(r.z), nd, fy);
+                es_phi_axis_poly<W>(__int_as_float(r.w), nd, fx);
+            } else {
+                es_phi_axis<W>(__int_as_float(r.y), beta, fz);
+                es_phi_axis<W>(__int_as_float(r.z), beta, fy);
+                es_phi_axis<W>(__int_as_float(r.w), beta, fx);
+            }
             const float2 *pt = tile + ((r.x & 255) * T1 + ((r.x >> 8) & 255)) * T2 + ((r.x >> 16) & 255);
             float ar = 0.0f, ai = 0.0f;
 #pragma unroll(W <= 8 ? W : 1)

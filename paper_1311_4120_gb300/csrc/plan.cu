@@ -22,6 +22,7 @@ namespace nlint {
 
 static thread_local std::string g_err;
 
+static void fit_phi_poly(nlint_plan_s *p);
 static int fail(int code, const std::string &msg) {
     g_err = msg;
     return code;
@@ -208,6 +209,8 @@ struct nlint_plan_s {
     int B[3], T[3];
     int bin_shape = 1;
     unsigned fft_sched = 0;      // FFT pass schedules (nlint_params.fft_sched; FP32 only)
+    int phpoly = 0;              // FP32 3D, w >= 7: stencil-value polynomials (fit_phi_poly)
+    float phc[nlint::NODE_MAXW * nlint::PH_NC] = {};
     int64_t nsub = 0, nbins = 0, ngsub = 0;
     int ncrowd = 0;
     size_t bytes_crowd = 0;
@@ -434,6 +437,7 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
         return fail(NLINT_EUNSUPPORTED, "grid too small for this spreading width (n_fine < 4*(w/2+1)+2)");
     const double sig_eff = (double)p->n_fine / (double)p->N;
     p->beta = 0.97 * M_PI * (1.0 - 1.0 / (2.0 * sig_eff)) * w;  // ES shape parameter
+    fit_phi_poly(p);
 
     const int64_t nr_alg2 = p->d == 3 ? (p->prec == NLINT_FP32 ? 32 : 40) : (p->prec == NLINT_FP32 ? 48 : 64);
     p->nr = q.n_r > 0 ? q.n_r : (p->algorithm == 2 ? nr_alg2 : default_nr(p->d, p->N));
@@ -1137,6 +1141,64 @@ static int run_type2(nlint_plan_s *p, const void *rho, cudaStream_t s) {
     return NLINT_OK;
 }
 
+// Stencil values of the FP32 3D interpolation as polynomials (the piecewise-polynomial kernel
+// evaluation of Barnett, Magland and af Klinteberg): on stencil cell q the value
+// phi(z), z = (q + 1 - w/2) (2/w) - u (2/w) for the node offset u in [0, 1], is interpolated at
+// the D + 1 Chebyshev points of t = 2u - 1 in [-1, 1] (FP64), and the Chebyshev series turned
+// into monomial coefficients in t.  The fit is kept only if FP32 Horner evaluation by fused
+// multiply-adds stays within 1.5e-7 of phi (absolute; phi <= 1) on a fine grid of u; else the
+// kernels evaluate phi by its formula.
+static void fit_phi_poly(nlint_plan_s *p) {
+    p->phpoly = 0;
+    const int w = p->w;
+    if (p->prec != NLINT_FP32 || p->d != 3 || w < 7 || w > NODE_MAXW) return;
+    const int D = ph_degree(w), NC = D + 1;
+    const double beta = p->beta;
+    auto phi = [&](double z) {
+        const double t = 1.0 - z * z;
+        return t > 0.0 ? std::exp(-beta * z * z / (1.0 + std::sqrt(t))) : std::exp(-beta);
+    };
+    float coef[NODE_MAXW * PH_NC] = {};
+    for (int q = 0; q < w; q++) {
+        const double vc = (q + 1.0 - 0.5 * w) * (2.0 / w);
+        double val[PH_NC], cheb[PH_NC];
+        for (int k = 0; k < NC; k++) {
+            const double tk = std::cos(M_PI * (k + 0.5) / NC);
+            val[k] = phi(vc - (tk + 1.0) / w);
+        }
+        for (int j = 0; j < NC; j++) {
+            double a = 0.0;
+            for (int k = 0; k < NC; k++) a += val[k] * std::cos(j * M_PI * (k + 0.5) / NC);
+            cheb[j] = a * (j == 0 ? 1.0 : 2.0) / NC;
+        }
+        // monomials: T_0 = 1, T_1 = t, T_{j+1} = 2 t T_j - T_{j-1}, as coefficient vectors
+        double mono[PH_NC] = {}, Tm[PH_NC] = {}, T0[PH_NC] = {}, T1[PH_NC] = {};
+        T0[0] = 1.0;
+        T1[1] = 1.0;
+        for (int j = 0; j < NC; j++) {
+            const double *Tj = j == 0 ? T0 : T1;
+            for (int k = 0; k < NC; k++) mono[k] += cheb[j] * Tj[k];
+            if (j >= 1) {  // advance: Tm = 2 t T1 - T0
+                for (int k = 0; k < NC; k++) Tm[k] = (k > 0 ? 2.0 * T1[k - 1] : 0.0) - T0[k];
+                for (int k = 0; k < NC; k++) {
+                    T0[k] = T1[k];
+                    T1[k] = Tm[k];
+                }
+            }
+        }
+        for (int k = 0; k < NC; k++) coef[q * PH_NC + k] = (float)mono[k];
+        for (int i = 0; i <= 4000; i++) {  // FP32 Horner as the kernel evaluates it
+            const double u = i / 4000.0;
+            const float t = std::fmaf(2.0f, (float)u, -1.0f);
+            float acc = coef[q * PH_NC + D];
+            for (int k = D - 1; k >= 0; k--) acc = std::fmaf(acc, t, coef[q * PH_NC + k]);
+            if (!(std::fabs((double)acc - phi(vc - u * (2.0 / w))) <= 1.5e-7)) return;
+        }
+    }
+    std::memcpy(p->phc, coef, sizeof coef);
+    p->phpoly = 1;
+}
+
 static NodeDesc node_desc(nlint_plan_s *p) {
     NodeDesc nd;
     nd.d = p->d;
@@ -1167,6 +1229,8 @@ static NodeDesc node_desc(nlint_plan_s *p) {
     nd.crowd_bin = p->d_crowd_bin;
     nd.pair_order = p->d_pairs;
     nd.pair_order_i = p->d_pairs_i;
+    nd.phpoly = p->phpoly;
+    std::memcpy(nd.phc, p->phc, sizeof nd.phc);
     return nd;
 }
 
