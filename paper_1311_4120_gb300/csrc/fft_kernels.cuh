@@ -471,6 +471,10 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE, V>::THREADS, FftCfg<T, NF,
     constexpr int SES = MODE == 3 ? (int)sizeof(T) : (int)sizeof(T2);  // staged element bytes
     constexpr int EPC = 16 / SES;                                // elements per 16-byte copy
     int srows = 0;
+    // mode 4 with energy products also stages its density rows (N per column, floats) after the
+    // input and the transform buffer; they are waited for only before the epilogue
+    bool rstaged = false;
+    int roff = 0;  // byte offset of the staged density
     if constexpr (STAGE && !ROW) {
         const int64_t tiles = (P.I + CPT2 - 1) / CPT2;
         const int64_t i0 = (blockIdx.x % tiles) * CPT2;
@@ -489,7 +493,30 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE, V>::THREADS, FftCfg<T, NF,
                                  : "memory");
                 }
             }
-            asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            if constexpr (MODE == 4) {
+                const T *rho = reinterpret_cast<const T *>(P.rho);
+                constexpr int REPC = 16 / (int)sizeof(T);
+                rstaged = rho && P.I % REPC == 0 && P.out_so % REPC == 0 && P.out_sa % REPC == 0 &&
+                          CPT2 % REPC == 0 && (reinterpret_cast<uintptr_t>(rho) & 15) == 0;  // uniform
+                if (rstaged) {
+                    const int a = NF * B * (int)sizeof(T2), b = srows * CPT2 * SES;
+                    roff = ((a > b ? a : b) + 15) & ~15;
+                    const int64_t o0 = (blockIdx.x / tiles) * P.out_so + i0;
+                    constexpr int RCPR = CPT2 / REPC;
+                    for (int c = threadIdx.x; c < N * RCPR; c += blockDim.x) {
+                        const int row = c / RCPR, k = c - row * RCPR;
+                        if (i0 + (int64_t)k * REPC < P.I)
+                            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                                             dst0 + (uint32_t)(roff + (row * CPT2 + k * REPC) * (int)sizeof(T))),
+                                         "l"(rho + o0 + row * P.out_sa + (int64_t)k * REPC)
+                                         : "memory");
+                    }
+                    asm volatile("cp.async.commit_group;" ::: "memory");
+                }
+            }
+            if (rstaged) asm volatile("cp.async.wait_group 1;" ::: "memory");  // the input only
+            else asm volatile("cp.async.wait_group 0;" ::: "memory");
             __syncthreads();
         }
     }
@@ -678,9 +705,11 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE, V>::THREADS, FftCfg<T, NF,
     }
 
     if constexpr (MODE == 4) {  // x = Re z, y = Im z at the stored modes (+ energy)
+        if (rstaged) asm volatile("cp.async.wait_group 0;" ::: "memory");  // the staged density
         __syncthreads();
         const T *fac = reinterpret_cast<const T *>(P.fac);
         const T *rho = reinterpret_cast<const T *>(P.rho);
+        const T *rs = reinterpret_cast<const T *>(smem_raw + roff);
 #pragma unroll 4
         for (int a = t; a < N; a += TPL) {
             const int m = a - h;
@@ -691,14 +720,14 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE, V>::THREADS, FftCfg<T, NF,
                 T val = z.x * f * io.bfac;
                 if (P.accum) val += reinterpret_cast<const T *>(vout)[idx];
                 reinterpret_cast<T *>(vout)[idx] = val;
-                if (rho) eacc.add(val, rho[idx]);
+                if (rho) eacc.add(val, rstaged ? rs[a * (2 * B) + ll] : rho[idx]);
             }
             if (io2.valid) {
                 const int64_t idx = io2.out_base + a * io2.out_st;
                 T val = z.y * f * io2.bfac;
                 if (P.accum) val += reinterpret_cast<const T *>(vout)[idx];
                 reinterpret_cast<T *>(vout)[idx] = val;
-                if (rho) eacc.add(val, rho[idx]);
+                if (rho) eacc.add(val, rstaged ? rs[a * (2 * B) + ll + B] : rho[idx]);
             }
         }
     }

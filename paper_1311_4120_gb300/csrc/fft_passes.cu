@@ -109,6 +109,7 @@ size_t pass_smem(const PassDesc &p, int prec) {
         const size_t es = mode == 3 ? cs / 2 : cs;
         const size_t st = (size_t)fft_stage_rows(mode, p.n, p.N, p.win) * 2 * p.B * es;
         if (st > s) s = st;
+        if (mode == 4) s = ((s + 15) & ~(size_t)15) + (size_t)p.N * 2 * p.B * (cs / 2);  // + density rows
     }
     return s > 64 * sizeof(double) ? s : 64 * sizeof(double);  // >= the energy scratch
 }
