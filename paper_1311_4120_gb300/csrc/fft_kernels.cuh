@@ -497,11 +497,14 @@ __global__ void __launch_bounds__(FftCfg<T, NF, MODE, V>::THREADS, FftCfg<T, NF,
             if constexpr (MODE == 4) {
                 const T *rho = reinterpret_cast<const T *>(P.rho);
                 constexpr int REPC = 16 / (int)sizeof(T);
+                const int a = NF * B * (int)sizeof(T2), b = srows * CPT2 * SES;
+                roff = ((a > b ? a : b) + 15) & ~15;
+                uint32_t dsm;  // the launch's dynamic shared memory: room for the density rows?
+                asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dsm));
                 rstaged = rho && P.I % REPC == 0 && P.out_so % REPC == 0 && P.out_sa % REPC == 0 &&
-                          CPT2 % REPC == 0 && (reinterpret_cast<uintptr_t>(rho) & 15) == 0;  // uniform
+                          CPT2 % REPC == 0 && (reinterpret_cast<uintptr_t>(rho) & 15) == 0 &&
+                          (uint32_t)roff + (uint32_t)(N * CPT2 * (int)sizeof(T)) <= dsm;  // uniform
                 if (rstaged) {
-                    const int a = NF * B * (int)sizeof(T2), b = srows * CPT2 * SES;
-                    roff = ((a > b ? a : b) + 15) & ~15;
                     const int64_t o0 = (blockIdx.x / tiles) * P.out_so + i0;
                     constexpr int RCPR = CPT2 / REPC;
                     for (int c = threadIdx.x; c < N * RCPR; c += blockDim.x) {

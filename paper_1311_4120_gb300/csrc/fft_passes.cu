@@ -109,7 +109,9 @@ size_t pass_smem(const PassDesc &p, int prec) {
         const size_t es = mode == 3 ? cs / 2 : cs;
         const size_t st = (size_t)fft_stage_rows(mode, p.n, p.N, p.win) * 2 * p.B * es;
         if (st > s) s = st;
-        if (mode == 4) s = ((s + 15) & ~(size_t)15) + (size_t)p.N * 2 * p.B * (cs / 2);  // + density rows
+        // + the density rows of mode 4 when they fit (the kernel checks its shared memory)
+        const size_t with_rho = ((s + 15) & ~(size_t)15) + (size_t)p.N * 2 * p.B * (cs / 2);
+        if (mode == 4 && with_rho <= 200 * 1024) s = with_rho;
     }
     return s > 64 * sizeof(double) ? s : 64 * sizeof(double);  // >= the energy scratch
 }
