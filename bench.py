@@ -563,9 +563,9 @@ def run_ours(args, rank, world, local_rank):
         plan.eval_energy(rho, lam=wl.lam, out=u, E_out=E)
     torch.cuda.synchronize()
 
-    # ---- timed region: K steps, L2 flushed before each, per-step CUDA events on the stream
-    plan.set_stage_timing(True)
-    stage_ms = {}
+    # ---- timed region: K steps, L2 flushed before each, per-step CUDA events on the stream; no
+    # events between the stages of an evaluation (they would serialise its dependent launches)
+    # and no host synchronisation inside the loop
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     launches0 = plan.launch_count()
@@ -580,15 +580,25 @@ def run_ours(args, rank, world, local_rank):
             starts[k].record(stream)
             plan.eval_energy(rho, lam=wl.lam, out=u, E_out=E)
             ends[k].record(stream)
-            for name, ms in plan.stage_times():
-                stage_ms.setdefault(name, []).append(ms)
         torch.cuda.synchronize()
         barrier()
         t_wall = time.perf_counter() - t_wall0
     torch.cuda.nvtx.range_pop()
     launches = plan.launch_count() - launches0
-    plan.set_stage_timing(False)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+
+    # ---- the same K steps again with CUDA events between the stages (on the evaluation stream),
+    # for the per-kernel durations of the stage split and the roofline
+    plan.set_stage_timing(True)
+    stage_ms = {}
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        plan.eval_energy(rho, lam=wl.lam, out=u, E_out=E)
+        for name, ms in plan.stage_times():
+            stage_ms.setdefault(name, []).append(ms)
+    torch.cuda.synchronize()
+    plan.set_stage_timing(False)
     t_dev = sum(step_ms) / 1e3
     (t_max,) = max_over_ranks([t_dev], dev)
     points = wl.n_points * args.steps * world

@@ -32,6 +32,29 @@ __device__ __forceinline__ float2 cmuli(float2 a, int s) { return make_float2(-s
 __device__ __forceinline__ double2 cmuli(double2 a, int s) { return make_double2(-s * a.y, s * a.x); }
 template <typename T2> __device__ __forceinline__ T2 czero() { T2 r; r.x = 0; r.y = 0; return r; }
 
+// Programmatic dependent launch.  A kernel launched by launch_pdl may be scheduled while the
+// kernel before it on the stream is still finishing: it calls pdl_wait() first, which returns
+// once that kernel has completed and its writes are visible (so it reads and writes nothing
+// earlier), then pdl_trigger(), which lets the kernel after it be scheduled in turn.  Only the
+// launch latency and the CTA scheduling overlap; the stream order of the data is unchanged.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // Compile-time loop: f(IntC<B>{}), f(IntC<B+1>{}), ..., f(IntC<E-1>{}).
 template <int V> struct IntC { static constexpr int value = V; };
 template <int B, int E, typename F>

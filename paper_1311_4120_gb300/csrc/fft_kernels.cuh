@@ -347,6 +347,8 @@ struct LineIO {
 template <typename T, int NF, int MODE, int V>
 __global__ void __launch_bounds__(FftCfg<T, NF, MODE, V>::THREADS, FftCfg<T, NF, MODE, V>::MIN_BLOCKS) fft_pass_kernel(
     PassDesc P, const void *__restrict__ vin, void *__restrict__ vout, const cx_t<T> *__restrict__ tw) {
+    pdl_wait();  // (launched by launch_pdl)
+    pdl_trigger();
     using T2 = cx_t<T>;
     using C = FftCfg<T, NF, MODE, V>;
     constexpr bool ROW = fft_is_row(MODE);
@@ -809,9 +811,9 @@ cudaError_t launch_nf(const PassDesc &p, const void *in, void *out, const void *
     if (e != cudaSuccess) return e;
     const int64_t nb = pass_blocks(p, fft_is_row(MODE));
     if (nb == 0) return cudaSuccess;
-    fft_pass_kernel<T, NF, MODE, V><<<(unsigned)nb, FftCfg<T, NF, MODE, V>::THREADS, smem, s>>>(
-        p, in, out, reinterpret_cast<const cx_t<T> *>(tw));
-    return cudaGetLastError();
+    e = launch_pdl(fft_pass_kernel<T, NF, MODE, V>, dim3((unsigned)nb), dim3(FftCfg<T, NF, MODE, V>::THREADS),
+                   smem, s, p, in, out, reinterpret_cast<const cx_t<T> *>(tw));
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 // Schedule V of every supported length; for V = 1 a length without a second schedule runs

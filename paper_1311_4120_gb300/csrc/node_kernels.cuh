@@ -389,6 +389,8 @@ __global__ void __launch_bounds__(SUB_THREADS) interp_sub_kernel(NodeDesc nd,
                                                                 cx_t<T> *__restrict__ c_out,
                                                                 int apply_W,
                                                                 double2 *__restrict__ epart) {
+    pdl_wait();  // (launched by launch_pdl)
+    pdl_trigger();
     using T2 = cx_t<T>;
     using G_ = Geo<T, D, W, BS>;
     constexpr int PASSES = G_::PASSES, L = (D == 3) ? W : 1, PLANE = G_::PLANE;
@@ -477,6 +479,8 @@ template <typename T, int D, int W, int BS>
 __global__ void __launch_bounds__(SUB_THREADS) spread_sub_kernel(NodeDesc nd,
                                                                 const cx_t<T> *__restrict__ c_in,
                                                                 cx_t<T> *__restrict__ H) {
+    pdl_wait();  // (launched by launch_pdl)
+    pdl_trigger();
     using T2 = cx_t<T>;
     using G_ = Geo<T, D, W, BS>;
     using F = FixAcc<T>;
@@ -694,6 +698,8 @@ template <int D, int W, int BS, bool EN>
 __global__ void __launch_bounds__(SUB_THREADS) interp_f32_kernel(NodeDesc nd, const float2 *__restrict__ G,
                                                                 float2 *__restrict__ c_out, int apply_W,
                                                                 double2 *__restrict__ epart) {
+    pdl_wait();  // (launched by launch_pdl)
+    pdl_trigger();
     using G_ = Geo<float, D, W, BS>;
     using LN = F32Lane<D, W, BS>;
     constexpr int PASSES = G_::PASSES, L = (D == 3) ? W : 1, PLANE = G_::PLANE;
@@ -952,6 +958,8 @@ __global__ void __launch_bounds__(SUB_THREADS) interp_grp_kernel(NodeDesc nd, co
                                                                 const float2 *__restrict__ G,
                                                                 float2 *__restrict__ c_out, int apply_W,
                                                                 double2 *__restrict__ epart) {
+    pdl_wait();  // (launched by launch_pdl)
+    pdl_trigger();
     using G_ = Geo<float, 3, W, BS>;
     constexpr int T0 = G_::T0, T1 = G_::T1, T2 = G_::T2, RP = T1 * T2, NW = SUB_THREADS / 32;
     constexpr unsigned TILE_BYTES = (unsigned)(T0 * RP) * 8u;
@@ -1095,6 +1103,8 @@ __global__ void __launch_bounds__(SUB_THREADS) interp_grp_kernel(NodeDesc nd, co
 template <int D, int W, int BS>
 __global__ void __launch_bounds__(SUB_THREADS, (Geo<float, D, W, BS>::SPREAD_MINB)) spread_f32_kernel(NodeDesc nd, const float2 *__restrict__ c_in,
                                                                 float2 *__restrict__ H) {
+    pdl_wait();  // (launched by launch_pdl)
+    pdl_trigger();
     using G_ = Geo<float, D, W, BS>;
     using LN = F32Lane<D, W, BS>;
     using F = FixAcc<float>;
@@ -1271,42 +1281,48 @@ static cudaError_t launch_interp_w(const NodeDesc &nd, const void *G, void *c_ou
             cudaError_t e = cudaFuncSetAttribute(interp_grp_kernel<W, BS, true>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
             if (e != cudaSuccess) return e;
-            interp_grp_kernel<W, BS, true><<<ggrid, SUB_THREADS, gsm, s>>>(
-                nd, tm, (const float2 *)G, (float2 *)c_out, apply_W, epart);
+            e = launch_pdl(interp_grp_kernel<W, BS, true>, dim3(ggrid), dim3(SUB_THREADS), gsm, s, nd, tm,
+                           (const float2 *)G, (float2 *)c_out, apply_W, epart);
+            if (e != cudaSuccess) return e;
         } else {
             cudaError_t e = cudaFuncSetAttribute(interp_grp_kernel<W, BS, false>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gsm);
             if (e != cudaSuccess) return e;
-            interp_grp_kernel<W, BS, false><<<ggrid, SUB_THREADS, gsm, s>>>(
-                nd, tm, (const float2 *)G, (float2 *)c_out, apply_W, nullptr);
+            e = launch_pdl(interp_grp_kernel<W, BS, false>, dim3(ggrid), dim3(SUB_THREADS), gsm, s, nd, tm,
+                           (const float2 *)G, (float2 *)c_out, apply_W, (double2 *)nullptr);
+            if (e != cudaSuccess) return e;
         }
     } else if constexpr (sizeof(T) == 4) {
         if (epart) {
             cudaError_t e = cudaFuncSetAttribute(interp_f32_kernel<D, W, BS, true>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
-            interp_f32_kernel<D, W, BS, true><<<grid, SUB_THREADS, smem, s>>>(
-                nd, (const float2 *)G, (float2 *)c_out, apply_W, epart);
+            e = launch_pdl(interp_f32_kernel<D, W, BS, true>, dim3(grid), dim3(SUB_THREADS), smem, s, nd,
+                           (const float2 *)G, (float2 *)c_out, apply_W, epart);
+            if (e != cudaSuccess) return e;
         } else {
             cudaError_t e = cudaFuncSetAttribute(interp_f32_kernel<D, W, BS, false>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
-            interp_f32_kernel<D, W, BS, false><<<grid, SUB_THREADS, smem, s>>>(
-                nd, (const float2 *)G, (float2 *)c_out, apply_W, nullptr);
+            e = launch_pdl(interp_f32_kernel<D, W, BS, false>, dim3(grid), dim3(SUB_THREADS), smem, s, nd,
+                           (const float2 *)G, (float2 *)c_out, apply_W, (double2 *)nullptr);
+            if (e != cudaSuccess) return e;
         }
     } else {
         if (epart) {
             cudaError_t e = cudaFuncSetAttribute(interp_sub_kernel<T, D, W, BS, true>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
-            interp_sub_kernel<T, D, W, BS, true><<<grid, SUB_THREADS, smem, s>>>(
-                nd, (const cx_t<T> *)G, (cx_t<T> *)c_out, apply_W, epart);
+            e = launch_pdl(interp_sub_kernel<T, D, W, BS, true>, dim3(grid), dim3(SUB_THREADS), smem, s, nd,
+                           (const cx_t<T> *)G, (cx_t<T> *)c_out, apply_W, epart);
+            if (e != cudaSuccess) return e;
         } else {
             cudaError_t e = cudaFuncSetAttribute(interp_sub_kernel<T, D, W, BS, false>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
-            interp_sub_kernel<T, D, W, BS, false><<<grid, SUB_THREADS, smem, s>>>(
-                nd, (const cx_t<T> *)G, (cx_t<T> *)c_out, apply_W, nullptr);
+            e = launch_pdl(interp_sub_kernel<T, D, W, BS, false>, dim3(grid), dim3(SUB_THREADS), smem, s, nd,
+                           (const cx_t<T> *)G, (cx_t<T> *)c_out, apply_W, (double2 *)nullptr);
+            if (e != cudaSuccess) return e;
         }
     }
     return cudaGetLastError();
@@ -1320,13 +1336,16 @@ static cudaError_t launch_spread_w(const NodeDesc &nd, const void *c_in, void *H
         cudaError_t e = cudaFuncSetAttribute(spread_f32_kernel<D, W, BS>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        spread_f32_kernel<D, W, BS><<<grid, SUB_THREADS, smem, s>>>(nd, (const float2 *)c_in, (float2 *)H);
+        e = launch_pdl(spread_f32_kernel<D, W, BS>, dim3(grid), dim3(SUB_THREADS), smem, s, nd,
+                       (const float2 *)c_in, (float2 *)H);
+        if (e != cudaSuccess) return e;
     } else {
         cudaError_t e = cudaFuncSetAttribute(spread_sub_kernel<T, D, W, BS>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        spread_sub_kernel<T, D, W, BS><<<grid, SUB_THREADS, smem, s>>>(
-            nd, (const cx_t<T> *)c_in, (cx_t<T> *)H);
+        e = launch_pdl(spread_sub_kernel<T, D, W, BS>, dim3(grid), dim3(SUB_THREADS), smem, s, nd,
+                       (const cx_t<T> *)c_in, (cx_t<T> *)H);
+        if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }
@@ -1334,6 +1353,8 @@ static cudaError_t launch_spread_w(const NodeDesc &nd, const void *c_in, void *H
 // Adds the FP64 tiles of the crowded bins into the extended spread grid (one CTA per tile).
 template <typename T, int D>
 __global__ void __launch_bounds__(SUB_THREADS) crowd_merge_kernel(NodeDesc nd, cx_t<T> *__restrict__ H) {
+    pdl_wait();  // (launched by launch_pdl)
+    pdl_trigger();
     const int T1 = nd.T[1], T2n = (D == 3) ? nd.T[2] : 1;
     const int ncell = nd.T[0] * T1 * T2n;
     const int slot = blockIdx.x;
@@ -1358,8 +1379,9 @@ __global__ void __launch_bounds__(SUB_THREADS) crowd_merge_kernel(NodeDesc nd, c
 template <typename T, int D>
 cudaError_t launch_crowd_merge_d(const NodeDesc &nd, void *H, cudaStream_t s) {
     if (nd.ncrowd == 0) return cudaSuccess;
-    crowd_merge_kernel<T, D><<<(unsigned)nd.ncrowd, SUB_THREADS, 0, s>>>(nd, (cx_t<T> *)H);
-    return cudaGetLastError();
+    const cudaError_t e = launch_pdl(crowd_merge_kernel<T, D>, dim3((unsigned)nd.ncrowd), dim3(SUB_THREADS),
+                                     0, s, nd, (cx_t<T> *)H);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 #define NLINT_W_SWITCH(CALL)                                                   \

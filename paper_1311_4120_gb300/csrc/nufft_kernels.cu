@@ -74,6 +74,8 @@ __global__ void __launch_bounds__(256) energy_partials_kernel(int64_t count, con
 __global__ void __launch_bounds__(32) energy_fold_kernel(const double2 *__restrict__ partials,
                                                          int nparts, int per,
                                                          double2 *__restrict__ out) {
+    pdl_wait();  // (launched by launch_pdl)
+    pdl_trigger();
     KSum acc;
     acc.init();
     const int a = blockIdx.x * per, e = min(a + per, nparts);
@@ -85,6 +87,8 @@ __global__ void __launch_bounds__(32) energy_fold_kernel(const double2 *__restri
 __global__ void __launch_bounds__(1024) energy_final_kernel(const double2 *__restrict__ partials,
                                                             int nparts, double scale,
                                                             double *__restrict__ E) {
+    pdl_wait();  // (launched by launch_pdl)
+    pdl_trigger();
     __shared__ double sh[2 * 32];
     KSum acc;
     acc.init();
@@ -216,15 +220,17 @@ int energy_final_kernels(int nparts) { return nparts <= FOLD_DIRECT ? 1 : 2; }
 cudaError_t launch_energy_final(const double2 *partials, int nparts, double scale, double *E,
                                 cudaStream_t s) {
     if (nparts <= FOLD_DIRECT) {
-        energy_final_kernel<<<1, FOLD_DIRECT, 0, s>>>(partials, nparts, scale, E);
-        return cudaGetLastError();
+        const cudaError_t e = launch_pdl(energy_final_kernel, dim3(1), dim3(FOLD_DIRECT), 0, s, partials,
+                                         nparts, scale, E);
+        return e != cudaSuccess ? e : cudaGetLastError();
     }
     const int per = (nparts + FOLD_WARPS - 1) / FOLD_WARPS;
     const int g = (nparts + per - 1) / per;  // <= FOLD_WARPS
     double2 *mid = const_cast<double2 *>(partials) + nparts;
-    energy_fold_kernel<<<g, 32, 0, s>>>(partials, nparts, per, mid);
-    energy_final_kernel<<<1, FOLD_WARPS, 0, s>>>(mid, g, scale, E);
-    return cudaGetLastError();
+    cudaError_t e = launch_pdl(energy_fold_kernel, dim3(g), dim3(32), 0, s, partials, nparts, per, mid);
+    if (e != cudaSuccess) return e;
+    e = launch_pdl(energy_final_kernel, dim3(1), dim3(FOLD_WARPS), 0, s, (const double2 *)mid, g, scale, E);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 #define NLINT_INST(T)                                                                              \
