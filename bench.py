@@ -45,14 +45,14 @@ TOL = 1e-5                          # stated relative L-inf tolerance of the FP3
 # Measured with ncu on the 256^3 FP32 workload (one launch of each kernel, one pass of
 # dram__bytes_read.sum and dram__bytes_write.sum).
 TRAFFIC = {
-    "interp": {"bytes": 461.8e6, "src": "cef2e97f20c5a2db"},
-    "spread": {"bytes": 658.7e6, "src": "cef2e97f20c5a2db"},
-    "fwd_fft_z": {"bytes": 155.2e6, "src": "b0aea8d08f1a4998"},
-    "fwd_fft_y": {"bytes": 341.0e6, "src": "b0aea8d08f1a4998"},
-    "fwd_fft_x": {"bytes": 481.6e6, "src": "b0aea8d08f1a4998"},
-    "inv_fft_x": {"bytes": 530.2e6, "src": "b0aea8d08f1a4998"},
-    "inv_fft_y": {"bytes": 370.0e6, "src": "b0aea8d08f1a4998"},
-    "inv_fft_z": {"bytes": 254.9e6, "src": "b0aea8d08f1a4998"},
+    "interp": {"bytes": 460.9e6, "src": "53af5c4351994734"},
+    "spread": {"bytes": 659.0e6, "src": "53af5c4351994734"},
+    "fwd_fft_z": {"bytes": 155.3e6, "src": "1e5ea1bf908190b9"},
+    "fwd_fft_y": {"bytes": 340.9e6, "src": "1e5ea1bf908190b9"},
+    "fwd_fft_x": {"bytes": 482.3e6, "src": "1e5ea1bf908190b9"},
+    "inv_fft_x": {"bytes": 530.4e6, "src": "1e5ea1bf908190b9"},
+    "inv_fft_y": {"bytes": 370.2e6, "src": "1e5ea1bf908190b9"},
+    "inv_fft_z": {"bytes": 255.2e6, "src": "1e5ea1bf908190b9"},
 }
 
 

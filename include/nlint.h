@@ -233,7 +233,7 @@ int nlint_stage_times(nlint_plan plan, float *ms, const char **names, int max_st
  * precision and dimension whose tile fits in shared memory (evaluation time by CUDA events),
  * (3) for that width and shape the fastest subproblem size (max_sub) among 256..2048, and (4)
  * for FP32 plans the FFT pass schedules (nlint_params.fft_sched), one pass class at a time,
- * each kept when it measured faster.  *out = *in with w, bin_shape, max_sub, fft_sched and the
+ * each kept when the evaluation's FFT stages (its stage events) measured at least 1 % faster.  *out = *in with w, bin_shape, max_sub, fft_sched and the
  * precision (from tol when in->precision is -1) filled in; rep (may be NULL) reports the
  * choice, its measured error and time.  The choice is cached as one JSON object per line in
  * cache_path (NULL: $NLINT_TUNE_CACHE; neither: no cache); a cached key skips measurement.

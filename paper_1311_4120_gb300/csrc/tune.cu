@@ -13,7 +13,8 @@
 // 8x16x16, 16^3; 3D FP64 8^3, 4x8x8; the shapes whose tile fits in shared memory at w), then,
 // for the fastest width and shape, the subproblem sizes (nodes per CTA), and keeps the fastest;
 // then (FP32) the FFT pass schedules, one pass class at a time (coordinate descent over the
-// four bits of nlint_params.fft_sched), each kept when it measured faster.
+// four bits of nlint_params.fft_sched), each kept when the evaluation's FFT stages (timed by the
+// plan's stage events) measured at least 1 % faster.
 // Cache: one JSON object per line in `cache_path` (or $NLINT_TUNE_CACHE), keyed by the plan's
 // geometry, kernel, precision and tolerance; a hit skips all measurement.
 #include <algorithm>
@@ -214,6 +215,45 @@ int time_plan(nlint_plan p, int prec, const std::vector<double> &rho, int reps, 
     return NLINT_OK;
 }
 
+// median of `reps` evaluations of plan p of the summed times of its FFT stages (the stage events
+// of nlint_stage_times whose names name an FFT pass): the part of an evaluation that the FFT
+// pass schedules change, without the node kernels' larger share and its variation
+int time_fft_stages(nlint_plan p, int prec, const std::vector<double> &rho, int reps, cudaStream_t s,
+                    double &ms) {
+    const size_t cnt = rho.size(), es = prec == NLINT_FP32 ? 4 : 8;
+    Bufs b;
+    if (cudaMalloc(&b.rho, cnt * es) != cudaSuccess || cudaMalloc(&b.u, cnt * es) != cudaSuccess)
+        return tfail(NLINT_ENOMEM, "autotune: device allocation failed");
+    cudaError_t ce;
+    if (prec == NLINT_FP32) {
+        std::vector<float> r(rho.begin(), rho.end());
+        ce = cudaMemcpy(b.rho, r.data(), cnt * 4, cudaMemcpyHostToDevice);
+    } else {
+        ce = cudaMemcpy(b.rho, rho.data(), cnt * 8, cudaMemcpyHostToDevice);
+    }
+    if (ce != cudaSuccess) return tfail(NLINT_ECUDA, "autotune: copy failed");
+    int rc = nlint_eval(p, b.rho, b.u, s);  // warm-up
+    if (rc) return rc;
+    if ((rc = nlint_set_stage_timing(p, 1))) return rc;
+    std::vector<double> t;
+    for (int r = 0; r < reps && rc == NLINT_OK; r++) {
+        rc = nlint_eval(p, b.rho, b.u, s);
+        float st[32];
+        const char *nm[32];
+        int k = 0;
+        if (rc == NLINT_OK) rc = nlint_stage_times(p, st, nm, 32, &k);
+        double sum = 0.0;
+        for (int i = 0; i < k && rc == NLINT_OK; i++)
+            if (std::strstr(nm[i], "fft") || std::strstr(nm[i], "dual")) sum += st[i];
+        t.push_back(sum);
+    }
+    nlint_set_stage_timing(p, 0);
+    if (rc) return rc;
+    std::sort(t.begin(), t.end());
+    ms = t.empty() ? 0.0 : t[t.size() / 2];
+    return NLINT_OK;
+}
+
 }  // namespace
 
 extern "C" int nlint_autotune(const nlint_params *in, double tol, const char *cache_path,
@@ -362,17 +402,38 @@ extern "C" int nlint_autotune(const nlint_params *in, double tol, const char *ca
             best_sub = cs;
         }
     }
-    // FFT pass schedules (FP32): one pass class at a time, kept when faster
+    // FFT pass schedules (FP32): one pass class at a time, kept when the evaluation's FFT stages
+    // measured at least 1 % faster (their own stage events: the schedules change nothing else)
     int best_fs = 0;
     if (!f64) {
+        auto fft_ms = [&](int fs, double &t) -> int {
+            nlint_params cp = p;
+            cp.w = best_w;
+            cp.max_sub = best_sub;
+            cp.bin_shape = best_bs;
+            cp.fft_sched = fs;
+            nlint_plan pl = nullptr;
+            const int crc = nlint_plan_create_ex(&cp, &pl);
+            if (crc) return crc;
+            const int trc = time_fft_stages(pl, p.precision, rho, 9, s, t);
+            nlint_plan_destroy(pl);
+            return trc;
+        };
+        double base = 0.0;
+        rc = fft_ms(0, base);
+        if (rc) return rc;
         for (int bit = 0; bit < 4; bit++) {
             double t = 0.0;
-            rc = time_candidate(best_w, best_bs, best_sub, t, best_fs | (1 << bit));
+            rc = fft_ms(best_fs | (1 << bit), t);
             if (rc) return rc;
-            if (t < best_ms) {
-                best_ms = t;
+            if (t < 0.99 * base) {
+                base = t;
                 best_fs |= 1 << bit;
             }
+        }
+        if (best_fs) {  // the evaluation time of the final choice
+            rc = time_candidate(best_w, best_bs, best_sub, best_ms, best_fs);
+            if (rc) return rc;
         }
     }
     p.w = best_w;
