@@ -96,10 +96,11 @@ typedef struct nlint_params {
      * 16x16.  A shape whose tile does not fit in shared memory at the plan's width is
      * NLINT_EUNSUPPORTED (automatic: the smallest shape is taken instead).                  */
     int bin_shape;
-    /* FFT pass schedules (FP32 plans; ignored in FP64): bit set = the second values-per-thread
-     * choice (and with it threads per line and lines per CTA) for, bit 0: the column passes,
-     * 1: the row passes, 2: the first inverse row pass (fold), 3: the real-data column passes
-     * along the slowest axis; lines of 3 * 2^a points have one schedule.  0..15; 0 = default. */
+    /* FFT pass schedules (FP32 plans; ignored in FP64): bit set = the two-stage radix schedule
+     * (radix 2^ceil(a/2) x 2^floor(a/2) on lines of 2^a >= 128 points, one exchange through
+     * shared memory per line instead of two) for, bit 0: the column passes, 1: the row passes,
+     * 2: the first inverse row pass (fold), 3: the real-data column passes along the slowest
+     * axis; other lines have one schedule.  0..15; 0 = default.                              */
     int fft_sched;
 } nlint_params;
 
@@ -233,9 +234,10 @@ int nlint_stage_times(nlint_plan plan, float *ms, const char **names, int max_st
  * precision and dimension whose tile fits in shared memory (evaluation time by CUDA events),
  * (3) for that width and shape the fastest subproblem size (max_sub) among 256..2048, and (4)
  * for FP32 plans the FFT pass schedules (nlint_params.fft_sched), one pass class at a time,
- * each kept when the evaluation's FFT stages (its stage events) measured at least 1 % faster.  *out = *in with w, bin_shape, max_sub, fft_sched and the
- * precision (from tol when in->precision is -1) filled in; rep (may be NULL) reports the
- * choice, its measured error and time.  The choice is cached as one JSON object per line in
+ * each kept when the evaluation's FFT stages (its stage events) measured at least 1 % faster.
+ * *out = *in with w, bin_shape, max_sub, fft_sched and the precision (from tol when
+ * in->precision is -1) filled in; rep (may be NULL) reports the choice, its measured error
+ * and time.  The choice is cached as one JSON object per line in
  * cache_path (NULL: $NLINT_TUNE_CACHE; neither: no cache); a cached key skips measurement.
  * Synchronous; creates and destroys several plans (NLINT_ENOMEM etc. pass through). */
 typedef struct nlint_tune_report {

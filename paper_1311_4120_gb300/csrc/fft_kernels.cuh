@@ -69,9 +69,8 @@ __host__ __device__ constexpr int fft_vpt_small(int mode) {
 // each thread holds the larger radix's worth of values (16 or 32).  3 * 2^a lines, shorter lines
 // and modes 5-7 have schedule 0 only.
 __host__ __device__ constexpr bool fft_has_alt(int n, int mode) { return fft_two_stage(n, 1) && mode <= 4; }
-__host__ __device__ constexpr int fft_vpt_alt(int n, int mode) { return fft_radix(n, 0, 1) + 0 * mode; }
 __host__ __device__ constexpr int fft_vpt(int n, int mode = 0, int v = 0) {
-    return (v && fft_has_alt(n, mode)) ? fft_vpt_alt(n, mode)
+    return (v && fft_has_alt(n, mode)) ? fft_radix(n, 0, 1)
                                        : (fft_has3(n) ? 24 : (n <= 512 ? fft_vpt_small(mode) : 32));
 }
 __host__ __device__ constexpr int fft_vpt_ref(int n) { return fft_has3(n) ? 24 : (n <= 512 ? 16 : 32); }
