@@ -1,5 +1,5 @@
-"""Every FFT pass schedule (nlint_params.fft_sched: the second values-per-thread choice of the
-column, row, fold and packed real-data passes, FP32) computes the same operator: each
+"""Every FFT pass schedule (nlint_params.fft_sched: the two-stage radix schedule of the column,
+row, fold and packed real-data passes, FP32) computes the same operator: each
 schedule mask agrees with the default one to FP32 rounding and with the oracle (eqs. 3.2 and
 3.7 by Section 2's NUFFT at its FP32 reference setting) to the FP32 tolerance, on grids whose
 fine lines have two schedules (2^a points) and on grids whose lines have one (3 * 2^a), for
