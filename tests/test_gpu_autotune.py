@@ -33,6 +33,8 @@ def test_autotune_meets_tolerance_and_caches(pkg, tmp_path):
     assert rep["bin_shape"] in (1, 3, 4)  # the FP32 3D shapes
     assert tuned.w == rep["w"] and tuned.max_sub == rep["max_sub"]
     assert tuned.bin_shape == rep["bin_shape"]
+    # the FFT pass schedules: a mask of the four pass classes, carried into the tuned parameters
+    assert 0 <= rep["fft_sched"] <= 15 and tuned.fft_sched == rep["fft_sched"]
     # the other width timed, if any, is a neighbour that also meets the tolerance
     assert rep["w_alt"] == 0 or (abs(rep["w_alt"] - rep["w"]) == 1 and rep["err_alt"] <= 0.5e-5)
     # a tighter tolerance: the chosen width (the smallest qualifying one or the next, whichever
