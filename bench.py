@@ -47,12 +47,12 @@ TOL = 1e-5                          # stated relative L-inf tolerance of the FP3
 TRAFFIC = {
     "interp": {"bytes": 460.9e6, "src": "53af5c4351994734"},
     "spread": {"bytes": 659.0e6, "src": "53af5c4351994734"},
-    "fwd_fft_z": {"bytes": 155.3e6, "src": "1e5ea1bf908190b9"},
-    "fwd_fft_y": {"bytes": 340.9e6, "src": "1e5ea1bf908190b9"},
-    "fwd_fft_x": {"bytes": 482.3e6, "src": "1e5ea1bf908190b9"},
-    "inv_fft_x": {"bytes": 530.4e6, "src": "1e5ea1bf908190b9"},
-    "inv_fft_y": {"bytes": 370.2e6, "src": "1e5ea1bf908190b9"},
-    "inv_fft_z": {"bytes": 255.2e6, "src": "1e5ea1bf908190b9"},
+    "fwd_fft_z": {"bytes": 155.2e6, "src": "13173716e1349e52"},
+    "fwd_fft_y": {"bytes": 341.2e6, "src": "13173716e1349e52"},
+    "fwd_fft_x": {"bytes": 481.6e6, "src": "13173716e1349e52"},
+    "inv_fft_x": {"bytes": 530.2e6, "src": "13173716e1349e52"},
+    "inv_fft_y": {"bytes": 370.4e6, "src": "13173716e1349e52"},
+    "inv_fft_z": {"bytes": 254.8e6, "src": "13173716e1349e52"},
 }
 
 
