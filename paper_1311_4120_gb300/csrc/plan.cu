@@ -676,14 +676,16 @@ static int build_plan(const nlint_params *in, nlint_plan_s *p) {
     p->nbins = (int64_t)bins.size();
     p->ncrowd = (int)crowd_bin.size();
     if (p->nsub > (int64_t)INT32_MAX) return fail(NLINT_EUNSUPPORTED, "too many subproblems");
-    // the interpolation's subproblems: runs of at most max_sub / 32 half-group pairs of one bin
+    // the interpolation's subproblems: runs of at most max_sub / 16 half-group pairs of one bin
+    // (up to 2 max_sub nodes: a crowded bin's tile is staged half as often as the spreading's;
+    // 256^3 FP32: 2.17 -> 2.14 ms per evaluation against max_sub / 32)
     std::vector<int32_t> grp;
     std::vector<int4> gsubs;
     if (grouped) {
         grp.resize(gsize.size() + 1);
         grp[0] = 0;
         for (size_t g = 0; g < gsize.size(); g++) grp[g + 1] = grp[g] + gsize[g];
-        const int64_t gmax = std::max(1, max_sub / 32);
+        const int64_t gmax = std::max(1, max_sub / 16);
         int64_t g0 = 0;
         for (size_t bi = 0; bi < bins.size(); bi++) {  // in pairs of half-groups
             const int64_t g1 = gbin_end[bi] / 2, ng = g1 - g0, ns = (ng + gmax - 1) / gmax;
